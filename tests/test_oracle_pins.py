@@ -1,0 +1,329 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: exact
+lattice-point counts, the analytic point-lens magnification, conservation and
+symmetry invariants, the truncation bound of the Taylor series, values
+printed in the paper (tests/golden/table1.json) and finite differences.
+"""
+import dataclasses
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_14278_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+NO = np.zeros(0)
+
+
+def _geom(kappa, gamma, ks, lx, ly, sheet, map_box, map_n, **kw):
+    return oracle.derive_geometry(kappa, gamma, ks, lx, ly, sheet, map_box, map_n, **kw)
+
+
+# -- P1: no lenses, no sheet: the map is an affine image of the lattice ------
+
+def test_uniform_map_dyadic_exact():
+    """kappa = gamma = 1/4: beta = (theta_x / 2, theta_y); with dyadic spacings
+    every pixel receives exactly 8 x 4 = 32 rays and mu = 1/det = 2 (Eq. 12)."""
+    g = _geom(0.25, 0.25, 0.0, [], [], (0, 0, 1), (-1, -1, 1, 1), (32, 32),
+              ray_box=(-2, -1, 2, 1), ray_n=(256, 128))
+    counts, stats = oracle.shoot_direct(g, NO, NO, NO)
+    assert np.all(counts == 32)
+    assert list(stats) == [256 * 128, 0, 0]
+    mu = oracle.magnification(g, counts)
+    assert np.all(mu == 2.0)
+
+
+def _lattice_count_1d(a, r0, l3, n, m0, d, nb):
+    """Number of lattice points i in [0, n) with m0 + k d <= a (r0 + (i+1/2) l3)
+    < m0 + (k+1) d, for each bin k, by inverting the affine map (a > 0)."""
+    edges = m0 + np.arange(nb + 1) * d
+    first = np.ceil((edges / a - r0) / l3 - 0.5)          # first i at or past each edge
+    first = np.clip(first, 0, n)
+    return np.diff(first).astype(np.int64)
+
+
+def test_uniform_map_lattice_count():
+    """Non-dyadic macro model: each pixel count equals the product of the
+    numbers of lattice columns and rows whose images fall in it."""
+    kappa, gamma = 0.3, 0.17
+    a, b = 1 - kappa - gamma, 1 - kappa + gamma
+    g = _geom(kappa, gamma, 0.0, [], [], (0, 0, 1), (-1.0, -0.7, 0.9, 0.8), (37, 23),
+              ray_box=(-2.2, -1.1, 2.1, 1.0), ray_n=(731, 419))
+    counts, stats = oracle.shoot_direct(g, NO, NO, NO)
+    cx = _lattice_count_1d(a, g.rx0, g.l3x, g.n3x, g.mx0, g.dpx, g.mnx)
+    cy = _lattice_count_1d(b, g.ry0, g.l3y, g.n3y, g.my0, g.dpy, g.mny)
+    assert np.array_equal(counts.astype(np.int64), np.outer(cy, cx))
+    assert stats[0] == counts.sum() and stats[0] + stats[1] == g.n_rays
+
+
+# -- P2: single point lens, kappa = gamma = kappa_* = 0 ---------------------
+
+def test_point_lens_magnification():
+    """Pixel means of the analytic point-lens magnification
+    mu(u) = (u^2 + 2) / (u sqrt(u^2 + 4)) (Gauss-Legendre 16 x 16 per pixel)
+    against mu_ij = N_ij S_I / S_S.  Pixels within 2 of the lens are skipped."""
+    g = _geom(0.0, 0.0, 0.0, [0.0], [0.0], (0, 0, 1), (-1, -1, 1, 1), (32, 32),
+              ray_box=(-2.5, -2.5, 2.5, 2.5), ray_n=(4000, 4000))
+    counts, _ = oracle.shoot_direct(g, [0.0], [0.0], [1.0])
+    mu = oracle.magnification(g, counts)
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    W = np.outer(wg, wg) / 4.0
+    ref = np.zeros((32, 32))
+    for iy in range(32):
+        for ix in range(32):
+            X = -1 + (ix + (xg + 1) / 2) * g.dpx
+            Y = -1 + (iy + (xg + 1) / 2) * g.dpy
+            XX, YY = np.meshgrid(X, Y)
+            u = np.hypot(XX, YY)
+            ref[iy, ix] = np.sum(W * (u * u + 2) / (u * np.sqrt(u * u + 4)))
+    ii, jj = np.meshgrid(np.arange(32), np.arange(32))
+    keep = (np.abs(ii - 15.5) > 2.5) | (np.abs(jj - 15.5) > 2.5)
+    rel = ((mu - ref) / ref)[keep]
+    # lattice-sampling error: ~2500 rays per unit magnification per pixel
+    assert np.abs(rel).max() < 0.015
+    assert np.abs(rel).mean() < 0.003
+    assert abs(rel.mean()) < 0.001
+
+
+# -- P3, P4: ray conservation and split invariance ---------------------------
+
+def test_conservation_and_dropped_ray():
+    lf = inputs.lens_disc(30, 4.0, 5, "lognormal")
+    x, y, m = lf.x.copy(), lf.y.copy(), lf.m.copy()
+    g = _geom(0.4, 0.3, 0.02, x, y, (0, 0, 4.0), (-1, -1, 1, 1), (40, 40),
+              ray_box=(-3, -2, 3, 2), ray_n=(300, 200))
+    # put lens 0 exactly on ray (i, j) = (17, 9)
+    tx, ty = oracle.ray_position(g, [9 * 300 + 17])
+    x[0], y[0] = tx[0], ty[0]
+    counts, stats = oracle.shoot_direct(g, x, y, m)
+    assert stats[2] == 1
+    assert int(stats.sum()) == g.n_rays
+    assert int(counts.sum()) == int(stats[0])
+
+
+def test_split_invariance():
+    lf = inputs.lens_disc(25, 4.0, 6, "unit")
+    g = _geom(0.4, 0.3, 0.02, lf.x, lf.y, (0, 0, 4.0), (-1, -1, 1, 1), (40, 40),
+              ray_box=(-3, -2, 3, 2), ray_n=(300, 200))
+    full, s_full = oracle.shoot_direct(g, lf.x, lf.y, lf.m)
+    k = 12345
+    a, s_a = oracle.shoot_direct(g, lf.x, lf.y, lf.m, 0, k)
+    b, s_b = oracle.shoot_direct(g, lf.x, lf.y, lf.m, k, g.n_rays)
+    assert np.array_equal(full, a + b)
+    assert np.array_equal(s_full, s_a + s_b)
+
+
+# -- P5: mirror symmetry fixes the signs of both deflection components -------
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_mirror_symmetry(axis):
+    """Lenses mirrored across an axis, with a lattice and map symmetric about
+    it, give the mirrored map.  Spacings are dyadic so that mirrored rays sit
+    at exactly negated positions."""
+    lf = inputs.lens_disc(20, 3.0, 9, "lognormal")
+    x, y = lf.x, lf.y
+    kw = dict(ray_box=(-2.0, -2.0, 2.0, 2.0), ray_n=(512, 512))
+    g = _geom(0.35, 0.25, 0.03, x, y, (0, 0, 3.0), (-1, -1, 1, 1), (64, 64), **kw)
+    c1, _ = oracle.shoot_direct(g, x, y, lf.m)
+    mx, my = (-x, y) if axis == 0 else (x, -y)
+    c2, _ = oracle.shoot_direct(g, mx, my, lf.m)
+    flipped = c2[:, ::-1] if axis == 0 else c2[::-1, :]
+    assert np.array_equal(c1, flipped)
+    assert c1.sum() > 1000
+
+
+# -- P6: the far-field Taylor series against the direct sum ------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5])
+def test_interp_within_truncation_bound(p):
+    """|beta_interp - beta_direct| <= sum_far m rho^{p+1} / (r^{p+1} (r - rho)),
+    the tail of the geometric series of 1/(z_k - z), for every sampled ray;
+    the bound is nearly attained, so a wrong coefficient would break it."""
+    lf = inputs.lens_disc(40, 6.0, 3, "lognormal")
+    g = _geom(0.3, 0.2, 0.05, lf.x, lf.y, (0, 0, 6.0), (-2, -2, 2, 2), (64, 64),
+              ray_box=(-4, -3, 4, 3), ray_n=(400, 300), p=p)
+    idx = np.arange(0, g.n_rays, 61)
+    bd, fd = oracle.beta_direct(g, lf.x, lf.y, lf.m, idx)
+    bi, fi = oracle.beta_interp(g, lf.x, lf.y, lf.m, idx)
+    rb = oracle.remainder_bound(g, lf.x, lf.y, lf.m, idx)
+    err = np.hypot(*(bd - bi).T)
+    assert np.all(np.isfinite(rb))
+    assert np.all(err <= rb * (1 + 1e-9) + 1e-13)
+    assert np.max(err / rb) > 0.5          # the bound is tight, not vacuous
+    assert np.array_equal(fd, fi)
+
+
+def test_interp_converges_to_direct():
+    lf = inputs.lens_disc(40, 6.0, 3, "lognormal")
+    g = _geom(0.3, 0.2, 0.05, lf.x, lf.y, (0, 0, 6.0), (-2, -2, 2, 2), (64, 64),
+              ray_box=(-4, -3, 4, 3), ray_n=(400, 300), p=14)
+    idx = np.arange(0, g.n_rays, 211)
+    bd, _ = oracle.beta_direct(g, lf.x, lf.y, lf.m, idx)
+    bi, _ = oracle.beta_interp(g, lf.x, lf.y, lf.m, idx)
+    assert np.max(np.abs(bd - bi)) < 1e-12
+
+
+def test_node_coefficients_are_taylor_coefficients():
+    """c_n at a node equals the n-th Taylor coefficient of the far field,
+    checked by a complex-step-free route: a discrete Cauchy integral of the
+    far deflection sampled on a small circle around the node."""
+    lf = inputs.lens_disc(30, 5.0, 4, "unit")
+    g = _geom(0.3, 0.2, 0.05, lf.x, lf.y, (0, 0, 5.0), (-2, -2, 2, 2), (32, 32),
+              ray_box=(-4, -3, 4, 3), ray_n=(400, 300), p=4)
+    c2x, c2y = 7, 5
+    c = oracle.node_coeffs(g, lf.x, lf.y, lf.m, [c2x], [c2y])[0]
+    zx, zy = oracle.node_position(g, c2x, c2y)
+    z0 = complex(zx, zy)
+    c1x, c1y = c2x * g.n2x // g.n1x, c2y * g.n2y // g.n1y
+    l1x, l1y = g.n1x * g.l3x, g.n1y * g.l3y
+    cx = np.floor((lf.x - g.rx0) / l1x)
+    cy = np.floor((lf.y - g.ry0) / l1y)
+    far = ~((np.abs(cx - c1x) <= 1) & (np.abs(cy - c1y) <= 1))
+    zk = (lf.x + 1j * lf.y)[far]
+    mk = lf.m[far]
+    K, rad = 64, 0.2
+    zs = z0 + rad * np.exp(2j * np.pi * np.arange(K) / K)
+    f = np.array([np.sum(mk / (z - zk)) for z in zs])      # conj(alpha_far)
+    for n in range(5):
+        cauchy = np.mean(f * np.exp(-2j * np.pi * n * np.arange(K) / K)) / rad ** n
+        assert abs(cauchy - c[n]) <= 1e-10 * max(1.0, abs(c[0]))
+
+
+# -- P7: linearity of the deflection in the lens set --------------------------
+
+def test_linearity_in_lens_set():
+    lf = inputs.lens_disc(30, 4.0, 11, "lognormal")
+    g = _geom(0.4, 0.3, 0.02, lf.x, lf.y, (0, 0, 4.0), (-1, -1, 1, 1), (40, 40),
+              ray_box=(-3, -2, 3, 2), ray_n=(300, 200))
+    idx = np.arange(0, g.n_rays, 37)
+    ball, _ = oracle.beta_direct(g, lf.x, lf.y, lf.m, idx)
+    ba, _ = oracle.beta_direct(g, lf.x[:13], lf.y[:13], lf.m[:13], idx)
+    bb, _ = oracle.beta_direct(g, lf.x[13:], lf.y[13:], lf.m[13:], idx)
+    b0, _ = oracle.beta_direct(g, NO, NO, NO, idx)
+    assert np.allclose(ball, ba + bb - b0, rtol=0, atol=1e-11)
+
+
+# -- P8: the compensating sheet keeps the mean magnification -----------------
+
+def test_mean_magnification_with_compensating_sheet():
+    """With kappa_* = N m / R^2 and the sheet on the lens disc, the mean
+    magnification over the map is 1/|(1-kappa)^2 - gamma^2| (the protection
+    band of §3.1 is quoted as ~98% accurate).  Averaged over 16 fields."""
+    kappa, gamma, R = 0.3, 0.1, 38.0
+    mus = []
+    for seed in range(16):
+        n = int(round(0.05 * R * R))
+        lf = inputs.lens_disc(n, R, 100 + seed, "unit")
+        g = _geom(kappa, gamma, n / R ** 2, lf.x, lf.y, (0, 0, R), (-10, -10, 10, 10),
+                  (64, 64), n_av=100)
+        counts, _ = oracle.shoot_direct(g, lf.x, lf.y, lf.m)
+        mus.append(oracle.magnification(g, counts).mean())
+    expect = 1.0 / abs((1 - kappa) ** 2 - gamma ** 2)
+    assert abs(np.mean(mus) / expect - 1) < 0.03
+
+
+# -- P9: numbers printed in the paper ----------------------------------------
+
+def test_table1_and_figure2_values():
+    gold = json.load(open(os.path.join(GOLDEN, "table1.json")))
+    t = gold["table1"]
+    kc = oracle.kappa_c(t["theta_e_arcsec"], t["d_per_arcmin"])
+    assert float(f"{kc:.{t['kappa_c_printed_digits']}g}") == t["kappa_c"]
+    assert t["kappa_star"] > 10 * kc                 # "kappa_* >> kappa_c"
+    w = oracle.protection_width(t["kappa_star"])
+    assert round(-w, 6) == gold["fig2"]["beta_x_lower_edge"]
+    sx, sy = gold["section4_1"]["source_region"]
+    nx, ny = gold["section4_1"]["n_pix"]
+    assert abs(sx / nx - 5.5e-4) < 0.02 * 5.5e-4 and abs(sy / ny - 5.5e-4) < 0.02 * 5.5e-4
+    # N_* = L_ix L_iy kappa_* / pi inverts to the image-plane area of Table 1
+    area = math.pi * t["n_star"] / t["kappa_star"]
+    assert abs(oracle.n_star_from_area(area, t["kappa_star"]) - t["n_star"]) < 1e-9
+
+
+def test_level_grids_follow_eq10():
+    """Eq. 10: L1 = min(L0, L_i / 10), so at least ten level-1 cells per side;
+    level 2 is 1/20 of level 1."""
+    w = inputs.paper_map(0, n_rays=1e9, map_px=1024)
+    g = oracle.geometry_of(w)
+    assert g.N1x >= 10 and g.N1y >= 10
+    assert g.n1x == 20 * g.n2x and g.n1y == 20 * g.n2y
+    l1x = g.n1x * g.l3x
+    assert abs(l1x / g.l0 - 1) < 0.01                 # many lenses: L1 = L0 in x
+    # the uniform image of the ray rectangle is the widened source region
+    a = 1 - g.kappa - g.gamma
+    assert abs(a * g.rx0 - (w.map_box[0] - oracle.protection_width(g.kappa_star) / 2)) < 1e-9
+
+
+# -- Cloud-in-cell and its adjoint --------------------------------------------
+
+def test_cic_conserves_rays_in_interior():
+    """Without lenses every ray whose four neighbouring pixel centres lie in
+    the map deposits total weight 1."""
+    g = _geom(0.25, 0.25, 0.0, [], [], (0, 0, 1), (-1, -1, 1, 1), (32, 32),
+              ray_box=(-1.5, -0.75, 1.5, 0.75), ray_n=(300, 150))
+    M = oracle.cic_forward(g, NO, NO, NO)
+    # the lattice images into [-0.75, 0.75]^2, whose rays all have four in-map centres
+    assert abs(M.sum() - g.n_rays) < 1e-8
+
+
+def test_cic_gradient_matches_finite_differences():
+    lf = inputs.lens_disc(6, 5.0, 7, "lognormal")
+    lt = inputs.lens_disc(6, 5.0, 8, "lognormal")
+    g = _geom(0.3, 0.2, 0.05, lf.x, lf.y, (0, 0, 5.0), (-1.5, -1.5, 1.5, 1.5), (24, 24),
+              ray_box=(-3, -2, 3, 2), ray_n=(600, 400))
+    _, T = oracle.cic_loss(g, lt.x, lt.y, lt.m, np.zeros((24, 24)))
+    gl, gp = oracle.cic_grad(g, lf.x, lf.y, lf.m, T)
+    h = 1e-4
+    for k in range(4):
+        for c in range(3):
+            arr = [lf.x.copy(), lf.y.copy(), lf.m.copy()]
+            arr[c][k] += h
+            lp, _ = oracle.cic_loss(g, *arr, T)
+            arr[c][k] -= 2 * h
+            lm, _ = oracle.cic_loss(g, *arr, T)
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gl[k, c]) <= 0.01 * abs(gl[k, c]) + 1e-3 * np.abs(gl).max()
+    for q, name in enumerate(("kappa", "gamma", "kappa_star")):
+        lp, _ = oracle.cic_loss(dataclasses.replace(g, **{name: getattr(g, name) + h}),
+                                lf.x, lf.y, lf.m, T)
+        lm, _ = oracle.cic_loss(dataclasses.replace(g, **{name: getattr(g, name) - h}),
+                                lf.x, lf.y, lf.m, T)
+        assert abs((lp - lm) / (2 * h) - gp[q]) <= 0.01 * abs(gp[q])
+
+
+# -- Light curves -------------------------------------------------------------
+
+def test_gaussian_taps():
+    w = oracle.gaussian_taps(0.5)
+    assert len(w) == 5 and abs(w.sum() - 1) < 1e-15
+    assert abs(w[1] / w[2] - math.exp(-2.0)) < 1e-15
+
+
+def test_light_curves_pins():
+    """A constant map stays constant away from the edge; a single bright
+    pixel reproduces the source profile; a linear ramp is sampled exactly."""
+    mu = np.full((40, 50), 3.5)
+    tr = np.array([[10.0, 10.0, 40.0, 30.0]])
+    lc = oracle.light_curves(mu, tr, 33, 0.5)
+    assert np.allclose(lc, 3.5, rtol=0, atol=1e-14)
+
+    delta = np.zeros((21, 21))
+    delta[10, 10] = 1.0
+    w = oracle.gaussian_taps(0.5)
+    tr = np.array([[8.5, 10.5, 12.5, 10.5]])                # along the centre row
+    lc = oracle.light_curves(delta, tr, 5, 0.5)
+    assert np.allclose(lc[0], w[2] * w, rtol=0, atol=1e-15)
+
+    yy, xx = np.mgrid[0:30, 0:30]
+    ramp = 0.25 * xx - 0.5 * yy + 3.0
+    tr = np.array([[6.3, 7.1, 21.7, 19.9]])
+    lc = oracle.light_curves(ramp, tr, 17, 0.5)
+    t = np.linspace(0, 1, 17)
+    u = 6.3 + t * (21.7 - 6.3) - 0.5
+    v = 7.1 + t * (19.9 - 7.1) - 0.5
+    assert np.allclose(lc[0], 0.25 * u - 0.5 * v + 3.0, rtol=0, atol=1e-12)
