@@ -1,0 +1,250 @@
+/*
+ * ml.h - C ABI of the GB300 microlensing ray-shooting library.
+ *
+ * Computes source-plane magnification maps by inverse ray-shooting through a
+ * field of point-mass microlenses embedded in a locally linearised macro lens,
+ * following Yang, Chen, Zheng & Luo, "Simulation of the microlensing effect
+ * near the critical curve of the galaxy cluster" (§2-§3).
+ *
+ * Conventions (every entry point):
+ *  - Angles are in Einstein radii theta_E of the unit mass (Eq. 7); masses in
+ *    units of that mass.
+ *  - Every call returns an ml_status; nothing throws across the ABI.  On an
+ *    error, ml_last_error() returns a message for the calling thread.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are ordered on that stream; a call that must read device
+ *    results on the host (ml_field_create, ml_field_stats) synchronises it.
+ *  - The library owns ml_field objects and every device buffer inside them
+ *    (stream-ordered allocations on the device current at create time).  The
+ *    caller owns every pointer it passes in and every output buffer.
+ *  - Pointers documented as "device" must point to memory of the field's
+ *    device; "host" pointers to ordinary (pageable or pinned) host memory.
+ *  - The library is built for sm_103a only and fails with ML_ERR_CUDA on any
+ *    other device.  There is no CPU fallback.
+ */
+#ifndef ML_H
+#define ML_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ML_ABI_VERSION 1
+
+typedef enum {
+    ML_OK = 0,
+    ML_ERR_INVALID_ARG = 1,  /* a null pointer, a bad size or an inconsistent descriptor */
+    ML_ERR_OOM = 2,          /* a device or host allocation failed */
+    ML_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    ML_ERR_ABORTED = 4,      /* ml_field_abort() stopped a shooting run; the map holds a prefix */
+    ML_ERR_OVERFLOW = 5,     /* a uint32 pixel count wrapped; the map is invalid */
+    ML_ERR_STATE = 6,        /* the call does not fit the field's mode (e.g. counts of a CIC map) */
+    ML_ERR_UNSUPPORTED = 7   /* the inputs need a feature this build does not have */
+} ml_status;
+
+/* precision modes (ml_field_desc.precision) */
+#define ML_PREC_DIRECT64   0  /* FP64 direct sum over all lenses for every ray (§3.2, first formula) */
+#define ML_PREC_NEARFAR64  1  /* FP64 near/far scheme (Eq. 9), node coefficients in FP64 */
+#define ML_PREC_MIXED      2  /* near sum and Taylor evaluation in FP32 on node-relative
+                                 coordinates; node coefficients, node positions and the
+                                 integer pixel base in FP64 */
+
+/* deposition modes (ml_field_desc.deposit) */
+#define ML_DEPOSIT_NGP 0      /* nearest grid point: uint32 ray counts N_ij (§3.2) */
+#define ML_DEPOSIT_CIC 1      /* cloud in cell: float32 bilinear ray weights */
+
+/* coefficient builds (ml_field_desc.build) */
+#define ML_BUILD_AUTO         0  /* hierarchical when it is available, else direct */
+#define ML_BUILD_DIRECT       1  /* far-field sum evaluated at every level-2 node */
+#define ML_BUILD_HIERARCHICAL 2  /* high-order expansions shifted to the nodes */
+
+/* ml_magnification_map(want) */
+#define ML_MAP_COUNTS_U32 0   /* N_ij as uint32 (NGP only) */
+#define ML_MAP_MU_F32     1   /* mu_ij = N_ij S_I / S_S (Eq. 12) as float32 */
+#define ML_MAP_MU_F64     2   /* the same as float64 */
+
+/* indices into the array filled by ml_field_stats */
+#define ML_STAT_RAYS_IN     0  /* rays binned inside the map */
+#define ML_STAT_RAYS_OUT    1  /* rays landing outside the map */
+#define ML_STAT_RAYS_DROP   2  /* rays that hit a lens exactly (|theta - theta_k| = 0) */
+#define ML_STAT_NEAR_PAIRS  3  /* ray-lens pairs summed directly */
+#define ML_STAT_TASKS       4  /* warp tasks processed */
+#define ML_STAT_LAUNCHES    5  /* shooting kernel launches */
+#define ML_STAT_FLAGS       6  /* bit 0: count overflow, bit 1: aborted */
+#define ML_STAT_RAYS_ASKED  7  /* rays requested by ml_shoot_rays so far */
+
+typedef struct ml_field ml_field;  /* opaque, owned by the library */
+
+/*
+ * Description of one magnification map.  Zero-initialise, set abi_version =
+ * ML_ABI_VERSION, then fill in what is needed; zero fields take the defaults
+ * stated beside them.
+ */
+typedef struct {
+    int32_t abi_version;
+    int32_t precision;          /* ML_PREC_*; default ML_PREC_DIRECT64 (= 0) */
+    int32_t deposit;            /* ML_DEPOSIT_*; default NGP */
+    int32_t build;              /* ML_BUILD_*; default AUTO */
+
+    /* Macro model, Eq. 1 with constant convergence and shear: total kappa,
+     * shear gamma, and the stellar convergence kappa_* removed by the
+     * negative sheet of Eq. 6. */
+    double kappa, gamma, kappa_star;
+
+    /* Microlenses (Eq. 6): positions and masses, n_lens entries, FP64,
+     * copied at create time.  Host or device memory per lens_mem_is_device. */
+    const double *lens_x, *lens_y, *lens_m;
+    int64_t n_lens;
+    int32_t lens_mem_is_device;
+    int32_t taylor_p;           /* highest Taylor order of the far field; 0 = the
+                                   smallest order whose truncation bound meets far_tol */
+
+    /* Support of the negative mass sheet: a uniform disc of density
+     * -kappa_* with this centre and radius (reading of Eq. 6). */
+    double sheet_cx, sheet_cy, sheet_radius;
+
+    /* Ray rectangle (image plane).  All four zero: the pre-image of the map
+     * widened by the protection band 10 sqrt(kappa_*) per side (§3.1). */
+    double ray_x0, ray_y0, ray_x1, ray_y1;
+    /* Rays per side.  Both zero: N_rays = n_av * map_nx * map_ny (Eq. 8) on a
+     * square lattice of spacing L_3 (Eq. 11). */
+    int64_t n_rays_x, n_rays_y;
+    double n_av;
+
+    /* Source-plane map: [map_x0, map_x1) x [map_y0, map_y1), map_nx x map_ny
+     * pixels, row-major with x fastest. */
+    double map_x0, map_y0, map_x1, map_y1;
+    int32_t map_nx, map_ny;
+
+    /* Level grids (§3.2).  l1_x, l1_y zero: Eq. 10 on each side.  l2_sub zero:
+     * 20 level-2 cells per level-1 side. */
+    double l1_x, l1_y;
+    int32_t l2_sub;
+    int32_t reserved0;
+    double far_tol;             /* target truncation bound for taylor_p = 0; 0 = 1e-7 */
+    uint64_t max_launch_rays;   /* rays per shooting launch; 0 = 2^36 */
+} ml_field_desc;
+
+/* Derived parameters of a field (what §3.1-§3.2 compute from the desc). */
+typedef struct {
+    double ray_x0, ray_y0, ray_x1, ray_y1;  /* ray rectangle */
+    double l3x, l3y;                        /* level-3 pixel (ray spacing) */
+    int64_t n_rays_x, n_rays_y;             /* lattice size; ray r = j * n_rays_x + i */
+    double map_x0, map_y0, dpx, dpy;        /* map origin and pixel size */
+    int32_t map_nx, map_ny;
+    int64_t n_star_in;                      /* lenses inside the ray rectangle (N_* of §3.1) */
+    double l0;                              /* mean spacing per lens (Eq. 10); +inf if none */
+    int64_t n1x, n1y, n2x, n2y;             /* rays per level-1 and level-2 cell side */
+    int64_t N1x, N1y, N2x, N2y;             /* cells across the lattice */
+    int32_t taylor_p, l2_sub;
+    int32_t precision, deposit;
+    int32_t max_near;                       /* largest near-lens list of a level-1 cell */
+    int32_t build;                          /* coefficient build that ran (ML_BUILD_*) */
+    double far_bound;                       /* truncation bound at taylor_p (theta_E) */
+    double mu_per_count;                    /* S_I / S_S of Eq. 12 */
+} ml_field_params;
+
+/*
+ * ml_field_create - set up one map (§3.1 parameters, §3.2 level grids, the
+ * far-field Taylor coefficients at every level-2 node, a zeroed map).
+ *  desc:   host pointer, read only; lens arrays are copied.
+ *  stream: stream for the device work; synchronised before return.
+ *  out:    receives the new field (host pointer to a handle).
+ * Errors: ML_ERR_INVALID_ARG for a bad descriptor (null lens arrays with
+ * n_lens > 0, empty map, singular macro map with no explicit ray rectangle,
+ * non-positive sizes, abi_version mismatch); ML_ERR_UNSUPPORTED when the
+ * near/far modes meet rays outside the sheet's disc, or a level-1 cell has
+ * more near lenses than shared memory holds; ML_ERR_OOM; ML_ERR_CUDA.
+ * On error *out is NULL and nothing is leaked.
+ */
+ml_status ml_field_create(const ml_field_desc *desc, void *stream, ml_field **out);
+
+/*
+ * ml_shoot_rays - shoot rays with linear lattice indices [ray_begin, ray_end)
+ * (ray r = (i, j), i = r mod n_rays_x, j = r div n_rays_x, at the centre of
+ * level-3 pixel (i, j); §3.2 Level 3) and add them to the map: NGP counts
+ * N_ij, or CIC weights.  Accumulates across calls, so disjoint ranges can be
+ * shot in any order (bit-identical NGP result).  Asynchronous on `stream`;
+ * long ranges are split into launches of at most max_launch_rays rays.
+ * Errors: ML_ERR_INVALID_ARG if ray_begin > ray_end or ray_end exceeds the
+ * lattice; ML_ERR_CUDA.  Errors found inside kernels (overflow, abort) are
+ * reported by ml_field_stats / ml_field_check.
+ */
+ml_status ml_shoot_rays(ml_field *f, uint64_t ray_begin, uint64_t ray_end, void *stream);
+
+/*
+ * ml_magnification_map - write the map: want = ML_MAP_COUNTS_U32 (NGP counts,
+ * map_ny x map_nx uint32), ML_MAP_MU_F32 or ML_MAP_MU_F64 (mu_ij = N_ij S_I /
+ * S_S, Eq. 12; for CIC maps the weights take the place of N_ij).
+ *  out: caller-owned buffer of map_nx * map_ny elements, device memory if
+ *       out_is_device else host memory (then the call synchronises stream).
+ * Errors: ML_ERR_STATE for counts of a CIC map; ML_ERR_INVALID_ARG; ML_ERR_CUDA.
+ */
+ml_status ml_magnification_map(ml_field *f, int32_t want, void *out, int32_t out_is_device,
+                               void *stream);
+
+/*
+ * ml_light_curves - light curves of a Gaussian source (§4.1, Fig. 3): the
+ * magnification map convolved with a normalised Gaussian of sigma_px pixels
+ * (taps at integer offsets up to 4 sigma, zero outside the map), sampled
+ * bilinearly between pixel centres at n_samples equally spaced points of each
+ * straight track, endpoints included.
+ *  tracks: host, n_tracks x (x0, y0, x1, y1) in map pixel coordinates (pixel
+ *          i spans [i, i+1)).
+ *  out:    n_tracks x n_samples float32, device if out_is_device else host.
+ * Errors: ML_ERR_INVALID_ARG (sigma_px <= 0 or > 64, counts < 1); ML_ERR_CUDA.
+ */
+ml_status ml_light_curves(ml_field *f, const double *tracks, int32_t n_tracks, int32_t n_samples,
+                          double sigma_px, float *out, int32_t out_is_device, void *stream);
+
+/*
+ * ml_trace_rays - source positions of single rays by exactly the arithmetic
+ * the shooting kernel of the field's precision mode uses (for checking).
+ *  ray_idx: device, n linear ray indices (each < n_rays_x * n_rays_y).
+ *  beta:    device, n x 2 float64, source position in theta_E.
+ *  pix:     device, n x 2 int32, the pixel the shooting kernel bins the ray
+ *           into, (-1, -1) outside the map, (-2, -2) for a dropped ray,
+ *           (-3, -3) with NaN beta for an index outside the lattice.
+ * Errors: ML_ERR_INVALID_ARG; ML_ERR_CUDA.
+ */
+ml_status ml_trace_rays(ml_field *f, const int64_t *ray_idx, int64_t n, double *beta,
+                        int32_t *pix, void *stream);
+
+/*
+ * ml_field_clear - zero the map and the counters (stream-ordered).
+ */
+ml_status ml_field_clear(ml_field *f, void *stream);
+
+/*
+ * ml_field_stats - synchronise `stream` and copy the field's counters
+ * (ML_STAT_* indices) into out[8] (host).  Returns ML_ERR_OVERFLOW or
+ * ML_ERR_ABORTED when the corresponding flag is set, after filling out.
+ */
+ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream);
+
+/* ml_field_info - copy the derived parameters into *out (host). */
+ml_status ml_field_info(const ml_field *f, ml_field_params *out);
+
+/*
+ * ml_field_abort - raise (on != 0) or lower the field's abort flag.  It lives
+ * in mapped host memory; running shooting kernels read it between warp tasks
+ * and stop early, leaving a valid partial map and setting the aborted flag.
+ */
+ml_status ml_field_abort(ml_field *f, int32_t on);
+
+/* ml_field_destroy - free the field and its device memory.  NULL is a no-op. */
+ml_status ml_field_destroy(ml_field *f);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ml_last_error(void);
+
+/* ABI version the library was built with (ML_ABI_VERSION). */
+int32_t ml_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ML_H */

@@ -1,0 +1,307 @@
+"""GB300 microlensing ray-shooting library: thin Python binding.
+
+The work happens in the CUDA library built from csrc/ (include/ml.h is its C
+ABI).  This module only marshals arguments: the functions below carry the
+ABI's names (ml_field_create, ml_shoot_rays, ml_magnification_map,
+ml_light_curves, ...), take torch device tensors or numpy host arrays, and
+pass their pointers and the current CUDA stream through ctypes.  There is no
+CPU fallback: every call fails loudly if the library is missing.
+
+Yang, Chen, Zheng & Luo, "Simulation of the microlensing effect near the
+critical curve of the galaxy cluster": lens equation Eq. 6 / Eq. 9, the
+parameters of §3.1, the three-level grid of §3.2, magnification Eq. 12.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded synthetic inputs, no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libml.so")
+
+ABI_VERSION = 1
+PREC_DIRECT64, PREC_NEARFAR64, PREC_MIXED = 0, 1, 2
+DEPOSIT_NGP, DEPOSIT_CIC = 0, 1
+BUILD_AUTO, BUILD_DIRECT, BUILD_HIERARCHICAL = 0, 1, 2
+MAP_COUNTS_U32, MAP_MU_F32, MAP_MU_F64 = 0, 1, 2
+STAT_NAMES = ("rays_in", "rays_out", "rays_dropped", "near_pairs", "tasks", "launches",
+              "flags", "rays_asked")
+STATUS = {0: "ML_OK", 1: "ML_ERR_INVALID_ARG", 2: "ML_ERR_OOM", 3: "ML_ERR_CUDA",
+          4: "ML_ERR_ABORTED", 5: "ML_ERR_OVERFLOW", 6: "ML_ERR_STATE", 7: "ML_ERR_UNSUPPORTED"}
+
+# every symbol include/ml.h declares
+EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays",
+           "ml_magnification_map", "ml_light_curves", "ml_trace_rays", "ml_field_clear",
+           "ml_field_stats", "ml_field_info", "ml_field_abort", "ml_field_destroy")
+
+
+class MLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class FieldDesc(C.Structure):
+    """ml_field_desc of include/ml.h."""
+    _fields_ = [
+        ("abi_version", C.c_int32), ("precision", C.c_int32), ("deposit", C.c_int32),
+        ("build", C.c_int32),
+        ("kappa", C.c_double), ("gamma", C.c_double), ("kappa_star", C.c_double),
+        ("lens_x", C.c_void_p), ("lens_y", C.c_void_p), ("lens_m", C.c_void_p),
+        ("n_lens", C.c_int64), ("lens_mem_is_device", C.c_int32), ("taylor_p", C.c_int32),
+        ("sheet_cx", C.c_double), ("sheet_cy", C.c_double), ("sheet_radius", C.c_double),
+        ("ray_x0", C.c_double), ("ray_y0", C.c_double), ("ray_x1", C.c_double),
+        ("ray_y1", C.c_double),
+        ("n_rays_x", C.c_int64), ("n_rays_y", C.c_int64), ("n_av", C.c_double),
+        ("map_x0", C.c_double), ("map_y0", C.c_double), ("map_x1", C.c_double),
+        ("map_y1", C.c_double), ("map_nx", C.c_int32), ("map_ny", C.c_int32),
+        ("l1_x", C.c_double), ("l1_y", C.c_double), ("l2_sub", C.c_int32),
+        ("reserved0", C.c_int32), ("far_tol", C.c_double), ("max_launch_rays", C.c_uint64),
+    ]
+
+
+class FieldParams(C.Structure):
+    """ml_field_params of include/ml.h."""
+    _fields_ = [
+        ("ray_x0", C.c_double), ("ray_y0", C.c_double), ("ray_x1", C.c_double),
+        ("ray_y1", C.c_double), ("l3x", C.c_double), ("l3y", C.c_double),
+        ("n_rays_x", C.c_int64), ("n_rays_y", C.c_int64),
+        ("map_x0", C.c_double), ("map_y0", C.c_double), ("dpx", C.c_double), ("dpy", C.c_double),
+        ("map_nx", C.c_int32), ("map_ny", C.c_int32),
+        ("n_star_in", C.c_int64), ("l0", C.c_double),
+        ("n1x", C.c_int64), ("n1y", C.c_int64), ("n2x", C.c_int64), ("n2y", C.c_int64),
+        ("N1x", C.c_int64), ("N1y", C.c_int64), ("N2x", C.c_int64), ("N2y", C.c_int64),
+        ("taylor_p", C.c_int32), ("l2_sub", C.c_int32), ("precision", C.c_int32),
+        ("deposit", C.c_int32), ("max_near", C.c_int32), ("build", C.c_int32),
+        ("far_bound", C.c_double), ("mu_per_count", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (built by build.build_library or __graft_entry__.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built ({path} missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    P, V = C.POINTER, C.c_void_p
+    st = C.c_int
+    sig = {
+        "ml_abi_version": ([], C.c_int32),
+        "ml_last_error": ([], C.c_char_p),
+        "ml_field_create": ([P(FieldDesc), V, P(V)], st),
+        "ml_shoot_rays": ([V, C.c_uint64, C.c_uint64, V], st),
+        "ml_magnification_map": ([V, C.c_int32, V, C.c_int32, V], st),
+        "ml_light_curves": ([V, V, C.c_int32, C.c_int32, C.c_double, V, C.c_int32, V], st),
+        "ml_trace_rays": ([V, V, C.c_int64, V, V, V], st),
+        "ml_field_clear": ([V, V], st),
+        "ml_field_stats": ([V, P(C.c_uint64), V], st),
+        "ml_field_info": ([V, P(FieldParams)], st),
+        "ml_field_abort": ([V, C.c_int32], st),
+        "ml_field_destroy": ([V], st),
+    }
+    for name, (argt, rest) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = argt
+        f.restype = rest
+    if lib.ml_abi_version() != ABI_VERSION:
+        raise RuntimeError("libml.so ABI version mismatch")
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise MLError(status, load().ml_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (must be contiguous, on CUDA)."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+# ---- functions with the ABI's names ------------------------------------------
+
+def ml_field_create(desc: FieldDesc, stream=None):
+    h = C.c_void_p()
+    _check(load().ml_field_create(C.byref(desc), _stream(stream), C.byref(h)))
+    return h
+
+
+def ml_shoot_rays(field, ray_begin: int, ray_end: int, stream=None):
+    _check(load().ml_shoot_rays(field, int(ray_begin), int(ray_end), _stream(stream)))
+
+
+def ml_magnification_map(field, want: int, out, stream=None):
+    """out: torch CUDA tensor (device) or numpy array (host)."""
+    if isinstance(out, np.ndarray):
+        _check(load().ml_magnification_map(field, want, out.ctypes.data, 0, _stream(stream)))
+    else:
+        _check(load().ml_magnification_map(field, want, _dptr(out), 1, _stream(stream)))
+
+
+def ml_light_curves(field, tracks, n_samples: int, sigma_px: float, out, stream=None):
+    tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
+    if isinstance(out, np.ndarray):
+        _check(load().ml_light_curves(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
+                                      out.ctypes.data, 0, _stream(stream)))
+    else:
+        _check(load().ml_light_curves(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
+                                      _dptr(out), 1, _stream(stream)))
+
+
+def ml_trace_rays(field, ray_idx, beta, pix, stream=None):
+    _check(load().ml_trace_rays(field, _dptr(ray_idx), ray_idx.numel(), _dptr(beta), _dptr(pix),
+                                _stream(stream)))
+
+
+def ml_field_clear(field, stream=None):
+    _check(load().ml_field_clear(field, _stream(stream)))
+
+
+def ml_field_stats(field, stream=None, check=True):
+    out = (C.c_uint64 * 8)()
+    st = load().ml_field_stats(field, out, _stream(stream))
+    d = dict(zip(STAT_NAMES, list(out)))
+    if check:
+        _check(st)
+    return d, st
+
+
+def ml_field_info(field) -> dict:
+    p = FieldParams()
+    _check(load().ml_field_info(field, C.byref(p)))
+    return p.as_dict()
+
+
+def ml_field_abort(field, on: bool):
+    _check(load().ml_field_abort(field, 1 if on else 0))
+
+
+def ml_field_destroy(field):
+    _check(load().ml_field_destroy(field))
+
+
+# ---- convenience wrapper -------------------------------------------------------
+
+def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_AUTO,
+              taylor_p=0, far_tol=0.0, l1=None, l2_sub=0, max_launch_rays=0, lens_arrays=None):
+    """ml_field_desc for an inputs.Workload (lens arrays from host numpy)."""
+    w = workload
+    lx, ly, lm = lens_arrays if lens_arrays is not None else (w.lenses.x, w.lenses.y, w.lenses.m)
+    lx = np.ascontiguousarray(lx, np.float64)
+    ly = np.ascontiguousarray(ly, np.float64)
+    lm = np.ascontiguousarray(lm, np.float64)
+    d = FieldDesc()
+    d.abi_version = ABI_VERSION
+    d.precision, d.deposit, d.build = precision, deposit, build
+    d.kappa, d.gamma, d.kappa_star = w.kappa, w.gamma, w.kappa_star
+    d.lens_x, d.lens_y, d.lens_m = lx.ctypes.data, ly.ctypes.data, lm.ctypes.data
+    d.n_lens = len(lx)
+    d.lens_mem_is_device = 0
+    d.taylor_p = taylor_p
+    d.sheet_cx, d.sheet_cy, d.sheet_radius = w.sheet
+    if w.ray_box is not None:
+        d.ray_x0, d.ray_y0, d.ray_x1, d.ray_y1 = w.ray_box
+    if w.ray_n is not None:
+        d.n_rays_x, d.n_rays_y = w.ray_n
+    d.n_av = w.n_av
+    d.map_x0, d.map_y0, d.map_x1, d.map_y1 = w.map_box
+    d.map_nx, d.map_ny = w.map_n
+    if l1 is not None:
+        d.l1_x, d.l1_y = l1
+    d.l2_sub = l2_sub
+    d.far_tol = far_tol
+    d.max_launch_rays = max_launch_rays
+    d._keep = (lx, ly, lm)       # keep the arrays alive until create returns
+    return d
+
+
+class Field:
+    """One magnification map on the current CUDA device."""
+
+    def __init__(self, workload=None, desc: FieldDesc | None = None, stream=None, **kw):
+        if desc is None:
+            desc = make_desc(workload, **kw)
+        self.desc = desc
+        self.h = ml_field_create(desc, stream)
+        self.info = ml_field_info(self.h)
+
+    @property
+    def n_rays(self) -> int:
+        return self.info["n_rays_x"] * self.info["n_rays_y"]
+
+    def shoot(self, ray_begin=0, ray_end=None, stream=None):
+        ml_shoot_rays(self.h, ray_begin, self.n_rays if ray_end is None else ray_end, stream)
+
+    def counts(self, stream=None):
+        import torch
+        out = torch.empty((self.info["map_ny"], self.info["map_nx"]), dtype=torch.int32,
+                          device="cuda")
+        ml_magnification_map(self.h, MAP_COUNTS_U32, out, stream)
+        return out
+
+    def mu(self, dtype="f32", stream=None):
+        import torch
+        td = torch.float32 if dtype == "f32" else torch.float64
+        out = torch.empty((self.info["map_ny"], self.info["map_nx"]), dtype=td, device="cuda")
+        ml_magnification_map(self.h, MAP_MU_F32 if dtype == "f32" else MAP_MU_F64, out, stream)
+        return out
+
+    def light_curves(self, tracks, n_samples, sigma_px, stream=None):
+        import torch
+        out = torch.empty((len(tracks), n_samples), dtype=torch.float32, device="cuda")
+        ml_light_curves(self.h, tracks, n_samples, sigma_px, out, stream)
+        return out
+
+    def trace(self, idx, stream=None):
+        import torch
+        idx = torch.as_tensor(np.asarray(idx, np.int64)).cuda()
+        beta = torch.empty((idx.numel(), 2), dtype=torch.float64, device="cuda")
+        pix = torch.empty((idx.numel(), 2), dtype=torch.int32, device="cuda")
+        ml_trace_rays(self.h, idx, beta, pix, stream)
+        return beta, pix
+
+    def stats(self, stream=None, check=True):
+        return ml_field_stats(self.h, stream, check)[0]
+
+    def clear(self, stream=None):
+        ml_field_clear(self.h, stream)
+
+    def abort(self, on=True):
+        ml_field_abort(self.h, on)
+
+    def close(self):
+        if self.h is not None:
+            ml_field_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,630 @@
+// C ABI of the microlensing library: descriptor validation, the parameter
+// derivation of §3.1-§3.2, device buffers, and stream-ordered launches.
+#include "ml_internal.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+using namespace ml;
+
+namespace {
+
+thread_local std::string g_err;
+
+ml_status fail(ml_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+ml_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? ML_ERR_OOM : ML_ERR_CUDA;
+}
+
+#define ML_CK(call)                                                   \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);           \
+    } while (0)
+
+}  // namespace
+
+struct ml_field {
+    Geo g{};
+    int device = 0;
+    int num_sms = 0;
+    int build_used = 0;
+    double far_bound = 0.0;
+    int32_t max_near = 0;
+    uint64_t max_launch_rays = 0;
+    uint64_t rays_asked = 0, launches = 0;
+    int64_t n_lens = 0;
+    // device buffers
+    double *d_x = nullptr, *d_y = nullptr, *d_m = nullptr;
+    int32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_cursor = nullptr;
+    double *d_sx = nullptr, *d_sy = nullptr, *d_sm = nullptr;
+    int32_t *d_scell = nullptr;
+    double *d_coef64 = nullptr;
+    unsigned char *d_nodes = nullptr;
+    uint32_t *d_map_u32 = nullptr;
+    float *d_map_f32 = nullptr;
+    unsigned long long *d_stats = nullptr, *d_work = nullptr;
+    unsigned int *d_status = nullptr;
+    int *h_abort = nullptr, *d_abort = nullptr;
+    std::vector<void *> owned;       // device allocations to free
+
+    template <class T>
+    cudaError_t alloc(T **p, size_t count, cudaStream_t s)
+    {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), s);
+        if (e == cudaSuccess) owned.push_back(*p);
+        return e;
+    }
+    void release()
+    {
+        if (!owned.empty() || h_abort) cudaDeviceSynchronize();
+        for (void *p : owned) cudaFree(p);
+        owned.clear();
+        if (h_abort) cudaFreeHost(h_abort);
+        h_abort = nullptr;
+    }
+    LensTable table() const
+    {
+        LensTable L;
+        L.x = d_sx; L.y = d_sy; L.m = d_sm; L.cell = d_scell; L.start = d_start; L.n = n_lens;
+        return L;
+    }
+};
+
+namespace {
+
+bool is_fin(double v) { return isfinite(v) != 0; }
+
+int64_t round_half_up(double v) { return (int64_t)floor(v + 0.5); }
+
+// §3.1-§3.2: ray rectangle, lattice, N_*, level grids.
+ml_status derive_geometry(const ml_field_desc &d, const std::vector<double> &hx,
+                          const std::vector<double> &hy, Geo &g)
+{
+    g.kappa = d.kappa;
+    g.gamma = d.gamma;
+    g.kappa_star = d.kappa_star;
+    g.sheet_cx = d.sheet_cx;
+    g.sheet_cy = d.sheet_cy;
+    g.sheet_r = d.sheet_radius;
+    g.precision = d.precision;
+    g.deposit = d.deposit;
+    g.mnx = d.map_nx;
+    g.mny = d.map_ny;
+    g.mx0 = d.map_x0;
+    g.my0 = d.map_y0;
+    g.dpx = (d.map_x1 - d.map_x0) / d.map_nx;
+    g.dpy = (d.map_y1 - d.map_y0) / d.map_ny;
+    double rx0, rx1, ry0, ry1;
+    if (d.ray_x0 == 0.0 && d.ray_y0 == 0.0 && d.ray_x1 == 0.0 && d.ray_y1 == 0.0) {
+        // pre-image of s' = s widened by 10 sqrt(kappa_*) per side (§3.1)
+        double w = 0.5 * (20.0 * sqrt(d.kappa_star));
+        double a = 1.0 - d.kappa - d.gamma, b = 1.0 - d.kappa + d.gamma;
+        if (a == 0.0 || b == 0.0)
+            return fail(ML_ERR_INVALID_ARG, "macro map is singular (1-kappa-gamma or 1-kappa+gamma "
+                                            "is 0): give the ray rectangle explicitly");
+        double xa = (d.map_x0 - w) / a, xb = (d.map_x1 + w) / a;
+        double ya = (d.map_y0 - w) / b, yb = (d.map_y1 + w) / b;
+        rx0 = std::min(xa, xb); rx1 = std::max(xa, xb);
+        ry0 = std::min(ya, yb); ry1 = std::max(ya, yb);
+    } else {
+        rx0 = d.ray_x0; rx1 = d.ray_x1; ry0 = d.ray_y0; ry1 = d.ray_y1;
+    }
+    if (!(rx1 > rx0) || !(ry1 > ry0) || !is_fin(rx0) || !is_fin(rx1) || !is_fin(ry0) ||
+        !is_fin(ry1))
+        return fail(ML_ERR_INVALID_ARG, "empty or non-finite ray rectangle");
+    g.rx0 = rx0; g.rx1 = rx1; g.ry0 = ry0; g.ry1 = ry1;
+    double lix = rx1 - rx0, liy = ry1 - ry0;
+    if (d.n_rays_x == 0 && d.n_rays_y == 0) {
+        if (!(d.n_av > 0.0) || !is_fin(d.n_av))
+            return fail(ML_ERR_INVALID_ARG, "need n_av > 0 or explicit n_rays_x, n_rays_y");
+        double n_rays = d.n_av * d.map_nx * d.map_ny;          // Eq. 8
+        double l3 = sqrt(lix * liy / n_rays);                  // Eq. 11
+        g.n3x = std::max<int64_t>(1, round_half_up(lix / l3));
+        g.n3y = std::max<int64_t>(1, round_half_up(liy / l3));
+    } else {
+        if (d.n_rays_x <= 0 || d.n_rays_y <= 0)
+            return fail(ML_ERR_INVALID_ARG, "n_rays_x and n_rays_y must both be positive");
+        g.n3x = d.n_rays_x;
+        g.n3y = d.n_rays_y;
+    }
+    if ((double)g.n3x * (double)g.n3y > 9.0e18)
+        return fail(ML_ERR_INVALID_ARG, "ray lattice too large for 64-bit indices");
+    g.l3x = lix / g.n3x;
+    g.l3y = liy / g.n3y;
+    int64_t n_in = 0;
+    for (size_t k = 0; k < hx.size(); ++k)
+        if (hx[k] >= rx0 && hx[k] < rx1 && hy[k] >= ry0 && hy[k] < ry1) ++n_in;
+    g.n_star_in = n_in;
+    g.l0 = n_in > 0 ? sqrt(lix * liy / (double)n_in) : INFINITY;
+    double l1x = d.l1_x > 0.0 ? d.l1_x : std::min(g.l0, lix / 10.0);   // Eq. 10
+    double l1y = d.l1_y > 0.0 ? d.l1_y : std::min(g.l0, liy / 10.0);
+    g.l2sub = d.l2_sub > 0 ? d.l2_sub : 20;
+    double l2x = l1x / g.l2sub, l2y = l1y / g.l2sub;
+    g.n2x = std::max<int64_t>(1, round_half_up(l2x / g.l3x));
+    g.n2y = std::max<int64_t>(1, round_half_up(l2y / g.l3y));
+    g.n1x = g.l2sub * g.n2x;
+    g.n1y = g.l2sub * g.n2y;
+    g.N1x = (g.n3x + g.n1x - 1) / g.n1x;
+    g.N1y = (g.n3y + g.n1y - 1) / g.n1y;
+    g.N2x = (g.n3x + g.n2x - 1) / g.n2x;
+    g.N2y = (g.n3y + g.n2y - 1) / g.n2y;
+    g.l1x = (double)g.n1x * g.l3x;
+    g.l1y = (double)g.n1y * g.l3y;
+    g.l2x = (double)g.n2x * g.l3x;
+    g.l2y = (double)g.n2y * g.l3y;
+    g.NEx = g.N1x + 2;
+    g.NEy = g.N1y + 2;
+    return ML_OK;
+}
+
+ml_status validate(const ml_field_desc *d)
+{
+    if (!d) return fail(ML_ERR_INVALID_ARG, "desc is NULL");
+    if (d->abi_version != ML_ABI_VERSION)
+        return fail(ML_ERR_INVALID_ARG, "abi_version mismatch (expected " +
+                                            std::to_string(ML_ABI_VERSION) + ")");
+    if (d->precision < ML_PREC_DIRECT64 || d->precision > ML_PREC_MIXED)
+        return fail(ML_ERR_INVALID_ARG, "unknown precision mode");
+    if (d->deposit != ML_DEPOSIT_NGP && d->deposit != ML_DEPOSIT_CIC)
+        return fail(ML_ERR_INVALID_ARG, "unknown deposit mode");
+    if (d->build < ML_BUILD_AUTO || d->build > ML_BUILD_HIERARCHICAL)
+        return fail(ML_ERR_INVALID_ARG, "unknown build mode");
+    if (d->n_lens < 0) return fail(ML_ERR_INVALID_ARG, "n_lens < 0");
+    if (d->n_lens > 0 && (!d->lens_x || !d->lens_y || !d->lens_m))
+        return fail(ML_ERR_INVALID_ARG, "lens arrays are NULL");
+    if (d->n_lens > (1 << 30)) return fail(ML_ERR_INVALID_ARG, "too many lenses (max 2^30)");
+    if (d->map_nx <= 0 || d->map_ny <= 0) return fail(ML_ERR_INVALID_ARG, "empty map");
+    if ((uint64_t)d->map_nx * (uint64_t)d->map_ny >= 0xFFFFFFF0ull)
+        return fail(ML_ERR_INVALID_ARG, "map has 2^32 pixels or more");
+    if (!(d->map_x1 > d->map_x0) || !(d->map_y1 > d->map_y0) || !is_fin(d->map_x0) ||
+        !is_fin(d->map_x1) || !is_fin(d->map_y0) || !is_fin(d->map_y1))
+        return fail(ML_ERR_INVALID_ARG, "map rectangle is empty or not finite");
+    if (!is_fin(d->kappa) || !is_fin(d->gamma) || !is_fin(d->kappa_star) || d->kappa_star < 0.0)
+        return fail(ML_ERR_INVALID_ARG, "kappa, gamma must be finite and kappa_* >= 0");
+    if (!is_fin(d->sheet_cx) || !is_fin(d->sheet_cy) || !is_fin(d->sheet_radius) ||
+        d->sheet_radius < 0.0)
+        return fail(ML_ERR_INVALID_ARG, "sheet disc must be finite with radius >= 0");
+    if (d->taylor_p < 0 || d->taylor_p > PMAX)
+        return fail(ML_ERR_INVALID_ARG, "taylor_p must be in [0, 16]");
+    if (d->l2_sub < 0 || d->l2_sub > 4096) return fail(ML_ERR_INVALID_ARG, "bad l2_sub");
+    if (d->l1_x < 0.0 || d->l1_y < 0.0) return fail(ML_ERR_INVALID_ARG, "negative l1 size");
+    if (d->far_tol < 0.0) return fail(ML_ERR_INVALID_ARG, "negative far_tol");
+    return ML_OK;
+}
+
+bool rays_inside_sheet(const Geo &g)
+{
+    double R2 = g.sheet_r * g.sheet_r;
+    double xs[2] = {g.rx0 - g.sheet_cx, g.rx1 - g.sheet_cx};
+    double ys[2] = {g.ry0 - g.sheet_cy, g.ry1 - g.sheet_cy};
+    for (double x : xs)
+        for (double y : ys)
+            if (x * x + y * y > R2) return false;
+    return true;
+}
+
+ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
+{
+    ML_CK(cudaGetDevice(&f->device));
+    cudaDeviceProp prop;
+    ML_CK(cudaGetDeviceProperties(&prop, f->device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(ML_ERR_CUDA, "this library is built for sm_103a (GB300); device is sm_" +
+                                     std::to_string(prop.major) + std::to_string(prop.minor));
+    f->num_sms = prop.multiProcessorCount;
+
+    const int64_t n = d->n_lens;
+    f->n_lens = n;
+    std::vector<double> hx(n), hy(n), hm(n);
+    if (n > 0) {
+        if (d->lens_mem_is_device) {
+            ML_CK(cudaMemcpy(hx.data(), d->lens_x, n * sizeof(double), cudaMemcpyDeviceToHost));
+            ML_CK(cudaMemcpy(hy.data(), d->lens_y, n * sizeof(double), cudaMemcpyDeviceToHost));
+            ML_CK(cudaMemcpy(hm.data(), d->lens_m, n * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+            memcpy(hx.data(), d->lens_x, n * sizeof(double));
+            memcpy(hy.data(), d->lens_y, n * sizeof(double));
+            memcpy(hm.data(), d->lens_m, n * sizeof(double));
+        }
+        for (int64_t k = 0; k < n; ++k)
+            if (!is_fin(hx[k]) || !is_fin(hy[k]) || !is_fin(hm[k]))
+                return fail(ML_ERR_INVALID_ARG, "lens " + std::to_string(k) + " is not finite");
+    }
+    ml_status st = derive_geometry(*d, hx, hy, f->g);
+    if (st != ML_OK) return st;
+    Geo &g = f->g;
+    const bool nearfar = d->precision != ML_PREC_DIRECT64;
+    if (nearfar && !rays_inside_sheet(g))
+        return fail(ML_ERR_UNSUPPORTED, "near/far modes need the whole ray rectangle inside the "
+                                        "sheet's disc; use ML_PREC_DIRECT64");
+    if (d->precision == ML_PREC_MIXED &&
+        (g.n2x >= (1 << 23) || g.n2y >= (1 << 22) || g.n1y > (int64_t)1 << 40))
+        return fail(ML_ERR_UNSUPPORTED, "level-2 cells too large for FP32 offsets");
+    if (g.NEx * g.NEy >= (int64_t)1 << 30)
+        return fail(ML_ERR_UNSUPPORTED, "level-1 grid too large");
+    f->max_launch_rays = d->max_launch_rays ? d->max_launch_rays : (1ull << 36);
+
+    // lenses, binning (§3.2 Level 1)
+    const int64_t NE = g.NEx * g.NEy;
+    ML_CK(f->alloc(&f->d_x, n, s));
+    ML_CK(f->alloc(&f->d_y, n, s));
+    ML_CK(f->alloc(&f->d_m, n, s));
+    ML_CK(f->alloc(&f->d_cell, n, s));
+    ML_CK(f->alloc(&f->d_count, NE + 1, s));
+    ML_CK(f->alloc(&f->d_start, NE + 2, s));
+    ML_CK(f->alloc(&f->d_cursor, NE + 1, s));
+    ML_CK(f->alloc(&f->d_sx, n, s));
+    ML_CK(f->alloc(&f->d_sy, n, s));
+    ML_CK(f->alloc(&f->d_sm, n, s));
+    ML_CK(f->alloc(&f->d_scell, n, s));
+    ML_CK(f->alloc(&f->d_stats, 8, s));
+    ML_CK(f->alloc(&f->d_work, 1, s));
+    ML_CK(f->alloc(&f->d_status, 1, s));
+    ML_CK(cudaHostAlloc((void **)&f->h_abort, sizeof(int), cudaHostAllocMapped));
+    *f->h_abort = 0;
+    ML_CK(cudaHostGetDevicePointer((void **)&f->d_abort, f->h_abort, 0));
+    if (n > 0) {
+        ML_CK(cudaMemcpyAsync(f->d_x, hx.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        ML_CK(cudaMemcpyAsync(f->d_y, hy.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        ML_CK(cudaMemcpyAsync(f->d_m, hm.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    ML_CK(cudaMemsetAsync(f->d_count, 0, (NE + 1) * sizeof(int32_t), s));
+    ML_CK(cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s));
+    ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
+    ML_CK(launch_lens_cells(g, f->d_x, f->d_y, n, f->d_cell, f->d_count, s));
+    ML_CK(launch_scan(f->d_count, f->d_start, NE + 1, s));
+    ML_CK(launch_scatter(f->d_x, f->d_y, f->d_m, f->d_cell, n, f->d_start, NE + 1, f->d_cursor,
+                         f->d_sx, f->d_sy, f->d_sm, f->d_scell, s));
+    LensTable L = f->table();
+
+    if (nearfar) {
+        // largest near list: the 3 x 3 block of each level-1 cell
+        std::vector<int32_t> start(NE + 2);
+        ML_CK(cudaMemcpyAsync(start.data(), f->d_start, (NE + 2) * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, s));
+        ML_CK(cudaStreamSynchronize(s));
+        int32_t mx = 0;
+        for (int64_t cy = 0; cy < g.N1y; ++cy)
+            for (int64_t cx = 0; cx < g.N1x; ++cx) {
+                int32_t t = 0;
+                for (int64_t ey = cy; ey <= cy + 2; ++ey) {
+                    int64_t b = ey * g.NEx + cx;
+                    t += start[b + 3] - start[b];
+                }
+                mx = std::max(mx, t);
+            }
+        f->max_near = mx;
+        if (d->precision == ML_PREC_MIXED && (int64_t)mx * WARPS_PER_CTA * 24 > 200 * 1024)
+            return fail(ML_ERR_UNSUPPORTED, "a level-1 cell has " + std::to_string(mx) +
+                                                " near lenses; use a finer level-1 grid (l1_x, l1_y)");
+
+        // Taylor order: the smallest whose truncation bound meets far_tol
+        std::vector<double> bound((size_t)(g.N1x * g.N1y) * PMAX);
+        double *d_bound = nullptr;
+        ML_CK(cudaMallocAsync((void **)&d_bound, bound.size() * sizeof(double), s));
+        g.p = 1;
+        cudaError_t e = launch_p_bound(g, L, d_bound, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bound.data(), d_bound, bound.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(d_bound, s);
+        if (e != cudaSuccess) return cuda_fail(e, "truncation bound");
+        ML_CK(cudaStreamSynchronize(s));
+        std::vector<double> worst(PMAX, 0.0);
+        for (size_t c = 0; c < bound.size() / PMAX; ++c)
+            for (int q = 0; q < PMAX; ++q) worst[q] = std::max(worst[q], bound[c * PMAX + q]);
+        int p = d->taylor_p;
+        if (p == 0) {
+            double tol = d->far_tol > 0.0 ? d->far_tol : 1e-7;
+            p = PMAX;
+            for (int q = 1; q <= PMAX; ++q)
+                if (worst[q - 1] <= tol) { p = q; break; }
+        }
+        if (d->precision == ML_PREC_MIXED) p = mixed_p_supported(p);
+        g.p = p;
+        f->far_bound = worst[p - 1];
+
+        // far-field Taylor coefficients at the level-2 nodes (§3.2 Level 2)
+        const int64_t nodes = g.N2x * g.N2y;
+        ML_CK(f->alloc(&f->d_coef64, (size_t)nodes * (p + 1) * 2, s));
+        f->build_used = ML_BUILD_DIRECT;
+        bool done = false;
+        if (d->build != ML_BUILD_DIRECT) {
+            size_t ns = hier_scratch_doubles(g);
+            if (ns > 0) {
+                double *scratch = nullptr;
+                ML_CK(cudaMallocAsync((void **)&scratch, ns * sizeof(double), s));
+                e = launch_coeffs_hier(g, L, f->d_coef64, scratch, ns, s);
+                cudaFreeAsync(scratch, s);
+                if (e != cudaSuccess) return cuda_fail(e, "hierarchical coefficient build");
+                f->build_used = ML_BUILD_HIERARCHICAL;
+                done = true;
+            } else if (d->build == ML_BUILD_HIERARCHICAL) {
+                return fail(ML_ERR_UNSUPPORTED, "hierarchical build not available");
+            }
+        }
+        if (!done) ML_CK(launch_coeffs_direct(g, L, f->d_coef64, s));
+        if (d->precision == ML_PREC_MIXED) {
+            ML_CK(f->alloc(&f->d_nodes, (size_t)nodes * node_stride(p), s));
+            ML_CK(launch_node_finalize(g, f->d_coef64, f->d_nodes, s));
+        }
+    } else {
+        g.p = 0;
+    }
+
+    const size_t npix = (size_t)g.mnx * g.mny;
+    if (d->deposit == ML_DEPOSIT_NGP) {
+        ML_CK(f->alloc(&f->d_map_u32, npix, s));
+        ML_CK(cudaMemsetAsync(f->d_map_u32, 0, npix * sizeof(uint32_t), s));
+    } else {
+        ML_CK(f->alloc(&f->d_map_f32, npix, s));
+        ML_CK(cudaMemsetAsync(f->d_map_f32, 0, npix * sizeof(float), s));
+    }
+    ML_CK(cudaStreamSynchronize(s));
+    ML_CK(cudaGetLastError());
+    return ML_OK;
+}
+
+ShootArgs make_args(const ml_field *f)
+{
+    ShootArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = f->g;
+    a.L = f->table();
+    a.coef64 = f->d_coef64;
+    a.nodes = f->d_nodes;
+    a.map_u32 = f->d_map_u32;
+    a.map_f32 = f->d_map_f32;
+    a.stats = f->d_stats;
+    a.status = f->d_status;
+    a.work = f->d_work;
+    a.abort_flag = f->d_abort;
+    const Geo &g = f->g;
+    a.near_cap = std::max(1, f->max_near);
+    a.l3x_f = (float)g.l3x;
+    a.l3x_lo = (float)(g.l3x - (double)a.l3x_f);
+    a.c0_f = (float)(0.5 - 0.5 * (double)g.n2x);
+    // close-pass radius: FP32 offsets of size up to |t| + |dyl| give a relative
+    // near-term error of 2 * 2^-24 (|t| + |dyl|) / r; below r_c it could pass
+    // 5e-7, so those rays take the hi/lo path
+    {
+        double rc = 4.0 * 5.9604644775390625e-8 * (0.5 * g.l2x + 32.0 * g.l3y) / 5e-7;
+        a.rc2 = (float)(rc * rc);
+    }
+    a.ipx_f = (float)(1.0 / g.dpx);
+    a.ipy_f = (float)(1.0 / g.dpy);
+    a.Ax_f = (float)((1.0 - g.kappa - g.gamma + g.kappa_star) / g.dpx);
+    a.rho_y = (1.0 - g.kappa + g.gamma + g.kappa_star) * g.l3y / g.dpy;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ml_abi_version(void) { return ML_ABI_VERSION; }
+
+const char *ml_last_error(void) { return g_err.c_str(); }
+
+ml_status ml_field_create(const ml_field_desc *desc, void *stream, ml_field **out)
+{
+    if (!out) return fail(ML_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    ml_status st = validate(desc);
+    if (st != ML_OK) return st;
+    ml_field *f = new (std::nothrow) ml_field();
+    if (!f) return fail(ML_ERR_OOM, "host allocation failed");
+    st = create_impl(desc, (cudaStream_t)stream, f);
+    if (st != ML_OK) {
+        std::string keep = g_err;
+        f->release();
+        delete f;
+        cudaGetLastError();
+        g_err = keep;
+        return st;
+    }
+    g_err.clear();
+    *out = f;
+    return ML_OK;
+}
+
+ml_status ml_shoot_rays(ml_field *f, uint64_t ray_begin, uint64_t ray_end, void *stream)
+{
+    if (!f) return fail(ML_ERR_INVALID_ARG, "field is NULL");
+    const Geo &g = f->g;
+    const uint64_t total = (uint64_t)g.n3x * (uint64_t)g.n3y;
+    if (ray_begin > ray_end || ray_end > total)
+        return fail(ML_ERR_INVALID_ARG, "ray range outside the lattice [0, " +
+                                            std::to_string(total) + ")");
+    cudaStream_t s = (cudaStream_t)stream;
+    ShootArgs a = make_args(f);
+    const int64_t gpb = (g.n1y + 31) / 32;
+    const int64_t l2_per_cc = std::max<int64_t>(1, std::min<int64_t>(g.l2sub, (2048 + g.n2x - 1) / g.n2x));
+    const int64_t cc_per_l1 = (g.l2sub + l2_per_cc - 1) / l2_per_cc;
+    for (uint64_t b = ray_begin; b < ray_end;) {
+        uint64_t e = std::min<uint64_t>(ray_end, b + f->max_launch_rays);
+        a.ray_begin = (int64_t)b;
+        a.ray_end = (int64_t)e;
+        if (g.precision == ML_PREC_MIXED) {
+            int64_t jb = a.ray_begin / g.n3x, je = (a.ray_end - 1) / g.n3x;
+            auto rg = [&](int64_t j) { return (j / g.n1y) * gpb + (j % g.n1y) / 32; };
+            a.groups_per_band = gpb;
+            a.rg_first = rg(jb);
+            a.n_rg = rg(je) - a.rg_first + 1;
+            a.l2_per_cc = l2_per_cc;
+            a.cc_per_l1 = cc_per_l1;
+            a.n_cc = g.N1x * cc_per_l1;
+            a.n_tasks = a.n_rg * a.n_cc;
+            ML_CK(cudaMemsetAsync(f->d_work, 0, sizeof(unsigned long long), s));
+        }
+        ML_CK(launch_shoot(a, f->num_sms, s));
+        ++f->launches;
+        b = e;
+    }
+    f->rays_asked += ray_end - ray_begin;
+    return ML_OK;
+}
+
+ml_status ml_trace_rays(ml_field *f, const int64_t *ray_idx, int64_t n, double *beta, int32_t *pix,
+                        void *stream)
+{
+    if (!f) return fail(ML_ERR_INVALID_ARG, "field is NULL");
+    if (n < 0 || (n > 0 && (!ray_idx || !beta || !pix)))
+        return fail(ML_ERR_INVALID_ARG, "bad trace arguments");
+    ShootArgs a = make_args(f);
+    ML_CK(launch_trace(a, ray_idx, n, beta, pix, (cudaStream_t)stream));
+    return ML_OK;
+}
+
+ml_status ml_magnification_map(ml_field *f, int32_t want, void *out, int32_t out_is_device,
+                               void *stream)
+{
+    if (!f || !out) return fail(ML_ERR_INVALID_ARG, "field or out is NULL");
+    if (want < ML_MAP_COUNTS_U32 || want > ML_MAP_MU_F64)
+        return fail(ML_ERR_INVALID_ARG, "unknown map kind");
+    const Geo &g = f->g;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t npix = (size_t)g.mnx * g.mny;
+    const double scale = (g.l3x * g.l3y) / (g.dpx * g.dpy);   // S_I / S_S, Eq. 12
+    if (want == ML_MAP_COUNTS_U32) {
+        if (!f->d_map_u32) return fail(ML_ERR_STATE, "a CIC field has no integer counts");
+        ML_CK(cudaMemcpyAsync(out, f->d_map_u32, npix * sizeof(uint32_t),
+                              out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        if (!out_is_device) ML_CK(cudaStreamSynchronize(s));
+        return ML_OK;
+    }
+    const size_t esz = want == ML_MAP_MU_F32 ? 4 : 8;
+    void *dst = out;
+    if (!out_is_device) ML_CK(cudaMallocAsync(&dst, npix * esz, s));
+    else if ((uintptr_t)out % 16 != 0)
+        return fail(ML_ERR_INVALID_ARG, "device output must be 16-byte aligned");
+    cudaError_t e = launch_mu(g, f->d_map_u32, f->d_map_f32, want, dst, scale, s);
+    if (e == cudaSuccess && !out_is_device)
+        e = cudaMemcpyAsync(out, dst, npix * esz, cudaMemcpyDeviceToHost, s);
+    if (!out_is_device) {
+        cudaFreeAsync(dst, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "magnification map");
+    return ML_OK;
+}
+
+ml_status ml_light_curves(ml_field *f, const double *tracks, int32_t n_tracks, int32_t n_samples,
+                          double sigma_px, float *out, int32_t out_is_device, void *stream)
+{
+    if (!f || !tracks || !out) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (n_tracks < 1 || n_samples < 1) return fail(ML_ERR_INVALID_ARG, "need >= 1 track and sample");
+    if (!(sigma_px > 0.0) || sigma_px > 16.0) return fail(ML_ERR_INVALID_ARG, "sigma_px must be in (0, 16]");
+    for (int q = 0; q < 4 * n_tracks; ++q)
+        if (!is_fin(tracks[q])) return fail(ML_ERR_INVALID_ARG, "track coordinates must be finite");
+    const Geo &g = f->g;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double scale = (g.l3x * g.l3y) / (g.dpx * g.dpy);
+    const size_t nout = (size_t)n_tracks * n_samples;
+    double *d_tr = nullptr;
+    float *dst = out;
+    ML_CK(cudaMallocAsync((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
+    cudaError_t e = cudaMemcpyAsync(d_tr, tracks, sizeof(double) * 4 * n_tracks,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !out_is_device) e = cudaMallocAsync((void **)&dst, nout * sizeof(float), s);
+    if (e == cudaSuccess)
+        e = launch_light_curves(g, f->d_map_u32, f->d_map_f32, scale, d_tr, n_tracks, n_samples,
+                                sigma_px, dst, s);
+    if (e == cudaSuccess && !out_is_device)
+        e = cudaMemcpyAsync(out, dst, nout * sizeof(float), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d_tr, s);
+    if (!out_is_device && dst != out) cudaFreeAsync(dst, s);
+    if (e == cudaSuccess && !out_is_device) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "light curves");
+    return ML_OK;
+}
+
+ml_status ml_field_clear(ml_field *f, void *stream)
+{
+    if (!f) return fail(ML_ERR_INVALID_ARG, "field is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t npix = (size_t)f->g.mnx * f->g.mny;
+    if (f->d_map_u32) ML_CK(cudaMemsetAsync(f->d_map_u32, 0, npix * sizeof(uint32_t), s));
+    if (f->d_map_f32) ML_CK(cudaMemsetAsync(f->d_map_f32, 0, npix * sizeof(float), s));
+    ML_CK(cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s));
+    ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
+    f->rays_asked = 0;
+    f->launches = 0;
+    return ML_OK;
+}
+
+ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream)
+{
+    if (!f || !out) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long st[8];
+    unsigned flags = 0;
+    ML_CK(cudaMemcpyAsync(st, f->d_stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+    ML_CK(cudaMemcpyAsync(&flags, f->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    ML_CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < 8; ++q) out[q] = st[q];
+    out[ML_STAT_LAUNCHES] = f->launches;
+    out[ML_STAT_FLAGS] = flags;
+    out[ML_STAT_RAYS_ASKED] = f->rays_asked;
+    if (flags & 1u) return fail(ML_ERR_OVERFLOW, "a uint32 pixel count wrapped");
+    if (flags & 2u) return fail(ML_ERR_ABORTED, "shooting was aborted");
+    return ML_OK;
+}
+
+ml_status ml_field_info(const ml_field *f, ml_field_params *out)
+{
+    if (!f || !out) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    const Geo &g = f->g;
+    memset(out, 0, sizeof(*out));
+    out->ray_x0 = g.rx0; out->ray_y0 = g.ry0; out->ray_x1 = g.rx1; out->ray_y1 = g.ry1;
+    out->l3x = g.l3x; out->l3y = g.l3y;
+    out->n_rays_x = g.n3x; out->n_rays_y = g.n3y;
+    out->map_x0 = g.mx0; out->map_y0 = g.my0; out->dpx = g.dpx; out->dpy = g.dpy;
+    out->map_nx = g.mnx; out->map_ny = g.mny;
+    out->n_star_in = g.n_star_in; out->l0 = g.l0;
+    out->n1x = g.n1x; out->n1y = g.n1y; out->n2x = g.n2x; out->n2y = g.n2y;
+    out->N1x = g.N1x; out->N1y = g.N1y; out->N2x = g.N2x; out->N2y = g.N2y;
+    out->taylor_p = g.p; out->l2_sub = g.l2sub;
+    out->precision = g.precision; out->deposit = g.deposit;
+    out->max_near = f->max_near;
+    out->build = f->build_used;
+    out->far_bound = f->far_bound;
+    out->mu_per_count = (g.l3x * g.l3y) / (g.dpx * g.dpy);
+    return ML_OK;
+}
+
+ml_status ml_field_abort(ml_field *f, int32_t on)
+{
+    if (!f) return fail(ML_ERR_INVALID_ARG, "field is NULL");
+    *(volatile int *)f->h_abort = on ? 1 : 0;
+    return ML_OK;
+}
+
+ml_status ml_field_destroy(ml_field *f)
+{
+    if (!f) return ML_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(f->device);
+    f->release();
+    cudaSetDevice(cur);
+    delete f;
+    return ML_OK;
+}
+
+}  // extern "C"

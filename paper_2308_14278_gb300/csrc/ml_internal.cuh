@@ -1,0 +1,248 @@
+// Internal declarations of the GB300 microlensing library: derived geometry,
+// device-buffer bundles, launch wrappers and the per-ray arithmetic that the
+// shooting and tracing kernels share.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ml.h"
+
+namespace ml {
+
+constexpr int PMAX = 16;                  // highest Taylor order supported
+constexpr uint32_t PIX_OUT = 0xFFFFFFFFu;   // run-length code: outside the map
+constexpr uint32_t PIX_DROP = 0xFFFFFFFEu;  // run-length code: ray hit a lens
+constexpr int WARPS_PER_CTA = 8;
+
+// Parameters derived from an ml_field_desc (§3.1 and §3.2).
+struct Geo {
+    double kappa, gamma, kappa_star;
+    double sheet_cx, sheet_cy, sheet_r;
+    double rx0, ry0, rx1, ry1;      // ray rectangle
+    double l3x, l3y;                // level-3 pixel (ray spacing)
+    int64_t n3x, n3y;               // lattice size
+    double mx0, my0, dpx, dpy;      // map origin and pixel size
+    int32_t mnx, mny;
+    int64_t n_star_in;
+    double l0;
+    int32_t l2sub, p;
+    int64_t n1x, n1y, n2x, n2y;     // rays per level-1 / level-2 cell side
+    int64_t N1x, N1y, N2x, N2y;     // cells across the lattice
+    double l1x, l1y, l2x, l2y;      // = n1 * l3, n2 * l3
+    int64_t NEx, NEy;               // level-1 grid with one ring around it
+    int32_t precision, deposit;
+};
+
+// Lenses sorted by extended level-1 cell (a ring of cells around the lattice
+// included); lenses outside the ring follow in one last bucket.
+struct LensTable {
+    const double *x, *y, *m;        // sorted, FP64
+    const int32_t *cell;            // extended cell id of each sorted lens, NE for outside
+    const int32_t *start;           // NE + 2 offsets: bucket b holds [start[b], start[b+1])
+    int64_t n;
+};
+
+// Per-node record of the mixed-precision path, stride 16 + 8p bytes:
+//   double Sy;  int32 bx;  float fx;  float2 c[p]
+// (Sy, bx + fx) is the smooth part of beta at the node in map pixel units
+// (macro model, sheet and far-field c_0); c[n-1] is the FP32 far-field
+// Taylor coefficient c_n, n = 1..p, in theta_E units.
+__host__ __device__ inline size_t node_stride(int p) { return 16 + 8 * (size_t)p; }
+
+// Everything a shooting or tracing kernel needs.
+struct ShootArgs {
+    Geo g;
+    LensTable L;
+    const double *coef64;           // (p+1) complex FP64 per node (near/far FP64 mode)
+    const unsigned char *nodes;     // node records (mixed mode)
+    uint32_t *map_u32;
+    float *map_f32;
+    unsigned long long *stats;      // ML_STAT_* counters on the device
+    unsigned int *status;           // bit 0 overflow, bit 1 aborted
+    unsigned long long *work;       // persistent-kernel task counter
+    const volatile int *abort_flag; // mapped host flag
+    // ray range of this launch
+    int64_t ray_begin, ray_end;
+    // task decomposition of the mixed kernel
+    int64_t rg_first, n_rg, groups_per_band, n_cc, cc_per_l1, l2_per_cc;
+    int64_t n_tasks;
+    int near_cap;                   // float4 slots of shared memory per warp
+    // float constants of the mixed kernel
+    float l3x_f, l3x_lo, c0_f, ipx_f, ipy_f, Ax_f;  // Ax_f = (1-kappa-gamma+kappa_*)/dpx
+    float rc2;                      // close-pass radius^2 of near_sum_f32
+    double rho_y;                   // (1-kappa+gamma+kappa_*) * l3y / dpy
+};
+
+// ---- launch wrappers (defined in the .cu files) ----
+cudaError_t launch_lens_cells(const Geo &g, const double *x, const double *y, int64_t n,
+                              int32_t *cell, int32_t *count, cudaStream_t s);
+cudaError_t launch_scan(const int32_t *count, int32_t *start, int64_t nb, cudaStream_t s);
+cudaError_t launch_scatter(const double *x, const double *y, const double *m,
+                           const int32_t *cell, int64_t n, const int32_t *start, int64_t nb,
+                           int32_t *cursor, double *sx, double *sy, double *sm, int32_t *scell,
+                           cudaStream_t s);
+cudaError_t launch_p_bound(const Geo &g, const LensTable &L, double *bound, cudaStream_t s);
+cudaError_t launch_coeffs_direct(const Geo &g, const LensTable &L, double *coef64, cudaStream_t s);
+cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64, double *scratch,
+                               size_t scratch_doubles, cudaStream_t s);
+size_t hier_scratch_doubles(const Geo &g);
+cudaError_t launch_node_finalize(const Geo &g, const double *coef64, unsigned char *nodes,
+                                 cudaStream_t s);
+cudaError_t launch_shoot(const ShootArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_trace(const ShootArgs &a, const int64_t *idx, int64_t n, double *beta,
+                         int32_t *pix, cudaStream_t s);
+cudaError_t launch_mu(const Geo &g, const uint32_t *cu, const float *cf, int want, void *out,
+                      double scale, cudaStream_t s);
+cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *cf, double scale,
+                                const double *tracks, int n_tracks, int n_samples,
+                                double sigma_px, float *out, cudaStream_t s);
+int mixed_p_supported(int p);     // the Taylor order the mixed kernel will use for p
+
+// ---- shared device arithmetic ---------------------------------------------
+
+#if defined(__CUDACC__)
+
+// Near-lens records: rec(k) = (x_k - x_node, y_k - y_ref, m_k, -) rounded to
+// FP32, lo(k) = the rounding remainders of the two offsets.  Deflection of the near lenses (the directly summed part of
+// Eq. 9) in FP32 on these node-relative coordinates:
+//   dx = t - lx,  dy = dyl - ly,  t = u * l3x (u a half-integer lattice offset).
+// The FP32 rounding of the offsets costs a relative error of about
+// 2^-23 (|t| + |dyl|) / r for a ray at distance r from a lens.  Rays that pass
+// closer than r_c (sqrt(rc2), where that error would exceed 1e-6) redo the
+// sum with the offsets carried as hi + lo float pairs, exact to ~2^-46.
+template <class Near>
+__device__ __forceinline__ void near_sum_f32(const Near &nl, int nn, float u, float t, float dyl,
+                                             float dyl_lo, float l3x_hi, float l3x_lo, float rc2,
+                                             float &ax, float &ay)
+{
+    float sx = 0.f, sy = 0.f, rmin = 3.0e38f;
+    for (int k = 0; k < nn; ++k) {
+        float4 L = nl.rec(k);
+        float dx = __fsub_rn(t, L.x);
+        float dy = __fsub_rn(dyl, L.y);
+        float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        rmin = fminf(rmin, r2);
+        float s = __fdividef(L.z, r2);
+        sx = __fmaf_rn(dx, s, sx);
+        sy = __fmaf_rn(dy, s, sy);
+    }
+    if (rmin < rc2) {
+        float t_lo = __fmaf_rn(u, l3x_lo, __fmaf_rn(u, l3x_hi, -t));
+        sx = 0.f;
+        sy = 0.f;
+        for (int k = 0; k < nn; ++k) {
+            float4 L = nl.rec(k);
+            float2 R = nl.lo(k);
+            float dx = __fadd_rn(__fsub_rn(t, L.x), __fsub_rn(t_lo, R.x));
+            float dy = __fadd_rn(__fsub_rn(dyl, L.y), __fsub_rn(dyl_lo, R.y));
+            float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+            float s = __fdividef(L.z, r2);
+            sx = __fmaf_rn(dx, s, sx);
+            sy = __fmaf_rn(dy, s, sy);
+        }
+    }
+    ax = sx;
+    ay = sy;
+}
+
+// Near records staged in shared memory by the shooting kernels.
+struct SmemNear {
+    const float4 *near;
+    const float2 *lo_;
+    __device__ __forceinline__ float4 rec(int k) const { return near[k]; }
+    __device__ __forceinline__ float2 lo(int k) const { return lo_[k]; }
+};
+
+// Per-ray-row polynomial of the smooth part of beta (map pixel units) in the
+// node-relative x offset t:  X(t) = sum X[m] t^m,  Y(t) = sum Y[m] t^m, with
+// integer bases bx, by (pixel = base + floor(value)).
+template <int P>
+struct RowPoly {
+    float X[P + 1], Y[P + 1];
+    int bx, by;
+};
+
+// Build the row polynomial of one node for the ray row at node-relative y
+// offset s = q * l3y (q a half-integer):  the far series
+// F(t + i s) = sum_{n=1..P} c_n (t + i s)^n is re-expanded in t by a Taylor
+// shift (repeated synthetic division), then beta_x = Sx + Ax t - Re F / dpx
+// and beta_y = Sy + Ay s + Im F / dpy.
+template <int P>
+__device__ __forceinline__ void row_setup(const unsigned char *rec, float q, const ShootArgs &a,
+                                          RowPoly<P> &rp)
+{
+    const double Sy = *reinterpret_cast<const double *>(rec);
+    const int bx0 = *reinterpret_cast<const int *>(rec + 8);
+    const float fx = *reinterpret_cast<const float *>(rec + 12);
+    const float2 *c = reinterpret_cast<const float2 *>(rec + 16);
+    const float s = __fmul_rn(q, (float)a.g.l3y);
+    float br[P + 1], bi[P + 1];
+    br[0] = 0.f;
+    bi[0] = 0.f;
+#pragma unroll
+    for (int n = 1; n <= P; ++n) {
+        float2 cn = c[n - 1];
+        br[n] = cn.x;
+        bi[n] = cn.y;
+    }
+    // b_n += (i s) b_{n+1}:  (i s)(u + i v) = -s v + i s u
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
+        for (int n = P - 1; n >= k; --n) {
+            float nr = __fmaf_rn(-s, bi[n + 1], br[n]);
+            float ni = __fmaf_rn(s, br[n + 1], bi[n]);
+            br[n] = nr;
+            bi[n] = ni;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m <= P; ++m) {
+        rp.X[m] = __fmul_rn(-br[m], a.ipx_f);
+        rp.Y[m] = __fmul_rn(bi[m], a.ipy_f);
+    }
+    rp.X[1] = __fadd_rn(rp.X[1], a.Ax_f);
+    // x base: fx in [0, 1) plus the far-field offset of this row
+    float x0 = __fadd_rn(fx, rp.X[0]);
+    float kx = floorf(x0);
+    rp.X[0] = __fsub_rn(x0, kx);
+    rp.bx = bx0 + (int)kx;
+    // y base in FP64: Sy + q * rho_y, then the FP32 far-field offset
+    double y0 = fma((double)q, a.rho_y, Sy);
+    double ky = floor(y0);
+    ky = fmin(fmax(ky, -16777216.0), 16777216.0);
+    float y0f = __fadd_rn((float)(y0 - ky), rp.Y[0]);
+    float ky2 = floorf(y0f);
+    rp.Y[0] = __fsub_rn(y0f, ky2);
+    rp.by = (int)ky + (int)ky2;
+}
+
+template <int P>
+__device__ __forceinline__ void row_eval(const RowPoly<P> &rp, float t, float &X, float &Y)
+{
+    float x = rp.X[P], y = rp.Y[P];
+#pragma unroll
+    for (int m = P - 1; m >= 0; --m) {
+        x = __fmaf_rn(x, t, rp.X[m]);
+        y = __fmaf_rn(y, t, rp.Y[m]);
+    }
+    X = x;
+    Y = y;
+}
+
+// Nearest-grid-point pixel of the ray (Eq. 12 binning) or PIX_OUT / PIX_DROP.
+__device__ __forceinline__ uint32_t classify(float X, float Y, float ax, int bx, int by,
+                                             int mnx, int mny)
+{
+    int ix = __float2int_rd(X);
+    int iy = __float2int_rd(Y);
+    unsigned gx = (unsigned)bx + (unsigned)ix;
+    unsigned gy = (unsigned)by + (unsigned)iy;
+    uint32_t pix = (gx < (unsigned)mnx && gy < (unsigned)mny) ? gy * (unsigned)mnx + gx : PIX_OUT;
+    return (ax != ax) ? PIX_DROP : pix;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace ml

@@ -1,0 +1,164 @@
+// Map kernels: magnification from counts (Eq. 12) and light curves of a
+// Gaussian source along straight tracks (§4.1, Fig. 3).
+#include "ml_internal.cuh"
+
+#include <math.h>
+
+namespace ml {
+
+// mu_ij = N_ij * S_I / S_S.  Vectorised: four pixels per thread per step,
+// uint4 loads and float4 / double2 stores, grid-stride over the map.
+__global__ void k_mu_u32_f32(const uint4 *__restrict__ in, float4 *__restrict__ out, int64_t n4,
+                             float scale)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint4 v = __ldcs(in + i);
+        __stcs(out + i, make_float4((float)v.x * scale, (float)v.y * scale, (float)v.z * scale,
+                                    (float)v.w * scale));
+    }
+}
+
+__global__ void k_mu_u32_f64(const uint4 *__restrict__ in, double2 *__restrict__ out, int64_t n4,
+                             double scale)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint4 v = __ldcs(in + i);
+        __stcs(out + 2 * i, make_double2((double)v.x * scale, (double)v.y * scale));
+        __stcs(out + 2 * i + 1, make_double2((double)v.z * scale, (double)v.w * scale));
+    }
+}
+
+__global__ void k_mu_f32(const float4 *__restrict__ in, float4 *__restrict__ out, int64_t n4,
+                         float scale)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = __ldcs(in + i);
+        __stcs(out + i, make_float4(v.x * scale, v.y * scale, v.z * scale, v.w * scale));
+    }
+}
+
+__global__ void k_mu_f32_f64(const float4 *__restrict__ in, double2 *__restrict__ out, int64_t n4,
+                             double scale)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = __ldcs(in + i);
+        __stcs(out + 2 * i, make_double2((double)v.x * scale, (double)v.y * scale));
+        __stcs(out + 2 * i + 1, make_double2((double)v.z * scale, (double)v.w * scale));
+    }
+}
+
+// Scalar tail (maps whose pixel count is not a multiple of 4).
+__global__ void k_mu_tail(const uint32_t *cu, const float *cf, int want, void *out, int64_t from,
+                          int64_t n, double scale)
+{
+    int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = cu ? (double)cu[i] : (double)cf[i];
+    if (want == ML_MAP_MU_F32) reinterpret_cast<float *>(out)[i] = (float)(v * scale);
+    else reinterpret_cast<double *>(out)[i] = v * scale;
+}
+
+cudaError_t launch_mu(const Geo &g, const uint32_t *cu, const float *cf, int want, void *out,
+                      double scale, cudaStream_t s)
+{
+    int64_t n = (int64_t)g.mnx * g.mny, n4 = n / 4;
+    int64_t blocks = (n4 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    if (n4 > 0) {
+        if (cu && want == ML_MAP_MU_F32)
+            k_mu_u32_f32<<<(unsigned)blocks, 256, 0, s>>>((const uint4 *)cu, (float4 *)out, n4,
+                                                          (float)scale);
+        else if (cu)
+            k_mu_u32_f64<<<(unsigned)blocks, 256, 0, s>>>((const uint4 *)cu, (double2 *)out, n4,
+                                                          scale);
+        else if (want == ML_MAP_MU_F32)
+            k_mu_f32<<<(unsigned)blocks, 256, 0, s>>>((const float4 *)cf, (float4 *)out, n4,
+                                                      (float)scale);
+        else
+            k_mu_f32_f64<<<(unsigned)blocks, 256, 0, s>>>((const float4 *)cf, (double2 *)out, n4,
+                                                          scale);
+    }
+    if (n > 4 * n4)
+        k_mu_tail<<<1, 32, 0, s>>>(cu, cf, want, out, 4 * n4, n, scale);
+    return cudaGetLastError();
+}
+
+// Light curves.  For every sample: bilinear interpolation between the four
+// pixel centres around the point, each value being the map convolved with
+// the separable normalised Gaussian taps (zero outside the map).  Only the
+// pixels the samples need are convolved.  One warp per sample group; taps
+// in shared memory.
+__global__ void k_light_curves(Geo g, const uint32_t *__restrict__ cu, const float *__restrict__ cf,
+                               double scale, const double *__restrict__ tracks, int n_tracks,
+                               int n_samples, int h, const float *__restrict__ taps_g,
+                               float *__restrict__ out)
+{
+    __shared__ float taps[129];
+    for (int t = threadIdx.x; t <= 2 * h; t += blockDim.x) taps[t] = taps_g[t];
+    __syncthreads();
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n_tracks * n_samples) return;
+    int tr = (int)(q / n_samples), k = (int)(q % n_samples);
+    const double *T = tracks + 4 * tr;
+    double t = n_samples > 1 ? (double)k / (double)(n_samples - 1) : 0.0;
+    double u = T[0] + t * (T[2] - T[0]) - 0.5;
+    double v = T[1] + t * (T[3] - T[1]) - 0.5;
+    double fu = floor(u), fv = floor(v);
+    double wx = u - fu, wy = v - fv;
+    int i0 = (int)fu, j0 = (int)fv;
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        int pi = i0 + (c & 1), pj = j0 + (c >> 1);
+        double wc = ((c & 1) ? wx : 1.0 - wx) * ((c >> 1) ? wy : 1.0 - wy);
+        if (pi < 0 || pi >= g.mnx || pj < 0 || pj >= g.mny || wc == 0.0) continue;
+        double conv = 0.0;
+        for (int dy = -h; dy <= h; ++dy) {
+            int yy = pj + dy;
+            if (yy < 0 || yy >= g.mny) continue;
+            double row = 0.0;
+            const int64_t base = (int64_t)yy * g.mnx;
+            for (int dx = -h; dx <= h; ++dx) {
+                int xx = pi + dx;
+                if (xx < 0 || xx >= g.mnx) continue;
+                double val = cu ? (double)cu[base + xx] : (double)cf[base + xx];
+                row += (double)taps[dx + h] * val;
+            }
+            conv += (double)taps[dy + h] * row;
+        }
+        acc += wc * conv;
+    }
+    out[q] = (float)(acc * scale);
+}
+
+cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *cf, double scale,
+                                const double *tracks, int n_tracks, int n_samples,
+                                double sigma_px, float *out, cudaStream_t s)
+{
+    int h = (int)floor(4.0 * sigma_px);
+    if (h > 64) return cudaErrorInvalidValue;
+    float taps[129];
+    double sum = 0.0, w[129];
+    for (int t = -h; t <= h; ++t) {
+        w[t + h] = exp(-0.5 * ((double)t / sigma_px) * ((double)t / sigma_px));
+        sum += w[t + h];
+    }
+    for (int t = 0; t <= 2 * h; ++t) taps[t] = (float)(w[t] / sum);
+    float *d_taps = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_taps, sizeof(float) * (2 * h + 1), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_taps, taps, sizeof(float) * (2 * h + 1), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaFreeAsync(d_taps, s); return e; }
+    int64_t n = (int64_t)n_tracks * n_samples;
+    k_light_curves<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, cu, cf, scale, tracks, n_tracks,
+                                                               n_samples, h, d_taps, out);
+    e = cudaGetLastError();
+    cudaFreeAsync(d_taps, s);
+    return e;
+}
+
+}  // namespace ml

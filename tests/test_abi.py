@@ -1,0 +1,111 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/ml.h declares, and the ctypes mirrors of its structs have
+the C layout."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import paper_2308_14278_gb300 as ml
+from paper_2308_14278_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ml.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ml_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return build.build_library()
+
+
+def test_header_and_binding_agree():
+    assert sorted(ml.EXPORTS) == declared_functions()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (ml_[a-z0-9_]+)$", out, flags=re.M))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    lib = C.CDLL(libpath)
+    for f in declared_functions():
+        assert hasattr(lib, f)
+
+
+def test_abi_version_and_error_string(libpath):
+    lib = ml.load(libpath)
+    assert lib.ml_abi_version() == ml.ABI_VERSION
+    # a NULL descriptor is rejected before any CUDA call
+    h = C.c_void_p()
+    st = lib.ml_field_create(None, None, C.byref(h))
+    assert st == 1 and h.value is None
+    assert b"desc is NULL" in lib.ml_last_error()
+    d = ml.FieldDesc()
+    d.abi_version = 99
+    assert lib.ml_field_create(C.byref(d), None, C.byref(h)) == 1
+    assert b"abi_version" in lib.ml_last_error()
+    assert lib.ml_field_destroy(None) == 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(map_nx=0), dict(map_x1=-2.0), dict(n_lens=5), dict(precision=7), dict(deposit=3),
+    dict(taylor_p=17), dict(kappa_star=-1.0), dict(sheet_radius=-1.0), dict(l2_sub=-1),
+])
+def test_descriptor_validation_without_gpu(libpath, bad):
+    lib = ml.load(libpath)
+    d = ml.FieldDesc()
+    d.abi_version = ml.ABI_VERSION
+    d.map_x0, d.map_y0, d.map_x1, d.map_y1 = -1, -1, 1, 1
+    d.map_nx = d.map_ny = 8
+    d.n_av = 10
+    for k, v in bad.items():
+        setattr(d, k, v)
+    h = C.c_void_p()
+    assert lib.ml_field_create(C.byref(d), None, C.byref(h)) == 1   # ML_ERR_INVALID_ARG
+    assert h.value is None
+
+
+_LAYOUT_C = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "ml.h"
+#define P(T, f) printf(#T " " #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("ml_field_desc size %zu\n", sizeof(ml_field_desc));
+  printf("ml_field_params size %zu\n", sizeof(ml_field_params));
+  %FIELDS%
+  return 0;
+}
+"""
+
+
+def test_struct_layout_matches_header(tmp_path):
+    lines = []
+    for T, S in (("ml_field_desc", ml.FieldDesc), ("ml_field_params", ml.FieldParams)):
+        for name, _ in S._fields_:
+            lines.append(f"P({T}, {name});")
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C.replace("%FIELDS%", "\n  ".join(lines)))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                               check=True).stdout.splitlines():
+        T, f, v = line.split()
+        got[(T, f)] = int(v)
+    assert got[("ml_field_desc", "size")] == C.sizeof(ml.FieldDesc)
+    assert got[("ml_field_params", "size")] == C.sizeof(ml.FieldParams)
+    for T, S in (("ml_field_desc", ml.FieldDesc), ("ml_field_params", ml.FieldParams)):
+        for name, _ in S._fields_:
+            assert got[(T, name)] == getattr(S, name).offset, (T, name)
