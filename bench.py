@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--shoot-rays", type=float, default=0,
+                    help="profiling: shoot only this many rays (a centred slice of the lattice) "
+                         "per step; the default shoots them all")
     return ap.parse_args()
 
 
@@ -157,7 +160,10 @@ def run_ours(args, rank, world, local):
         h = ml.ml_field_create(make_desc(True), stream)
         info = ml.ml_field_info(h)
         if e: e[1].record(stream)
-        ml.ml_shoot_rays(h, 0, info["n_rays_x"] * info["n_rays_y"], stream)
+        n_all = info["n_rays_x"] * info["n_rays_y"]
+        n_shoot = int(min(args.shoot_rays, n_all)) if args.shoot_rays else n_all
+        r0 = (n_all - n_shoot) // 2
+        ml.ml_shoot_rays(h, r0, r0 + n_shoot, stream)
         if e: e[2].record(stream)
         ml.ml_magnification_map(h, ml.MAP_MU_F32, mu_out, stream)
         if e: e[3].record(stream)
@@ -190,6 +196,8 @@ def run_ours(args, rank, world, local):
     step_ms = float(per.sum(axis=1).mean())
     info, stats = info_holder["info"], info_holder["stats"]
     n_rays = info["n_rays_x"] * info["n_rays_y"]
+    if args.shoot_rays:
+        n_rays = int(min(args.shoot_rays, n_rays))
     t_local = step_ms
     if dist:
         t = torch.tensor([t_local], device=dev, dtype=torch.float64)
@@ -226,6 +234,7 @@ def run_ours(args, rank, world, local):
                      "kernel": "k_shoot_mixed", "flops_per_launch_survey_convention":
                          survey_flops / max(1, stats["launches"]),
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+        "shoot_rays_override": bool(args.shoot_rays),
         "rays_check": {"in": stats["rays_in"], "out": stats["rays_out"],
                        "dropped": stats["rays_dropped"], "total": n_rays,
                        "conserved": stats["rays_in"] + stats["rays_out"] + stats["rays_dropped"] == n_rays},

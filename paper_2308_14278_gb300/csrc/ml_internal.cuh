@@ -109,41 +109,83 @@ int mixed_p_supported(int p);     // the Taylor order the mixed kernel will use 
 //   dx = t - lx,  dy = dyl - ly,  t = u * l3x (u a half-integer lattice offset).
 // The FP32 rounding of the offsets costs a relative error of about
 // 2^-23 (|t| + |dyl|) / r for a ray at distance r from a lens.  Rays that pass
-// closer than r_c (sqrt(rc2), where that error would exceed 1e-6) redo the
-// sum with the offsets carried as hi + lo float pairs, exact to ~2^-46.
+// closer than r_c (sqrt(rc2), where that error could exceed 5e-7) redo the
+// sum with the offsets carried as hi + lo float pairs (near_sum_hilo).
 template <class Near>
-__device__ __forceinline__ void near_sum_f32(const Near &nl, int nn, float u, float t, float dyl,
-                                             float dyl_lo, float l3x_hi, float l3x_lo, float rc2,
-                                             float &ax, float &ay)
+__device__ __forceinline__ void near_sum_f32(const Near &nl, int nn, float t, float dyl,
+                                             float &ax, float &ay, float &rmin)
 {
-    float sx = 0.f, sy = 0.f, rmin = 3.0e38f;
+    float sx = 0.f, sy = 0.f, mn = 3.0e38f;
     for (int k = 0; k < nn; ++k) {
         float4 L = nl.rec(k);
-        float dx = __fsub_rn(t, L.x);
         float dy = __fsub_rn(dyl, L.y);
-        float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-        rmin = fminf(rmin, r2);
+        float dy2 = __fmul_rn(dy, dy);
+        float dx = __fsub_rn(t, L.x);
+        float r2 = __fmaf_rn(dx, dx, dy2);
+        mn = fminf(mn, r2);
         float s = __fdividef(L.z, r2);
         sx = __fmaf_rn(dx, s, sx);
         sy = __fmaf_rn(dy, s, sy);
     }
-    if (rmin < rc2) {
-        float t_lo = __fmaf_rn(u, l3x_lo, __fmaf_rn(u, l3x_hi, -t));
-        sx = 0.f;
-        sy = 0.f;
-        for (int k = 0; k < nn; ++k) {
-            float4 L = nl.rec(k);
-            float2 R = nl.lo(k);
-            float dx = __fadd_rn(__fsub_rn(t, L.x), __fsub_rn(t_lo, R.x));
-            float dy = __fadd_rn(__fsub_rn(dyl, L.y), __fsub_rn(dyl_lo, R.y));
-            float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-            float s = __fdividef(L.z, r2);
-            sx = __fmaf_rn(dx, s, sx);
-            sy = __fmaf_rn(dy, s, sy);
-        }
+    ax = sx;
+    ay = sy;
+    rmin = mn;
+}
+
+// The same for two rays of one row (t0, t1), sharing each lens record and
+// dy; per ray the operations are exactly those of near_sum_f32.
+template <class Near>
+__device__ __forceinline__ void near_sum2_f32(const Near &nl, int nn, float t0, float t1, float dyl,
+                                              float &ax0, float &ay0, float &rmin0,
+                                              float &ax1, float &ay1, float &rmin1)
+{
+    float sx0 = 0.f, sy0 = 0.f, mn0 = 3.0e38f, sx1 = 0.f, sy1 = 0.f, mn1 = 3.0e38f;
+    for (int k = 0; k < nn; ++k) {
+        float4 L = nl.rec(k);
+        float dy = __fsub_rn(dyl, L.y);
+        float dy2 = __fmul_rn(dy, dy);
+        float dx0 = __fsub_rn(t0, L.x);
+        float dx1 = __fsub_rn(t1, L.x);
+        float r20 = __fmaf_rn(dx0, dx0, dy2);
+        float r21 = __fmaf_rn(dx1, dx1, dy2);
+        mn0 = fminf(mn0, r20);
+        mn1 = fminf(mn1, r21);
+        float s0 = __fdividef(L.z, r20);
+        float s1 = __fdividef(L.z, r21);
+        sx0 = __fmaf_rn(dx0, s0, sx0);
+        sy0 = __fmaf_rn(dy, s0, sy0);
+        sx1 = __fmaf_rn(dx1, s1, sx1);
+        sy1 = __fmaf_rn(dy, s1, sy1);
+    }
+    ax0 = sx0; ay0 = sy0; rmin0 = mn0;
+    ax1 = sx1; ay1 = sy1; rmin1 = mn1;
+}
+
+// Close-pass path: the near sum with the offsets carried as hi + lo float
+// pairs (t = u * (l3x_hi + l3x_lo) split by an exact FMA remainder).  Returns
+// false when the ray coincides with a lens even at this precision.
+template <class Near>
+__device__ __forceinline__ bool near_sum_hilo(const Near &nl, int nn, float u, float t, float dyl,
+                                           float dyl_lo, float l3x_hi, float l3x_lo,
+                                           float &ax, float &ay)
+{
+    float t_lo = __fmaf_rn(u, l3x_lo, __fmaf_rn(u, l3x_hi, -t));
+    float sx = 0.f, sy = 0.f;
+    bool hit = false;
+    for (int k = 0; k < nn; ++k) {
+        float4 L = nl.rec(k);
+        float2 R = nl.lo(k);
+        float dx = __fadd_rn(__fsub_rn(t, L.x), __fsub_rn(t_lo, R.x));
+        float dy = __fadd_rn(__fsub_rn(dyl, L.y), __fsub_rn(dyl_lo, R.y));
+        float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        hit |= (r2 == 0.f);
+        float s = __fdividef(L.z, r2);
+        sx = __fmaf_rn(dx, s, sx);
+        sy = __fmaf_rn(dy, s, sy);
     }
     ax = sx;
     ay = sy;
+    return !hit;
 }
 
 // Near records staged in shared memory by the shooting kernels.
@@ -231,16 +273,32 @@ __device__ __forceinline__ void row_eval(const RowPoly<P> &rp, float t, float &X
     Y = y;
 }
 
-// Nearest-grid-point pixel of the ray (Eq. 12 binning) or PIX_OUT / PIX_DROP.
-__device__ __forceinline__ uint32_t classify(float X, float Y, float ax, int bx, int by,
-                                             int mnx, int mny)
+// floor(X) as an int using FP32 adds only.  On this GPU float-to-int
+// conversions issue to the narrow FP64 pipe, which a per-ray conversion
+// saturates.  For |X| < 2^22 the sum X + 1.5 * 2^23 rounded toward -inf is
+// exactly 1.5 * 2^23 + floor(X) (its ulp is 1), and its bit pattern minus
+// that of 1.5 * 2^23 is floor(X).  Larger |X| (and +-inf, NaN) give results
+// of magnitude >= 2^22 with the sign of X: pixels far outside any map.
+__device__ __forceinline__ int floor_to_int(float X)
 {
-    int ix = __float2int_rd(X);
-    int iy = __float2int_rd(Y);
-    unsigned gx = (unsigned)bx + (unsigned)ix;
-    unsigned gy = (unsigned)by + (unsigned)iy;
-    uint32_t pix = (gx < (unsigned)mnx && gy < (unsigned)mny) ? gy * (unsigned)mnx + gx : PIX_OUT;
-    return (ax != ax) ? PIX_DROP : pix;
+    return __float_as_int(__fadd_rd(X, 12582912.0f)) - 0x4B400000;
+}
+
+// floor(X) both as an int and as a float (exact for |X| < 2^22).
+__device__ __forceinline__ int floor_both(float X, float &fl)
+{
+    float s = __fadd_rd(X, 12582912.0f);
+    fl = __fsub_rn(s, 12582912.0f);
+    return __float_as_int(s) - 0x4B400000;
+}
+
+// Nearest-grid-point pixel coordinates of the ray (Eq. 12 binning), before
+// the bounds check; wrapping 32-bit arithmetic keeps far values out of
+// [0, mnx) x [0, mny).
+__device__ __forceinline__ void pixel_xy(float X, float Y, int bx, int by, int &gx, int &gy)
+{
+    gx = (int)((unsigned)bx + (unsigned)floor_to_int(X));
+    gy = (int)((unsigned)by + (unsigned)floor_to_int(Y));
 }
 
 #endif  // __CUDACC__

@@ -16,6 +16,11 @@
 
 #include <math.h>
 
+// CTAs per SM the mixed kernels are compiled for (register budget).
+#ifndef ML_MIN_BLOCKS
+#define ML_MIN_BLOCKS 3
+#endif
+
 namespace ml {
 
 // ---- helpers shared by the FP64 modes ---------------------------------------
@@ -213,6 +218,369 @@ __device__ __forceinline__ NearRuns near_runs(const ShootArgs &a, int64_t c1x, i
     return nr;
 }
 
+// Per-lane run-length state of the NGP deposit: consecutive rays of a lane's
+// walk usually land in the same pixel (the macro map compresses x), so counts
+// are merged and added with one atomic when the pixel changes.  The atomic's
+// old value is checked for wrap-around at the next flush, off the critical path.
+struct RunState {
+    int cx, cy;
+    unsigned cnt, pold, pcnt, ovf;
+    unsigned in, out;
+};
+
+__device__ __forceinline__ void run_flush(RunState &rs, uint32_t *map, int mnx, int mny)
+{
+    if (rs.cnt == 0) return;
+    if ((unsigned)rs.cx < (unsigned)mnx && (unsigned)rs.cy < (unsigned)mny) {
+        rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
+        rs.pold = atomicAdd(map + (size_t)rs.cy * (unsigned)mnx + (unsigned)rs.cx, rs.cnt);
+        rs.pcnt = rs.cnt;
+        rs.in += rs.cnt;
+    } else {
+        rs.out += rs.cnt;
+    }
+}
+
+__device__ __forceinline__ void run_add(RunState &rs, int gx, int gy, uint32_t *map, int mnx, int mny)
+{
+    if (gx != rs.cx || gy != rs.cy) {
+        run_flush(rs, map, mnx, mny);
+        rs.cx = gx;
+        rs.cy = gy;
+        rs.cnt = 0;
+    }
+    ++rs.cnt;
+}
+
+// Everything of one ray after its near sum: subtract it (pixel units), take
+// the close-pass path if needed, return the pixel coordinates.  A ray that
+// hits a lens exactly is sent to (-1, -1) and counted in `drop`.
+template <int P, class Near>
+__device__ __forceinline__ void finish_ray(const RowPoly<P> &rp, const ShootArgs &a, const Near &nl,
+                                           int nn, float u, float t, float dyl, float dyl_lo,
+                                           float X, float Y, float ax, float ay, float rmin,
+                                           int &gx, int &gy, unsigned &drop)
+{
+    bool ok = true;
+    if (rmin < a.rc2)
+        ok = near_sum_hilo(nl, nn, u, t, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
+    X = __fmaf_rn(-ax, a.ipx_f, X);
+    Y = __fmaf_rn(-ay, a.ipy_f, Y);
+    pixel_xy(X, Y, rp.bx, rp.by, gx, gy);
+    if (!ok) { gx = -1; gy = -1; ++drop; }
+}
+
+// Task staging common to the mixed kernels: near lens list of the task's
+// level-1 cell as FP32 offsets from the first row (y) and, per level-2
+// column, from the node (x), with their rounding remainders.
+__device__ __forceinline__ int stage_near_y(const ShootArgs &a, const NearRuns &nr, double yref,
+                                            float4 *near, float2 *nlo, int lane)
+{
+    const int nn = nr.total();
+    __syncwarp();
+    for (int k = lane; k < nn; k += 32) {
+        int32_t idx = nr.index(k);
+        double dy = a.L.y[idx] - yref;
+        float hi = (float)dy;
+        near[k] = make_float4(0.f, hi, (float)a.L.m[idx], __int_as_float(idx));
+        nlo[k].y = (float)(dy - (double)hi);
+    }
+    return nn;
+}
+
+__device__ __forceinline__ void stage_near_x(const ShootArgs &a, int nn, double xnode,
+                                             float4 *near, float2 *nlo, int lane)
+{
+    __syncwarp();
+    for (int k = lane; k < nn; k += 32) {
+        double dx = a.L.x[__float_as_int(near[k].w)] - xnode;
+        float hi = (float)dx;
+        near[k].x = hi;
+        nlo[k].x = (float)(dx - (double)hi);
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ int64_t fetch_task(const ShootArgs &a, int lane, bool &stop)
+{
+    long long t = 0;
+    int ab = 0;
+    if (lane == 0) {
+        t = (long long)atomicAdd(a.work, 1ull);
+        ab = *a.abort_flag;
+    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    ab = __shfl_sync(0xffffffffu, ab, 0);
+    stop = ab != 0;
+    if (stop && lane == 0) atomicOr(a.status, 2u);
+    return t;
+}
+
+// Lane-valid ray of a warp-uniform walk position.
+__device__ __forceinline__ bool in_range(int k, int k0, int k1) { return k >= k0 && k < k1; }
+
+// Run-length step for one ray, with a warp vote so that the common case (no
+// lane changes pixel) takes no divergent branch; the flush inside is
+// predicated.  `valid` rays of other lanes' ranges do not count.
+__device__ __forceinline__ void run_step(RunState &rs, bool valid, int gx, int gy, uint32_t *map,
+                                         int mnx, int mny)
+{
+    const bool chg = valid && (gx != rs.cx || gy != rs.cy);
+    if (__ballot_sync(0xffffffffu, chg)) {
+        if (chg) {
+            if (rs.cnt) {
+                if ((unsigned)rs.cx < (unsigned)mnx && (unsigned)rs.cy < (unsigned)mny) {
+                    rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
+                    rs.pold = atomicAdd(map + (size_t)rs.cy * (unsigned)mnx + (unsigned)rs.cx, rs.cnt);
+                    rs.pcnt = rs.cnt;
+                    rs.in += rs.cnt;
+                } else {
+                    rs.out += rs.cnt;
+                }
+            }
+            rs.cx = gx;
+            rs.cy = gy;
+            rs.cnt = 0;
+        }
+    }
+    rs.cnt += valid ? 1u : 0u;
+}
+
+// One level-2 column of a warp's walk with a near list of NN lenses known at
+// compile time (records and the lane's dy, dy^2 held in registers); rays in
+// pairs.  Per ray the arithmetic is exactly near_sum_f32's and row_eval's.
+template <int P, int NN>
+__device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
+                                           int kbeg, int kend, int k0, int k1, float dyl, float dyl_lo,
+                                           RunState &rs, unsigned &drop)
+{
+    float lx[NN > 0 ? NN : 1], lm[NN > 0 ? NN : 1], dy[NN > 0 ? NN : 1], dy2[NN > 0 ? NN : 1];
+#pragma unroll
+    for (int q = 0; q < NN; ++q) {
+        float4 L = nl.near[q];
+        lx[q] = L.x;
+        lm[q] = L.z;
+        dy[q] = __fsub_rn(dyl, L.y);
+        dy2[q] = __fmul_rn(dy[q], dy[q]);
+    }
+    const Geo &g = a.g;
+    float u = __fadd_rn((float)kbeg, a.c0_f);
+    for (int k = kbeg; k < kend; k += 2, u += 2.f) {
+        const float u1 = __fadd_rn(u, 1.f);
+        const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
+        float X0, Y0, X1, Y1;
+        row_eval<P>(rp, t0, X0, Y0);
+        row_eval<P>(rp, t1, X1, Y1);
+        float sx0 = 0.f, sy0 = 0.f, mn0 = 3.0e38f, sx1 = 0.f, sy1 = 0.f, mn1 = 3.0e38f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            float dx0 = __fsub_rn(t0, lx[q]), dx1 = __fsub_rn(t1, lx[q]);
+            float r20 = __fmaf_rn(dx0, dx0, dy2[q]), r21 = __fmaf_rn(dx1, dx1, dy2[q]);
+            mn0 = fminf(mn0, r20);
+            mn1 = fminf(mn1, r21);
+            float s0 = __fdividef(lm[q], r20), s1 = __fdividef(lm[q], r21);
+            sx0 = __fmaf_rn(dx0, s0, sx0);
+            sy0 = __fmaf_rn(dy[q], s0, sy0);
+            sx1 = __fmaf_rn(dx1, s1, sx1);
+            sy1 = __fmaf_rn(dy[q], s1, sy1);
+        }
+        const bool v0 = in_range(k, k0, k1), v1 = in_range(k + 1, k0, k1);
+        const bool c0 = v0 && mn0 < a.rc2, c1 = v1 && mn1 < a.rc2;
+        bool ok0 = true, ok1 = true;
+        if (__ballot_sync(0xffffffffu, c0 || c1)) {
+            if (c0) ok0 = near_sum_hilo(nl, NN, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx0, sy0);
+            if (c1) ok1 = near_sum_hilo(nl, NN, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx1, sy1);
+        }
+        int gx0, gy0, gx1, gy1;
+        pixel_xy(__fmaf_rn(-sx0, a.ipx_f, X0), __fmaf_rn(-sy0, a.ipy_f, Y0), rp.bx, rp.by, gx0, gy0);
+        pixel_xy(__fmaf_rn(-sx1, a.ipx_f, X1), __fmaf_rn(-sy1, a.ipy_f, Y1), rp.bx, rp.by, gx1, gy1);
+        if (!ok0) { gx0 = -1; gy0 = -1; ++drop; }
+        if (!ok1) { gx1 = -1; gy1 = -1; ++drop; }
+        run_step(rs, v0, gx0, gy0, a.map_u32, g.mnx, g.mny);
+        run_step(rs, v1, gx1, gy1, a.map_u32, g.mnx, g.mny);
+    }
+}
+
+// The same for a near list of any length (read from shared memory).
+template <int P>
+__device__ __forceinline__ void walk_any(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
+                                         int nn, int kbeg, int kend, int k0, int k1, float dyl,
+                                         float dyl_lo, RunState &rs, unsigned &drop)
+{
+    const Geo &g = a.g;
+    float u = __fadd_rn((float)kbeg, a.c0_f);
+    for (int k = kbeg; k < kend; k += 2, u += 2.f) {
+        const float u1 = __fadd_rn(u, 1.f);
+        const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
+        float X0, Y0, X1, Y1, sx0, sy0, mn0, sx1, sy1, mn1;
+        row_eval<P>(rp, t0, X0, Y0);
+        row_eval<P>(rp, t1, X1, Y1);
+        near_sum2_f32(nl, nn, t0, t1, dyl, sx0, sy0, mn0, sx1, sy1, mn1);
+        const bool v0 = in_range(k, k0, k1), v1 = in_range(k + 1, k0, k1);
+        const bool c0 = v0 && mn0 < a.rc2, c1 = v1 && mn1 < a.rc2;
+        bool ok0 = true, ok1 = true;
+        if (__ballot_sync(0xffffffffu, c0 || c1)) {
+            if (c0) ok0 = near_sum_hilo(nl, nn, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx0, sy0);
+            if (c1) ok1 = near_sum_hilo(nl, nn, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx1, sy1);
+        }
+        int gx0, gy0, gx1, gy1;
+        pixel_xy(__fmaf_rn(-sx0, a.ipx_f, X0), __fmaf_rn(-sy0, a.ipy_f, Y0), rp.bx, rp.by, gx0, gy0);
+        pixel_xy(__fmaf_rn(-sx1, a.ipx_f, X1), __fmaf_rn(-sy1, a.ipy_f, Y1), rp.bx, rp.by, gx1, gy1);
+        if (!ok0) { gx0 = -1; gy0 = -1; ++drop; }
+        if (!ok1) { gx1 = -1; gy1 = -1; ++drop; }
+        run_step(rs, v0, gx0, gy0, a.map_u32, g.mnx, g.mny);
+        run_step(rs, v1, gx1, gy1, a.map_u32, g.mnx, g.mny);
+    }
+}
+
+// Keeps a value in a register: the compiler may not recompute it (it would
+// otherwise rebuild FP64-derived constants inside the walk, and FP64
+// arithmetic is slow on this GPU).
+__device__ __forceinline__ float pin(float v)
+{
+    asm volatile("" : "+f"(v));
+    return v;
+}
+
+template <int P>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mixed(ShootArgs a)
+{
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4 *near = smem + wid * a.near_cap;
+    float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * a.near_cap) + wid * a.near_cap;
+    const SmemNear nl{near, nlo};
+    const Geo &g = a.g;
+    const int64_t jb = a.ray_begin / g.n3x, ib = a.ray_begin % g.n3x;
+    const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
+
+    RunState rs{-1, -1, 0u, 0u, 0u, 0u, 0u, 0u};
+    unsigned drop = 0;
+    unsigned long long pairs = 0, tasks = 0;
+    // lane offset from the task's first row (FP64 product rounded once)
+    const double dyl_d = (double)lane * g.l3y;
+    const float dyl = pin((float)dyl_d);
+    const float dyl_lo = pin((float)(dyl_d - (double)(float)dyl_d));
+
+    for (;;) {
+        bool stop;
+        const int64_t t = fetch_task(a, lane, stop);
+        if (stop || t >= a.n_tasks) break;
+        TaskShape ts;
+        if (!decode_task(a, t, ts)) continue;
+        ++tasks;
+        const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
+        const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
+        const int nn = stage_near_y(a, nr, yref, near, nlo, lane);
+        const int64_t j = ts.row0 + lane;
+        const bool active = j < ts.rows_end && j >= jb && j <= je;
+        const int64_t c2y = j / g.n2y;
+        const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
+        for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
+            stage_near_x(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
+            const int64_t i0 = c2x * g.n2x;
+            int k0 = 0, k1 = (int)(min(i0 + g.n2x, g.n3x) - i0);
+            if (j == jb) k0 = max(k0, (int)max((int64_t)0, ib - i0));
+            if (j == je) k1 = min(k1, (int)max((int64_t)0, ie - i0));
+            if (!active || k0 >= k1) { k0 = 0; k1 = 0; }
+            // warp-uniform walk range: the union of the lanes' ranges
+            const int kbeg = __reduce_min_sync(0xffffffffu, k1 > k0 ? k0 : 0x7fffffff);
+            const int kend = __reduce_max_sync(0xffffffffu, k1);
+            if (kbeg >= kend) continue;
+            RowPoly<P> rp;
+            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
+            pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
+            switch (nn) {
+            case 0: walk_fixed<P, 0>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
+            case 1: walk_fixed<P, 1>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
+            case 2: walk_fixed<P, 2>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
+            case 3: walk_fixed<P, 3>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
+            case 4: walk_fixed<P, 4>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
+            default: walk_any<P>(rp, a, nl, nn, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
+            }
+        }
+    }
+    run_flush(rs, a.map_u32, g.mnx, g.mny);
+    rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
+    // dropped rays were sent to (-1, -1) and counted as out above
+    flush_stats(a, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, rs.ovf);
+}
+
+// Cloud-in-cell variant: a float map, four weighted atomics per ray.
+template <int P>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mixed_cic(ShootArgs a)
+{
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4 *near = smem + wid * a.near_cap;
+    float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * a.near_cap) + wid * a.near_cap;
+    const SmemNear nl{near, nlo};
+    const Geo &g = a.g;
+    const int64_t jb = a.ray_begin / g.n3x, ib = a.ray_begin % g.n3x;
+    const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
+    unsigned in = 0, out = 0, drop = 0;
+    unsigned long long pairs = 0, tasks = 0;
+    for (;;) {
+        bool stop;
+        const int64_t t = fetch_task(a, lane, stop);
+        if (stop || t >= a.n_tasks) break;
+        TaskShape ts;
+        if (!decode_task(a, t, ts)) continue;
+        ++tasks;
+        const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
+        const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
+        const int nn = stage_near_y(a, nr, yref, near, nlo, lane);
+        const int64_t j = ts.row0 + lane;
+        const bool active = j < ts.rows_end && j >= jb && j <= je;
+        const double dyl_d = (double)lane * g.l3y;
+        const float dyl = (float)dyl_d;
+        const float dyl_lo = (float)(dyl_d - (double)dyl);
+        const int64_t c2y = j / g.n2y;
+        const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
+        for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
+            stage_near_x(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
+            if (!active) continue;
+            const int64_t i0 = c2x * g.n2x;
+            int k0 = 0, k1 = (int)(min(i0 + g.n2x, g.n3x) - i0);
+            if (j == jb) k0 = max(k0, (int)max((int64_t)0, ib - i0));
+            if (j == je) k1 = min(k1, (int)max((int64_t)0, ie - i0));
+            if (k0 >= k1) continue;
+            RowPoly<P> rp;
+            row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), q, a, rp);
+            pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
+            float u = __fadd_rn((float)k0, a.c0_f);
+            for (int k = k0; k < k1; ++k, u += 1.f) {
+                const float t0 = __fmul_rn(u, a.l3x_f);
+                float X, Y, ax, ay, mn;
+                row_eval<P>(rp, t0, X, Y);
+                near_sum_f32(nl, nn, t0, dyl, ax, ay, mn);
+                bool ok = true;
+                if (mn < a.rc2) ok = near_sum_hilo(nl, nn, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
+                if (!ok) { ++drop; continue; }
+                X = __fmaf_rn(-ax, a.ipx_f, X);
+                Y = __fmaf_rn(-ay, a.ipy_f, Y);
+                float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
+                float flx, fly;
+                int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
+                float wx = __fsub_rn(fx, flx), wy = __fsub_rn(fy, fly);
+                unsigned ix = (unsigned)rp.bx + (unsigned)kx;
+                unsigned iy = (unsigned)rp.by + (unsigned)ky;
+                bool any = false;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    unsigned px = ix + (unsigned)(qq & 1), py = iy + (unsigned)(qq >> 1);
+                    if (px >= (unsigned)g.mnx || py >= (unsigned)g.mny) continue;
+                    float w = __fmul_rn((qq & 1) ? wx : 1.f - wx, (qq >> 1) ? wy : 1.f - wy);
+                    atomicAdd(a.map_f32 + (size_t)py * (unsigned)g.mnx + px, w);
+                    any = true;
+                }
+                if (any) ++in; else ++out;
+            }
+        }
+    }
+    flush_stats(a, in, out, drop, pairs, lane == 0 ? tasks : 0, 0u);
+}
+
 // Near records computed from the FP64 lens table, for tracing single rays.
 struct GlobalNear {
     const LensTable *L;
@@ -230,219 +598,6 @@ struct GlobalNear {
         return make_float2((float)(dx - (double)(float)dx), (float)(dy - (double)(float)dy));
     }
 };
-
-template <int P>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_shoot_mixed(ShootArgs a)
-{
-    extern __shared__ float4 smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4 *near = smem + wid * a.near_cap;
-    float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * a.near_cap) + wid * a.near_cap;
-    const Geo &g = a.g;
-    const int64_t jb = a.ray_begin / g.n3x, ib = a.ray_begin % g.n3x;
-    const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
-
-    unsigned long long in = 0, out = 0, drop = 0, pairs = 0, tasks = 0;
-    unsigned ovf = 0;
-    uint32_t cur = PIX_OUT;
-    unsigned cnt = 0, pold = 0, pcnt = 0;
-
-    for (;;) {
-        int64_t t = 0;
-        int stop = 0;
-        if (lane == 0) {
-            t = (int64_t)atomicAdd(a.work, 1ull);
-            stop = *a.abort_flag;
-        }
-        t = __shfl_sync(0xffffffffu, t, 0);
-        stop = __shfl_sync(0xffffffffu, stop, 0);
-        if (stop) {
-            if (lane == 0) atomicOr(a.status, 2u);
-            break;
-        }
-        if (t >= a.n_tasks) break;
-        TaskShape ts;
-        if (!decode_task(a, t, ts)) continue;
-        ++tasks;
-        // stage the near lenses: y offset from the task's first row and mass
-        const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
-        const int nn = nr.total();
-        const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
-        __syncwarp();
-        for (int k = lane; k < nn; k += 32) {
-            int32_t idx = nr.index(k);
-            double dy = a.L.y[idx] - yref;
-            float hi = (float)dy;
-            near[k] = make_float4(0.f, hi, (float)a.L.m[idx], __int_as_float(idx));
-            nlo[k].y = (float)(dy - (double)hi);
-        }
-        const int64_t j = ts.row0 + lane;
-        const bool active = j < ts.rows_end && j >= jb && j <= je;
-        const double dyl_d = (double)lane * g.l3y;
-        const float dyl = (float)dyl_d;
-        const float dyl_lo = (float)(dyl_d - (double)dyl);
-        const int64_t c2y = j / g.n2y;
-        const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
-        for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
-            const double xnode = g.rx0 + ((double)c2x + 0.5) * g.l2x;
-            __syncwarp();
-            for (int k = lane; k < nn; k += 32) {
-                double dx = a.L.x[__float_as_int(near[k].w)] - xnode;
-                float hi = (float)dx;
-                near[k].x = hi;
-                nlo[k].x = (float)(dx - (double)hi);
-            }
-            __syncwarp();
-            if (!active) continue;
-            const int64_t i0 = c2x * g.n2x;
-            int64_t ia = i0, iend = min(i0 + g.n2x, g.n3x);
-            if (j == jb) ia = max(ia, ib);
-            if (j == je) iend = min(iend, ie);
-            if (ia >= iend) continue;
-            RowPoly<P> rp;
-            row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), q, a, rp);
-            pairs += (unsigned long long)nn * (unsigned long long)(iend - ia);
-            float u = __fadd_rn((float)(ia - i0), a.c0_f);
-            for (int64_t i = ia; i < iend; ++i, u += 1.f) {
-                float tt = __fmul_rn(u, a.l3x_f);
-                float X, Y, ax, ay;
-                row_eval<P>(rp, tt, X, Y);
-                near_sum_f32(SmemNear{near, nlo}, nn, u, tt, dyl, dyl_lo, a.l3x_f, a.l3x_lo, a.rc2, ax, ay);
-                X = __fmaf_rn(-ax, a.ipx_f, X);
-                Y = __fmaf_rn(-ay, a.ipy_f, Y);
-                uint32_t pix = classify(X, Y, ax, rp.bx, rp.by, g.mnx, g.mny);
-                if (pix != cur) {
-                    if (cnt) {
-                        if (cur < PIX_DROP) {
-                            ovf |= (pold > 0xFFFFFFFFu - pcnt);
-                            pold = atomicAdd(a.map_u32 + cur, cnt);
-                            pcnt = cnt;
-                            in += cnt;
-                        } else if (cur == PIX_OUT) {
-                            out += cnt;
-                        } else {
-                            drop += cnt;
-                        }
-                    }
-                    cur = pix;
-                    cnt = 0;
-                }
-                ++cnt;
-            }
-        }
-    }
-    if (cnt) {
-        if (cur < PIX_DROP) {
-            ovf |= (pold > 0xFFFFFFFFu - pcnt);
-            pold = atomicAdd(a.map_u32 + cur, cnt);
-            pcnt = cnt;
-            in += cnt;
-        } else if (cur == PIX_OUT) {
-            out += cnt;
-        } else {
-            drop += cnt;
-        }
-    }
-    ovf |= (pold > 0xFFFFFFFFu - pcnt);
-    // near pairs are counted per lane; sum over lanes is the exact pair count
-    flush_stats(a, in, out, drop, pairs, lane == 0 ? tasks : 0, ovf);
-}
-
-// Cloud-in-cell variant of the mixed kernel (float map, four atomics per ray).
-template <int P>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32) k_shoot_mixed_cic(ShootArgs a)
-{
-    extern __shared__ float4 smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float4 *near = smem + wid * a.near_cap;
-    float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * a.near_cap) + wid * a.near_cap;
-    const Geo &g = a.g;
-    const int64_t jb = a.ray_begin / g.n3x, ib = a.ray_begin % g.n3x;
-    const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
-    unsigned long long in = 0, out = 0, drop = 0, pairs = 0, tasks = 0;
-    for (;;) {
-        int64_t t = 0;
-        int stop = 0;
-        if (lane == 0) {
-            t = (int64_t)atomicAdd(a.work, 1ull);
-            stop = *a.abort_flag;
-        }
-        t = __shfl_sync(0xffffffffu, t, 0);
-        stop = __shfl_sync(0xffffffffu, stop, 0);
-        if (stop) {
-            if (lane == 0) atomicOr(a.status, 2u);
-            break;
-        }
-        if (t >= a.n_tasks) break;
-        TaskShape ts;
-        if (!decode_task(a, t, ts)) continue;
-        ++tasks;
-        const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
-        const int nn = nr.total();
-        const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
-        __syncwarp();
-        for (int k = lane; k < nn; k += 32) {
-            int32_t idx = nr.index(k);
-            double dy = a.L.y[idx] - yref;
-            float hi = (float)dy;
-            near[k] = make_float4(0.f, hi, (float)a.L.m[idx], __int_as_float(idx));
-            nlo[k].y = (float)(dy - (double)hi);
-        }
-        const int64_t j = ts.row0 + lane;
-        const bool active = j < ts.rows_end && j >= jb && j <= je;
-        const double dyl_d = (double)lane * g.l3y;
-        const float dyl = (float)dyl_d;
-        const float dyl_lo = (float)(dyl_d - (double)dyl);
-        const int64_t c2y = j / g.n2y;
-        const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
-        for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
-            const double xnode = g.rx0 + ((double)c2x + 0.5) * g.l2x;
-            __syncwarp();
-            for (int k = lane; k < nn; k += 32) {
-                double dx = a.L.x[__float_as_int(near[k].w)] - xnode;
-                float hi = (float)dx;
-                near[k].x = hi;
-                nlo[k].x = (float)(dx - (double)hi);
-            }
-            __syncwarp();
-            if (!active) continue;
-            const int64_t i0 = c2x * g.n2x;
-            int64_t ia = i0, iend = min(i0 + g.n2x, g.n3x);
-            if (j == jb) ia = max(ia, ib);
-            if (j == je) iend = min(iend, ie);
-            if (ia >= iend) continue;
-            RowPoly<P> rp;
-            row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), q, a, rp);
-            pairs += (unsigned long long)nn * (unsigned long long)(iend - ia);
-            float u = __fadd_rn((float)(ia - i0), a.c0_f);
-            for (int64_t i = ia; i < iend; ++i, u += 1.f) {
-                float tt = __fmul_rn(u, a.l3x_f);
-                float X, Y, ax, ay;
-                row_eval<P>(rp, tt, X, Y);
-                near_sum_f32(SmemNear{near, nlo}, nn, u, tt, dyl, dyl_lo, a.l3x_f, a.l3x_lo, a.rc2, ax, ay);
-                X = __fmaf_rn(-ax, a.ipx_f, X);
-                Y = __fmaf_rn(-ay, a.ipy_f, Y);
-                if (ax != ax) { ++drop; continue; }
-                float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
-                float flx = floorf(fx), fly = floorf(fy);
-                float wx = __fsub_rn(fx, flx), wy = __fsub_rn(fy, fly);
-                unsigned ix = (unsigned)rp.bx + (unsigned)__float2int_rd(flx);
-                unsigned iy = (unsigned)rp.by + (unsigned)__float2int_rd(fly);
-                bool any = false;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    unsigned px = ix + (unsigned)(qq & 1), py = iy + (unsigned)(qq >> 1);
-                    if (px >= (unsigned)g.mnx || py >= (unsigned)g.mny) continue;
-                    float w = __fmul_rn((qq & 1) ? wx : 1.f - wx, (qq >> 1) ? wy : 1.f - wy);
-                    atomicAdd(a.map_f32 + (int64_t)py * g.mnx + px, w);
-                    any = true;
-                }
-                if (any) ++in; else ++out;
-            }
-        }
-    }
-    flush_stats(a, in, out, drop, pairs, lane == 0 ? tasks : 0, 0u);
-}
 
 // ---- tracing: the same per-ray arithmetic for listed rays -------------------
 
@@ -465,30 +620,33 @@ __global__ void k_trace_mixed(ShootArgs a, const int64_t *__restrict__ idx, int6
     int64_t row0 = c1y * g.n1y + 32 * ((j - c1y * g.n1y) / 32);
     double yref = g.ry0 + ((double)row0 + 0.5) * g.l3y;
     double xnode = g.rx0 + ((double)c2x + 0.5) * g.l2x;
-    float dyl = (float)((double)(j - row0) * g.l3y);
+    const double dyl_d = (double)(j - row0) * g.l3y;
+    const float dyl = (float)dyl_d;
+    const float dyl_lo = (float)(dyl_d - (double)dyl);
     float qf = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
     RowPoly<P> rp;
     row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), qf, a, rp);
     float u = __fadd_rn((float)(i - c2x * g.n2x), a.c0_f);
     float tt = __fmul_rn(u, a.l3x_f);
-    float X, Y;
+    float X, Y, ax, ay, mn;
     row_eval<P>(rp, tt, X, Y);
-    // near sum over the same lenses, in the same order, with records built
-    // and summed exactly as in the walk
     const NearRuns nr = near_runs(a, c1x, c1y);
-    const double dyl_d = (double)(j - row0) * g.l3y;
-    const float dyl_lo = (float)(dyl_d - (double)dyl);
-    float sx, sy;
-    near_sum_f32(GlobalNear{&a.L, nr, xnode, yref}, nr.total(), u, tt, dyl, dyl_lo, a.l3x_f,
-                 a.l3x_lo, a.rc2, sx, sy);
-    X = __fmaf_rn(-sx, a.ipx_f, X);
-    Y = __fmaf_rn(-sy, a.ipy_f, Y);
-    uint32_t p = classify(X, Y, sx, rp.bx, rp.by, g.mnx, g.mny);
-    beta[2 * q] = g.mx0 + ((double)rp.bx + (double)X) * g.dpx;
-    beta[2 * q + 1] = g.my0 + ((double)rp.by + (double)Y) * g.dpy;
-    if (p == PIX_DROP) { pix[2 * q] = -2; pix[2 * q + 1] = -2; }
-    else if (p == PIX_OUT) { pix[2 * q] = -1; pix[2 * q + 1] = -1; }
-    else { pix[2 * q] = (int32_t)(p % (uint32_t)g.mnx); pix[2 * q + 1] = (int32_t)(p / (uint32_t)g.mnx); }
+    const GlobalNear nl{&a.L, nr, xnode, yref};
+    const int nn = nr.total();
+    near_sum_f32(nl, nn, tt, dyl, ax, ay, mn);
+    int gx, gy;
+    unsigned drop = 0;
+    finish_ray<P>(rp, a, nl, nn, u, tt, dyl, dyl_lo, X, Y, ax, ay, mn, gx, gy, drop);
+    // beta in theta_E from the kernel's own pixel-unit value
+    bool ok = true;
+    if (mn < a.rc2) ok = near_sum_hilo(nl, nn, u, tt, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
+    float Xf = __fmaf_rn(-ax, a.ipx_f, X), Yf = __fmaf_rn(-ay, a.ipy_f, Y);
+    beta[2 * q] = g.mx0 + ((double)rp.bx + (double)Xf) * g.dpx;
+    beta[2 * q + 1] = g.my0 + ((double)rp.by + (double)Yf) * g.dpy;
+    if (!ok) { pix[2 * q] = -2; pix[2 * q + 1] = -2; }
+    else if ((unsigned)gx >= (unsigned)g.mnx || (unsigned)gy >= (unsigned)g.mny) {
+        pix[2 * q] = -1; pix[2 * q + 1] = -1;
+    } else { pix[2 * q] = gx; pix[2 * q + 1] = gy; }
 }
 
 template <bool NEARFAR>
