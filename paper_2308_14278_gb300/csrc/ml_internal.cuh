@@ -111,6 +111,16 @@ int mixed_p_supported(int p);     // the Taylor order the mixed kernel will use 
 // 2^-23 (|t| + |dyl|) / r for a ray at distance r from a lens.  Rays that pass
 // closer than r_c (sqrt(rc2), where that error could exceed 5e-7) redo the
 // sum with the offsets carried as hi + lo float pairs (near_sum_hilo).
+// Approximate reciprocal (the PTX rcp.approx.ftz.f32 instruction, relative
+// error below 2^-23).  The near sums use m * rcp(r^2); r^2 never comes near
+// the float range limits for lenses and rays inside a field.
+__device__ __forceinline__ float rcp_approx(float y)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+    return r;
+}
+
 template <class Near>
 __device__ __forceinline__ void near_sum_f32(const Near &nl, int nn, float t, float dyl,
                                              float &ax, float &ay, float &rmin)
@@ -123,7 +133,7 @@ __device__ __forceinline__ void near_sum_f32(const Near &nl, int nn, float t, fl
         float dx = __fsub_rn(t, L.x);
         float r2 = __fmaf_rn(dx, dx, dy2);
         mn = fminf(mn, r2);
-        float s = __fdividef(L.z, r2);
+        float s = __fmul_rn(L.z, rcp_approx(r2));
         sx = __fmaf_rn(dx, s, sx);
         sy = __fmaf_rn(dy, s, sy);
     }
@@ -150,8 +160,8 @@ __device__ __forceinline__ void near_sum2_f32(const Near &nl, int nn, float t0, 
         float r21 = __fmaf_rn(dx1, dx1, dy2);
         mn0 = fminf(mn0, r20);
         mn1 = fminf(mn1, r21);
-        float s0 = __fdividef(L.z, r20);
-        float s1 = __fdividef(L.z, r21);
+        float s0 = __fmul_rn(L.z, rcp_approx(r20));
+        float s1 = __fmul_rn(L.z, rcp_approx(r21));
         sx0 = __fmaf_rn(dx0, s0, sx0);
         sy0 = __fmaf_rn(dy, s0, sy0);
         sx1 = __fmaf_rn(dx1, s1, sx1);
@@ -179,7 +189,7 @@ __device__ __forceinline__ bool near_sum_hilo(const Near &nl, int nn, float u, f
         float dy = __fadd_rn(__fsub_rn(dyl, L.y), __fsub_rn(dyl_lo, R.y));
         float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
         hit |= (r2 == 0.f);
-        float s = __fdividef(L.z, r2);
+        float s = __fmul_rn(L.z, rcp_approx(r2));
         sx = __fmaf_rn(dx, s, sx);
         sy = __fmaf_rn(dy, s, sy);
     }

@@ -346,12 +346,31 @@ __device__ __forceinline__ void run_step(RunState &rs, bool valid, int gx, int g
     rs.cnt += valid ? 1u : 0u;
 }
 
-// One level-2 column of a warp's walk with a near list of NN lenses known at
-// compile time (records and the lane's dy, dy^2 held in registers); rays in
-// pairs.  Per ray the arithmetic is exactly near_sum_f32's and row_eval's.
+// Flush a finished run of `cnt` rays in pixel (cx, cy) (predicated use).
+__device__ __forceinline__ void flush_run(RunState &rs, int cx, int cy, unsigned cnt, uint32_t *map,
+                                          int mnx, int mny)
+{
+    if (cnt == 0) return;
+    if ((unsigned)cx < (unsigned)mnx && (unsigned)cy < (unsigned)mny) {
+        rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
+        rs.pold = atomicAdd(map + (size_t)cy * (unsigned)mnx + (unsigned)cx, cnt);
+        rs.pcnt = cnt;
+        rs.in += cnt;
+    } else {
+        rs.out += cnt;
+    }
+}
+
+// One level-2 column of a warp's walk when every active lane covers the
+// warp's whole range [kbeg, kend) ("on" lanes) and the near list has NN
+// lenses (NN known at compile time: records and the lane's dy, dy^2 in
+// registers).  Rays go in pairs; a run's length is the distance between the
+// indices where it starts and ends, so no per-ray counting is needed; one
+// warp vote per pair decides whether any lane's pixel changed.  Per ray the
+// arithmetic is exactly near_sum_f32's and row_eval's.
 template <int P, int NN>
 __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
-                                           int kbeg, int kend, int k0, int k1, float dyl, float dyl_lo,
+                                           int kbeg, int kend, bool on, float dyl, float dyl_lo,
                                            RunState &rs, unsigned &drop)
 {
     float lx[NN > 0 ? NN : 1], lm[NN > 0 ? NN : 1], dy[NN > 0 ? NN : 1], dy2[NN > 0 ? NN : 1];
@@ -364,6 +383,7 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         dy2[q] = __fmul_rn(dy[q], dy[q]);
     }
     const Geo &g = a.g;
+    int kst = kbeg;                      // first ray of the current run in this walk
     float u = __fadd_rn((float)kbeg, a.c0_f);
     for (int k = kbeg; k < kend; k += 2, u += 2.f) {
         const float u1 = __fadd_rn(u, 1.f);
@@ -378,27 +398,49 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
             float r20 = __fmaf_rn(dx0, dx0, dy2[q]), r21 = __fmaf_rn(dx1, dx1, dy2[q]);
             mn0 = fminf(mn0, r20);
             mn1 = fminf(mn1, r21);
-            float s0 = __fdividef(lm[q], r20), s1 = __fdividef(lm[q], r21);
+            float s0 = __fmul_rn(lm[q], rcp_approx(r20)), s1 = __fmul_rn(lm[q], rcp_approx(r21));
             sx0 = __fmaf_rn(dx0, s0, sx0);
             sy0 = __fmaf_rn(dy[q], s0, sy0);
             sx1 = __fmaf_rn(dx1, s1, sx1);
             sy1 = __fmaf_rn(dy[q], s1, sy1);
         }
-        const bool v0 = in_range(k, k0, k1), v1 = in_range(k + 1, k0, k1);
-        const bool c0 = v0 && mn0 < a.rc2, c1 = v1 && mn1 < a.rc2;
+        const bool has1 = k + 1 < kend;  // warp-uniform
         bool ok0 = true, ok1 = true;
-        if (__ballot_sync(0xffffffffu, c0 || c1)) {
-            if (c0) ok0 = near_sum_hilo(nl, NN, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx0, sy0);
-            if (c1) ok1 = near_sum_hilo(nl, NN, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx1, sy1);
+        if (NN > 0) {
+            const bool c0 = on && mn0 < a.rc2, c1 = on && has1 && mn1 < a.rc2;
+            if (__ballot_sync(0xffffffffu, c0 || c1)) {
+                if (c0) ok0 = near_sum_hilo(nl, NN, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx0, sy0);
+                if (c1) ok1 = near_sum_hilo(nl, NN, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx1, sy1);
+            }
         }
         int gx0, gy0, gx1, gy1;
         pixel_xy(__fmaf_rn(-sx0, a.ipx_f, X0), __fmaf_rn(-sy0, a.ipy_f, Y0), rp.bx, rp.by, gx0, gy0);
         pixel_xy(__fmaf_rn(-sx1, a.ipx_f, X1), __fmaf_rn(-sy1, a.ipy_f, Y1), rp.bx, rp.by, gx1, gy1);
-        if (!ok0) { gx0 = -1; gy0 = -1; ++drop; }
-        if (!ok1) { gx1 = -1; gy1 = -1; ++drop; }
-        run_step(rs, v0, gx0, gy0, a.map_u32, g.mnx, g.mny);
-        run_step(rs, v1, gx1, gy1, a.map_u32, g.mnx, g.mny);
+        if (NN > 0) {
+            if (!ok0) { gx0 = -1; gy0 = -1; drop += on ? 1u : 0u; }
+            if (!ok1) { gx1 = -1; gy1 = -1; drop += (on && has1) ? 1u : 0u; }
+        }
+        const bool ch0 = on && (gx0 != rs.cx || gy0 != rs.cy);
+        const int nx = ch0 ? gx0 : rs.cx, ny = ch0 ? gy0 : rs.cy;
+        const bool ch1 = on && has1 && (gx1 != nx || gy1 != ny);
+        if (__ballot_sync(0xffffffffu, ch0 || ch1)) {
+            if (ch0) {
+                flush_run(rs, rs.cx, rs.cy, rs.cnt + (unsigned)(k - kst), a.map_u32, g.mnx, g.mny);
+                rs.cnt = 0;
+                kst = k;
+                rs.cx = gx0;
+                rs.cy = gy0;
+            }
+            if (ch1) {
+                flush_run(rs, rs.cx, rs.cy, rs.cnt + (unsigned)(k + 1 - kst), a.map_u32, g.mnx, g.mny);
+                rs.cnt = 0;
+                kst = k + 1;
+                rs.cx = gx1;
+                rs.cy = gy1;
+            }
+        }
     }
+    if (on) rs.cnt += (unsigned)(kend - kst);
 }
 
 // The same for a near list of any length (read from shared memory).
@@ -490,13 +532,18 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
             RowPoly<P> rp;
             row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
             pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
-            switch (nn) {
-            case 0: walk_fixed<P, 0>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
-            case 1: walk_fixed<P, 1>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
-            case 2: walk_fixed<P, 2>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
-            case 3: walk_fixed<P, 3>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
-            case 4: walk_fixed<P, 4>(rp, a, nl, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
-            default: walk_any<P>(rp, a, nl, nn, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop); break;
+            const bool on = k1 > k0;
+            const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
+            if (uniform && nn <= 4) {
+                switch (nn) {
+                case 0: walk_fixed<P, 0>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 1: walk_fixed<P, 1>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 2: walk_fixed<P, 2>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 3: walk_fixed<P, 3>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                default: walk_fixed<P, 4>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                }
+            } else {
+                walk_any<P>(rp, a, nl, nn, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop);
             }
         }
     }
