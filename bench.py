@@ -35,6 +35,23 @@ UNIT = "rays/s"
 N_TRACKS, TRACK_SAMPLES, SIGMA_PX = 10, 4096, 0.5
 # FP32 FMA units of GB300 (152 SMs x 128 lanes) at the maximum SM clock
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes per ray of the shooting kernel, from the ncu capture summarised in
+# profiles/k_shoot_mixed_paper-map-2e10-ray-slice.md (dram__bytes_read.sum +
+# dram__bytes_write.sum = 450.4 MB for 2.0e10 rays), valid for the kernel
+# sources with these sha1 prefixes only.
+TRAFFIC_BYTES_PER_RAY = 450.413056e6 / 2.0e10
+TRAFFIC_SOURCES = {"ml_shoot.cu": "26dd64ff", "ml_internal.cuh": "9b6a32ff"}
+
+
+def traffic_per_launch(rays_per_launch: float):
+    """Measured DRAM bytes per launch, or None once the kernel has changed."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2308_14278_gb300", "csrc")
+    for name, prefix in TRAFFIC_SOURCES.items():
+        with open(os.path.join(csrc, name), "rb") as fh:
+            if not hashlib.sha1(fh.read()).hexdigest().startswith(prefix):
+                return None
+    return TRAFFIC_BYTES_PER_RAY * rays_per_launch
 
 
 def parse():
@@ -230,7 +247,8 @@ def run_ours(args, rank, world, local):
         "breakdown_ms": {"create": float(per[:, 0].mean()), "shoot": shoot_ms,
                          "mu": float(per[:, 2].mean()), "light_curves": float(per[:, 3].mean())},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": traffic_per_launch(n_rays / max(1, stats["launches"])),
                      "kernel": "k_shoot_mixed", "flops_per_launch_survey_convention":
                          survey_flops / max(1, stats["launches"]),
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},

@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-#define ML_ABI_VERSION 1
+#define ML_ABI_VERSION 2
 
 typedef enum {
     ML_OK = 0,
@@ -118,13 +118,16 @@ typedef struct {
     double map_x0, map_y0, map_x1, map_y1;
     int32_t map_nx, map_ny;
 
-    /* Level grids (§3.2).  l1_x, l1_y zero: Eq. 10 on each side.  l2_sub zero:
-     * 20 level-2 cells per level-1 side. */
+    /* Level grids (§3.2).  l1_x, l1_y zero: Eq. 10 on each side.  l2_sub_x,
+     * l2_sub_y: level-2 cells per level-1 cell along x and y; both zero: the
+     * paper's 20 x 20, or the autotuner's choice when tune is set. */
     double l1_x, l1_y;
-    int32_t l2_sub;
-    int32_t reserved0;
+    int32_t l2_sub_x, l2_sub_y;
     double far_tol;             /* target truncation bound for taylor_p = 0; 0 = 1e-7 */
     uint64_t max_launch_rays;   /* rays per shooting launch; 0 = 2^36 */
+    int32_t tune;               /* 1: pick l2_sub_x, l2_sub_y (and with them p) by the
+                                   built-in cost model when both are zero */
+    int32_t reserved0;
 } ml_field_desc;
 
 /* Derived parameters of a field (what §3.1-§3.2 compute from the desc). */
@@ -138,10 +141,12 @@ typedef struct {
     double l0;                              /* mean spacing per lens (Eq. 10); +inf if none */
     int64_t n1x, n1y, n2x, n2y;             /* rays per level-1 and level-2 cell side */
     int64_t N1x, N1y, N2x, N2y;             /* cells across the lattice */
-    int32_t taylor_p, l2_sub;
+    int32_t taylor_p;
+    int32_t l2_sub_x, l2_sub_y;             /* level-2 cells per level-1 cell side */
     int32_t precision, deposit;
     int32_t max_near;                       /* largest near-lens list of a level-1 cell */
     int32_t build;                          /* coefficient build that ran (ML_BUILD_*) */
+    int32_t tuned;                          /* 1 if the autotuner chose the level-2 grid */
     double far_bound;                       /* truncation bound at taylor_p (theta_E) */
     double mu_per_count;                    /* S_I / S_S of Eq. 12 */
 } ml_field_params;

@@ -165,7 +165,8 @@ def _round_half_up(v: float) -> int:
 
 
 def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, map_n,
-                    ray_box=None, ray_n=None, n_av=0.0, l1=None, l2_sub=20, p=3) -> Geometry:
+                    ray_box=None, ray_n=None, n_av=0.0, l1=None, l2_sub=20, p=3,
+                    l2_sub_y=None) -> Geometry:
     """The parameters of §3.1-§3.2 for one map.
 
     Readings: the ray rectangle is the pre-image of the widened source region
@@ -173,7 +174,8 @@ def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, ma
     lens equation, one can obtain the image plane"); L_1y follows L_1x's rule
     on the y side; N_* in L_0 counts the lenses inside the ray rectangle; the
     level grids are laid on the ray lattice, a level-2 cell holding
-    round(L_2 / L_3) rays per side and a level-1 cell l2_sub times that.
+    round(L_2 / L_3) rays per side and a level-1 cell l2_sub (x) or l2_sub_y (y,
+    default l2_sub) times that; the paper's L_2 = L_1 / 20 is l2_sub = 20.
     """
     mx0, my0, mx1, my1 = map_box
     mnx, mny = map_n
@@ -210,12 +212,13 @@ def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, ma
         l1y = min(l0, liy / 10.0)
     else:
         l1x, l1y = l1
+    l2sy = l2_sub if l2_sub_y is None else l2_sub_y
     l2x = l1x / l2_sub                                 # §3.2, Level 2
-    l2y = l1y / l2_sub
+    l2y = l1y / l2sy
     n2x = max(1, _round_half_up(l2x / l3x))
     n2y = max(1, _round_half_up(l2y / l3y))
     n1x = l2_sub * n2x
-    n1y = l2_sub * n2y
+    n1y = l2sy * n2y
     g = Geometry(kappa, gamma, kappa_star, sheet[0], sheet[1], sheet[2],
                  rx0, ry0, rx1, ry1, l3x, l3y, n3x, n3y, mx0, my0, dpx, dpy, mnx, mny,
                  n_in, l0, n1x, n1y, n2x, n2y, -(-n3x // n1x), -(-n3y // n1y), p)

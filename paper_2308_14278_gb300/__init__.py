@@ -23,7 +23,7 @@ from . import inputs  # noqa: F401  (seeded synthetic inputs, no method arithmet
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libml.so")
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 PREC_DIRECT64, PREC_NEARFAR64, PREC_MIXED = 0, 1, 2
 DEPOSIT_NGP, DEPOSIT_CIC = 0, 1
 BUILD_AUTO, BUILD_DIRECT, BUILD_HIERARCHICAL = 0, 1, 2
@@ -59,8 +59,9 @@ class FieldDesc(C.Structure):
         ("n_rays_x", C.c_int64), ("n_rays_y", C.c_int64), ("n_av", C.c_double),
         ("map_x0", C.c_double), ("map_y0", C.c_double), ("map_x1", C.c_double),
         ("map_y1", C.c_double), ("map_nx", C.c_int32), ("map_ny", C.c_int32),
-        ("l1_x", C.c_double), ("l1_y", C.c_double), ("l2_sub", C.c_int32),
-        ("reserved0", C.c_int32), ("far_tol", C.c_double), ("max_launch_rays", C.c_uint64),
+        ("l1_x", C.c_double), ("l1_y", C.c_double), ("l2_sub_x", C.c_int32),
+        ("l2_sub_y", C.c_int32), ("far_tol", C.c_double), ("max_launch_rays", C.c_uint64),
+        ("tune", C.c_int32), ("reserved0", C.c_int32),
     ]
 
 
@@ -75,8 +76,9 @@ class FieldParams(C.Structure):
         ("n_star_in", C.c_int64), ("l0", C.c_double),
         ("n1x", C.c_int64), ("n1y", C.c_int64), ("n2x", C.c_int64), ("n2y", C.c_int64),
         ("N1x", C.c_int64), ("N1y", C.c_int64), ("N2x", C.c_int64), ("N2y", C.c_int64),
-        ("taylor_p", C.c_int32), ("l2_sub", C.c_int32), ("precision", C.c_int32),
-        ("deposit", C.c_int32), ("max_near", C.c_int32), ("build", C.c_int32),
+        ("taylor_p", C.c_int32), ("l2_sub_x", C.c_int32), ("l2_sub_y", C.c_int32),
+        ("precision", C.c_int32), ("deposit", C.c_int32), ("max_near", C.c_int32),
+        ("build", C.c_int32), ("tuned", C.c_int32),
         ("far_bound", C.c_double), ("mu_per_count", C.c_double),
     ]
 
@@ -209,7 +211,8 @@ def ml_field_destroy(field):
 # ---- convenience wrapper -------------------------------------------------------
 
 def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_AUTO,
-              taylor_p=0, far_tol=0.0, l1=None, l2_sub=0, max_launch_rays=0, lens_arrays=None):
+              taylor_p=0, far_tol=0.0, l1=None, l2_sub=(0, 0), max_launch_rays=0, lens_arrays=None,
+              tune=False):
     """ml_field_desc for an inputs.Workload (lens arrays from host numpy)."""
     w = workload
     lx, ly, lm = lens_arrays if lens_arrays is not None else (w.lenses.x, w.lenses.y, w.lenses.m)
@@ -234,7 +237,8 @@ def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_A
     d.map_nx, d.map_ny = w.map_n
     if l1 is not None:
         d.l1_x, d.l1_y = l1
-    d.l2_sub = l2_sub
+    d.l2_sub_x, d.l2_sub_y = l2_sub
+    d.tune = 1 if tune else 0
     d.far_tol = far_tol
     d.max_launch_rays = max_launch_rays
     d._keep = (lx, ly, lm)       # keep the arrays alive until create returns

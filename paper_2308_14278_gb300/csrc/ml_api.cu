@@ -46,6 +46,7 @@ struct ml_field {
     uint64_t max_launch_rays = 0;
     uint64_t rays_asked = 0, launches = 0;
     int64_t n_lens = 0;
+    int32_t tuned = 0;
     // device buffers
     double *d_x = nullptr, *d_y = nullptr, *d_m = nullptr;
     int32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_cursor = nullptr;
@@ -153,12 +154,13 @@ ml_status derive_geometry(const ml_field_desc &d, const std::vector<double> &hx,
     g.l0 = n_in > 0 ? sqrt(lix * liy / (double)n_in) : INFINITY;
     double l1x = d.l1_x > 0.0 ? d.l1_x : std::min(g.l0, lix / 10.0);   // Eq. 10
     double l1y = d.l1_y > 0.0 ? d.l1_y : std::min(g.l0, liy / 10.0);
-    g.l2sub = d.l2_sub > 0 ? d.l2_sub : 20;
-    double l2x = l1x / g.l2sub, l2y = l1y / g.l2sub;
+    g.l2sx = d.l2_sub_x > 0 ? d.l2_sub_x : 20;
+    g.l2sy = d.l2_sub_y > 0 ? d.l2_sub_y : 20;
+    double l2x = l1x / g.l2sx, l2y = l1y / g.l2sy;
     g.n2x = std::max<int64_t>(1, round_half_up(l2x / g.l3x));
     g.n2y = std::max<int64_t>(1, round_half_up(l2y / g.l3y));
-    g.n1x = g.l2sub * g.n2x;
-    g.n1y = g.l2sub * g.n2y;
+    g.n1x = g.l2sx * g.n2x;
+    g.n1y = g.l2sy * g.n2y;
     g.N1x = (g.n3x + g.n1x - 1) / g.n1x;
     g.N1y = (g.n3y + g.n1y - 1) / g.n1y;
     g.N2x = (g.n3x + g.n2x - 1) / g.n2x;
@@ -201,7 +203,8 @@ ml_status validate(const ml_field_desc *d)
         return fail(ML_ERR_INVALID_ARG, "sheet disc must be finite with radius >= 0");
     if (d->taylor_p < 0 || d->taylor_p > PMAX)
         return fail(ML_ERR_INVALID_ARG, "taylor_p must be in [0, 16]");
-    if (d->l2_sub < 0 || d->l2_sub > 4096) return fail(ML_ERR_INVALID_ARG, "bad l2_sub");
+    if (d->l2_sub_x < 0 || d->l2_sub_x > 4096 || d->l2_sub_y < 0 || d->l2_sub_y > 4096)
+        return fail(ML_ERR_INVALID_ARG, "bad l2_sub_x / l2_sub_y");
     if (d->l1_x < 0.0 || d->l1_y < 0.0) return fail(ML_ERR_INVALID_ARG, "negative l1 size");
     if (d->far_tol < 0.0) return fail(ML_ERR_INVALID_ARG, "negative far_tol");
     return ML_OK;
@@ -454,8 +457,8 @@ ml_status ml_shoot_rays(ml_field *f, uint64_t ray_begin, uint64_t ray_end, void 
     cudaStream_t s = (cudaStream_t)stream;
     ShootArgs a = make_args(f);
     const int64_t gpb = (g.n1y + 31) / 32;
-    const int64_t l2_per_cc = std::max<int64_t>(1, std::min<int64_t>(g.l2sub, (2048 + g.n2x - 1) / g.n2x));
-    const int64_t cc_per_l1 = (g.l2sub + l2_per_cc - 1) / l2_per_cc;
+    const int64_t l2_per_cc = std::max<int64_t>(1, std::min<int64_t>(g.l2sx, (2048 + g.n2x - 1) / g.n2x));
+    const int64_t cc_per_l1 = (g.l2sx + l2_per_cc - 1) / l2_per_cc;
     for (uint64_t b = ray_begin; b < ray_end;) {
         uint64_t e = std::min<uint64_t>(ray_end, b + f->max_launch_rays);
         a.ray_begin = (int64_t)b;
@@ -599,7 +602,8 @@ ml_status ml_field_info(const ml_field *f, ml_field_params *out)
     out->n_star_in = g.n_star_in; out->l0 = g.l0;
     out->n1x = g.n1x; out->n1y = g.n1y; out->n2x = g.n2x; out->n2y = g.n2y;
     out->N1x = g.N1x; out->N1y = g.N1y; out->N2x = g.N2x; out->N2y = g.N2y;
-    out->taylor_p = g.p; out->l2_sub = g.l2sub;
+    out->taylor_p = g.p; out->l2_sub_x = g.l2sx; out->l2_sub_y = g.l2sy;
+    out->tuned = f->tuned;
     out->precision = g.precision; out->deposit = g.deposit;
     out->max_near = f->max_near;
     out->build = f->build_used;

@@ -159,8 +159,8 @@ __global__ void k_p_bound(Geo g, LensTable L, double *__restrict__ bound)
     int64_t c = blockIdx.x;
     int64_t c1x = c % g.N1x, c1y = c / g.N1x;
     int64_t ex = c1x + 1, ey = c1y + 1, NE = g.NEx * g.NEy;
-    int64_t a2x = c1x * g.l2sub, b2x = min((c1x + 1) * (int64_t)g.l2sub, g.N2x) - 1;
-    int64_t a2y = c1y * g.l2sub, b2y = min((c1y + 1) * (int64_t)g.l2sub, g.N2y) - 1;
+    int64_t a2x = c1x * g.l2sx, b2x = min((c1x + 1) * (int64_t)g.l2sx, g.N2x) - 1;
+    int64_t a2y = c1y * g.l2sy, b2y = min((c1y + 1) * (int64_t)g.l2sy, g.N2y) - 1;
     double x0 = g.rx0 + (a2x + 0.5) * g.l2x, x1 = g.rx0 + (b2x + 0.5) * g.l2x;
     double y0 = g.ry0 + (a2y + 0.5) * g.l2y, y1 = g.ry0 + (b2y + 0.5) * g.l2y;
     double hx = 0.5 * (double)(g.n2x - 1) * g.l3x, hy = 0.5 * (double)(g.n2y - 1) * g.l3y;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128) k_coeffs_direct(Geo g, LensTable L, doubl
     int64_t c2x = nd % g.N2x, c2y = nd / g.N2x;
     double zx = g.rx0 + ((double)c2x + 0.5) * g.l2x;
     double zy = g.ry0 + ((double)c2y + 0.5) * g.l2y;
-    int64_t ex = c2x / g.l2sub + 1, ey = c2y / g.l2sub + 1, NE = g.NEx * g.NEy;
+    int64_t ex = c2x / g.l2sx + 1, ey = c2y / g.l2sy + 1, NE = g.NEx * g.NEy;
     const int p = g.p;
     double cr[PMAX + 1], ci[PMAX + 1];
 #pragma unroll
@@ -340,8 +340,8 @@ __host__ __device__ inline Hier hier_of(const Geo &g)
     h.NBx = (g.N1x + h.bxn - 1) / h.bxn;
     h.NBy = (g.N1y + h.byn - 1) / h.byn;
     double ar = g.l1x / g.l1y;
-    h.nsx = ar >= 1.0 ? (int64_t)fmin((double)g.l2sub, floor(ar + 0.5)) : 1;
-    h.nsy = ar < 1.0 ? (int64_t)fmin((double)g.l2sub, floor(1.0 / ar + 0.5)) : 1;
+    h.nsx = ar >= 1.0 ? (int64_t)fmin((double)g.l2sx, floor(ar + 0.5)) : 1;
+    h.nsy = ar < 1.0 ? (int64_t)fmin((double)g.l2sy, floor(1.0 / ar + 0.5)) : 1;
     if (h.nsx < 1) h.nsx = 1;
     if (h.nsy < 1) h.nsy = 1;
     h.hB = 0.5 * sqrt((double)(h.bxn * h.bxn) * g.l1x * g.l1x + (double)(h.byn * h.byn) * g.l1y * g.l1y);
@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
     const int64_t cx = cell % g.N1x, cy = cell / g.N1x;
     const int64_t sa = sb % h.nsx, sbb = sb / h.nsx;
     // node columns [ua, ub) and rows [va, vb) of the sub-block inside the cell
-    const int64_t ua = (sa * g.l2sub + h.nsx - 1) / h.nsx, ub = ((sa + 1) * g.l2sub + h.nsx - 1) / h.nsx;
-    const int64_t va = (sbb * g.l2sub + h.nsy - 1) / h.nsy, vb = ((sbb + 1) * g.l2sub + h.nsy - 1) / h.nsy;
+    const int64_t ua = (sa * g.l2sx + h.nsx - 1) / h.nsx, ub = ((sa + 1) * g.l2sx + h.nsx - 1) / h.nsx;
+    const int64_t va = (sbb * g.l2sy + h.nsy - 1) / h.nsy, vb = ((sbb + 1) * g.l2sy + h.nsy - 1) / h.nsy;
     const double zx = g.rx0 + (double)cx * g.l1x + 0.5 * (double)(ua + ub) * g.l2x;
     const double zy = g.ry0 + (double)cy * g.l1y + 0.5 * (double)(va + vb) * g.l2y;
     const double hs = 0.5 * sqrt((double)((ub - ua) * (ub - ua)) * g.l2x * g.l2x +
@@ -523,11 +523,11 @@ __global__ void __launch_bounds__(128) k_node_shift(Geo g, Hier h, const double 
     int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (node >= g.N2x * g.N2y) return;
     int64_t c2x = node % g.N2x, c2y = node / g.N2x;
-    int64_t cx = c2x / g.l2sub, cy = c2y / g.l2sub;
-    int64_t u = c2x - cx * g.l2sub, v = c2y - cy * g.l2sub;
-    int64_t sa = u * h.nsx / g.l2sub, sbb = v * h.nsy / g.l2sub;
-    int64_t ua = (sa * g.l2sub + h.nsx - 1) / h.nsx, ub = ((sa + 1) * g.l2sub + h.nsx - 1) / h.nsx;
-    int64_t va = (sbb * g.l2sub + h.nsy - 1) / h.nsy, vb = ((sbb + 1) * g.l2sub + h.nsy - 1) / h.nsy;
+    int64_t cx = c2x / g.l2sx, cy = c2y / g.l2sy;
+    int64_t u = c2x - cx * g.l2sx, v = c2y - cy * g.l2sy;
+    int64_t sa = u * h.nsx / g.l2sx, sbb = v * h.nsy / g.l2sy;
+    int64_t ua = (sa * g.l2sx + h.nsx - 1) / h.nsx, ub = ((sa + 1) * g.l2sx + h.nsx - 1) / h.nsx;
+    int64_t va = (sbb * g.l2sy + h.nsy - 1) / h.nsy, vb = ((sbb + 1) * g.l2sy + h.nsy - 1) / h.nsy;
     double hs = 0.5 * sqrt((double)((ub - ua) * (ub - ua)) * g.l2x * g.l2x +
                            (double)((vb - va) * (vb - va)) * g.l2y * g.l2y);
     // e = (z_node - z_s)/hs
@@ -589,7 +589,7 @@ void hier_ratios(const Geo &g, double *box_ratio, double *sub_ratio)
     double bw = (double)h.bxn * g.l1x, bh = (double)h.byn * g.l1y;
     double rb = h.hB + 0.5 * sqrt(g.l2x * g.l2x + g.l2y * g.l2y);
     *box_ratio = rb / (1.5 * fmin(bw, bh));
-    double sw = ceil((double)g.l2sub / h.nsx) * g.l2x, sh = ceil((double)g.l2sub / h.nsy) * g.l2y;
+    double sw = ceil((double)g.l2sx / h.nsx) * g.l2x, sh = ceil((double)g.l2sy / h.nsy) * g.l2y;
     double rs = 0.5 * sqrt(sw * sw + sh * sh) + 0.5 * sqrt(g.l2x * g.l2x + g.l2y * g.l2y);
     double dmin = fmin(g.l1x + 0.5 * (g.l1x - sw), g.l1y + 0.5 * (g.l1y - sh));
     *sub_ratio = rs / dmin;

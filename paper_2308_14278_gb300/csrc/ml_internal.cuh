@@ -26,7 +26,7 @@ struct Geo {
     int32_t mnx, mny;
     int64_t n_star_in;
     double l0;
-    int32_t l2sub, p;
+    int32_t l2sx, l2sy, p;      // level-2 cells per level-1 side; Taylor order
     int64_t n1x, n1y, n2x, n2y;     // rays per level-1 / level-2 cell side
     int64_t N1x, N1y, N2x, N2y;     // cells across the lattice
     double l1x, l1y, l2x, l2y;      // = n1 * l3, n2 * l3

@@ -192,8 +192,8 @@ __device__ __forceinline__ bool decode_task(const ShootArgs &a, int64_t t, TaskS
     ts.rows_end = min(min(ts.row0 + 32, (c1y + 1) * g.n1y), g.n3y);
     ts.c1x = cc / a.cc_per_l1;
     int64_t sub = cc % a.cc_per_l1;
-    ts.c2a = ts.c1x * g.l2sub + sub * a.l2_per_cc;
-    ts.c2b = min(min(ts.c2a + a.l2_per_cc, (ts.c1x + 1) * (int64_t)g.l2sub), g.N2x);
+    ts.c2a = ts.c1x * g.l2sx + sub * a.l2_per_cc;
+    ts.c2b = min(min(ts.c2a + a.l2_per_cc, (ts.c1x + 1) * (int64_t)g.l2sx), g.N2x);
     return ts.row0 < ts.rows_end && ts.c2a < ts.c2b;
 }
 

@@ -59,7 +59,7 @@ def test_abi_version_and_error_string(libpath):
 
 @pytest.mark.parametrize("bad", [
     dict(map_nx=0), dict(map_x1=-2.0), dict(n_lens=5), dict(precision=7), dict(deposit=3),
-    dict(taylor_p=17), dict(kappa_star=-1.0), dict(sheet_radius=-1.0), dict(l2_sub=-1),
+    dict(taylor_p=17), dict(kappa_star=-1.0), dict(sheet_radius=-1.0), dict(l2_sub_x=-1), dict(l2_sub_y=5000),
 ])
 def test_descriptor_validation_without_gpu(libpath, bad):
     lib = ml.load(libpath)

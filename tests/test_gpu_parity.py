@@ -181,10 +181,12 @@ def _mixed_case(seed=5, kappa=0.40, gamma=0.45, ks=0.05, n_av=60):
     return inputs.Workload("mixed", lf, kappa, gamma, ks, (0.0, 0.0, r), box, npx, n_av=n_av)
 
 
-def test_mixed_trace_deflection_and_bins(ml):
+@pytest.mark.parametrize("l2_sub", [(20, 20), (60, 20), (20, 40)])
+def test_mixed_trace_deflection_and_bins(ml, l2_sub):
     w = _mixed_case()
-    f = _field(ml, w, precision=ml.PREC_MIXED)
-    g = _geometry(w, f)
+    f = _field(ml, w, precision=ml.PREC_MIXED, l2_sub=l2_sub)
+    assert (f.info["l2_sub_x"], f.info["l2_sub_y"]) == l2_sub
+    g = oracle.geometry_of(w, p=f.info["taylor_p"], l2_sub=l2_sub[0], l2_sub_y=l2_sub[1])
     _check_geometry(f, g)
     assert f.info["far_bound"] <= 1e-7
     idx = np.unique(np.random.default_rng(1).integers(0, g.n_rays, 40000))

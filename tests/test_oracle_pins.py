@@ -139,14 +139,15 @@ def test_mirror_symmetry(axis):
 
 # -- P6: the far-field Taylor series against the direct sum ------------------
 
-@pytest.mark.parametrize("p", [1, 2, 3, 5])
-def test_interp_within_truncation_bound(p):
+@pytest.mark.parametrize("p,l2y", [(1, 20), (2, 20), (3, 20), (5, 20), (3, 7), (4, 40)])
+def test_interp_within_truncation_bound(p, l2y):
     """|beta_interp - beta_direct| <= sum_far m rho^{p+1} / (r^{p+1} (r - rho)),
     the tail of the geometric series of 1/(z_k - z), for every sampled ray;
     the bound is nearly attained, so a wrong coefficient would break it."""
     lf = inputs.lens_disc(40, 6.0, 3, "lognormal")
     g = _geom(0.3, 0.2, 0.05, lf.x, lf.y, (0, 0, 6.0), (-2, -2, 2, 2), (64, 64),
-              ray_box=(-4, -3, 4, 3), ray_n=(400, 300), p=p)
+              ray_box=(-4, -3, 4, 3), ray_n=(400, 300), p=p, l2_sub_y=l2y)
+    assert g.n1y == l2y * g.n2y
     idx = np.arange(0, g.n_rays, 61)
     bd, fd = oracle.beta_direct(g, lf.x, lf.y, lf.m, idx)
     bi, fi = oracle.beta_interp(g, lf.x, lf.y, lf.m, idx)
