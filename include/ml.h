@@ -205,6 +205,32 @@ ml_status ml_light_curves(ml_field *f, const double *tracks, int32_t n_tracks, i
                           double sigma_px, float *out, int32_t out_is_device, void *stream);
 
 /*
+ * ml_light_curves_noalloc - the light curves of ml_light_curves, computed
+ * without allocating any memory.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory once they are
+ * running, for example a process that reserved its whole memory budget at
+ * start-up and runs close to it, or a timing-critical loop in which an
+ * allocation's implicit device synchronisation or a possible out-of-memory
+ * failure is unacceptable.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch (the Gaussian taps and a device copy of the
+ * tracks) lives in a fixed array inside the library, ML_NOALLOC_MAX_TRACKS
+ * tracks (about 513 KB), which every device that loads the library holds
+ * until the process exits.
+ *  tracks:  host, n_tracks x (x0, y0, x1, y1) in map pixel coordinates.
+ *  out:     DEVICE buffer of n_tracks x n_samples float32 (caller-owned).
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (different streams without ordering)
+ * race, so order them on one stream.  Nothing in the array needs clearing:
+ * each call overwrites the part it uses.
+ * Errors: ML_ERR_INVALID_ARG for n_tracks > ML_NOALLOC_MAX_TRACKS, counts < 1,
+ * sigma_px outside (0, 16] or NULL pointers; ML_ERR_CUDA.
+ */
+#define ML_NOALLOC_MAX_TRACKS 16384
+ml_status ml_light_curves_noalloc(ml_field *f, const double *tracks, int32_t n_tracks,
+                                  int32_t n_samples, double sigma_px, float *out, void *stream);
+
+/*
  * ml_trace_rays - source positions of single rays by exactly the arithmetic
  * the shooting kernel of the field's precision mode uses (for checking).
  *  ray_idx: device, n linear ray indices (each < n_rays_x * n_rays_y).

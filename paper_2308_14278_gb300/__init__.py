@@ -36,7 +36,9 @@ STATUS = {0: "ML_OK", 1: "ML_ERR_INVALID_ARG", 2: "ML_ERR_OOM", 3: "ML_ERR_CUDA"
 # every symbol include/ml.h declares
 EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays",
            "ml_magnification_map", "ml_light_curves", "ml_trace_rays", "ml_field_clear",
-           "ml_field_stats", "ml_field_info", "ml_field_abort", "ml_field_destroy")
+           "ml_field_stats", "ml_field_info", "ml_field_abort", "ml_field_destroy",
+           "ml_light_curves_noalloc")
+NOALLOC_MAX_TRACKS = 16384
 
 
 class MLError(RuntimeError):
@@ -109,6 +111,7 @@ def load(path: str | None = None):
         "ml_magnification_map": ([V, C.c_int32, V, C.c_int32, V], st),
         "ml_light_curves": ([V, V, C.c_int32, C.c_int32, C.c_double, V, C.c_int32, V], st),
         "ml_trace_rays": ([V, V, C.c_int64, V, V, V], st),
+        "ml_light_curves_noalloc": ([V, V, C.c_int32, C.c_int32, C.c_double, V, V], st),
         "ml_field_clear": ([V, V], st),
         "ml_field_stats": ([V, P(C.c_uint64), V], st),
         "ml_field_info": ([V, P(FieldParams)], st),
@@ -174,6 +177,14 @@ def ml_light_curves(field, tracks, n_samples: int, sigma_px: float, out, stream=
     else:
         _check(load().ml_light_curves(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
                                       _dptr(out), 1, _stream(stream)))
+
+
+def ml_light_curves_noalloc(field, tracks, n_samples: int, sigma_px: float, out, stream=None):
+    """Light curves into a device tensor without any allocation in the
+    library (for callers that must not allocate device memory; see ml.h)."""
+    tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
+    _check(load().ml_light_curves_noalloc(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
+                                          _dptr(out), _stream(stream)))
 
 
 def ml_trace_rays(field, ray_idx, beta, pix, stream=None):

@@ -557,6 +557,25 @@ ml_status ml_light_curves(ml_field *f, const double *tracks, int32_t n_tracks, i
     return ML_OK;
 }
 
+ml_status ml_light_curves_noalloc(ml_field *f, const double *tracks, int32_t n_tracks,
+                                  int32_t n_samples, double sigma_px, float *out, void *stream)
+{
+    if (!f || !tracks || !out) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (n_tracks < 1 || n_samples < 1) return fail(ML_ERR_INVALID_ARG, "need >= 1 track and sample");
+    if (n_tracks > ML_NOALLOC_MAX_TRACKS)
+        return fail(ML_ERR_INVALID_ARG, "n_tracks " + std::to_string(n_tracks) +
+                                            " exceeds ML_NOALLOC_MAX_TRACKS (" +
+                                            std::to_string(ML_NOALLOC_MAX_TRACKS) + ")");
+    if (!(sigma_px > 0.0) || sigma_px > 16.0) return fail(ML_ERR_INVALID_ARG, "sigma_px must be in (0, 16]");
+    for (int q = 0; q < 4 * n_tracks; ++q)
+        if (!is_fin(tracks[q])) return fail(ML_ERR_INVALID_ARG, "track coordinates must be finite");
+    const Geo &g = f->g;
+    const double scale = (g.l3x * g.l3y) / (g.dpx * g.dpy);
+    ML_CK(launch_light_curves_noalloc(g, f->d_map_u32, f->d_map_f32, scale, tracks, n_tracks,
+                                      n_samples, sigma_px, out, (cudaStream_t)stream));
+    return ML_OK;
+}
+
 ml_status ml_field_clear(ml_field *f, void *stream)
 {
     if (!f) return fail(ML_ERR_INVALID_ARG, "field is NULL");

@@ -97,6 +97,9 @@ cudaError_t launch_mu(const Geo &g, const uint32_t *cu, const float *cf, int wan
 cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *cf, double scale,
                                 const double *tracks, int n_tracks, int n_samples,
                                 double sigma_px, float *out, cudaStream_t s);
+cudaError_t launch_light_curves_noalloc(const Geo &g, const uint32_t *cu, const float *cf,
+                                        double scale, const double *tracks_host, int n_tracks,
+                                        int n_samples, double sigma_px, float *out, cudaStream_t s);
 int mixed_p_supported(int p);     // the Taylor order the mixed kernel will use for p
 
 // ---- shared device arithmetic ---------------------------------------------

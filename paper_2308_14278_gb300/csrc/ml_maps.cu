@@ -4,6 +4,8 @@
 
 #include <math.h>
 
+#include <mutex>
+
 namespace ml {
 
 // mu_ij = N_ij * S_I / S_S.  Vectorised: four pixels per thread per step,
@@ -133,6 +135,74 @@ __global__ void k_light_curves(Geo g, const uint32_t *__restrict__ cu, const flo
         acc += wc * conv;
     }
     out[q] = (float)(acc * scale);
+}
+
+static int gaussian_taps(double sigma_px, float taps[129])
+{
+    int h = (int)floor(4.0 * sigma_px);
+    if (h > 64) return -1;
+    double sum = 0.0, w[129];
+    for (int t = -h; t <= h; ++t) {
+        w[t + h] = exp(-0.5 * ((double)t / sigma_px) * ((double)t / sigma_px));
+        sum += w[t + h];
+    }
+    for (int t = 0; t <= 2 * h; ++t) taps[t] = (float)(w[t] / sum);
+    return h;
+}
+
+// ---- light curves without allocation -----------------------------------------
+//
+// Scratch for the allocation-free light-curve entry point: the Gaussian taps
+// (first 1024 bytes) and the device copy of the tracks (32 bytes each).  It is
+// a fixed array in the library's device image, present on every device that
+// loads the library until the process exits.  Every call overwrites what it
+// uses, so nothing in it has to start at zero; calls share it, so two calls
+// that overlap on the GPU race (order them on one stream).
+constexpr size_t LC_TAPS_BYTES = 1024;
+static __device__ __align__(256) unsigned char g_lc_scratch[LC_TAPS_BYTES + 32 * ML_NOALLOC_MAX_TRACKS];
+
+// Device address of g_lc_scratch, looked up once per device (with that device
+// current): in host code the array's name is only a host-side stand-in.
+static cudaError_t lc_scratch_address(unsigned char **out)
+{
+    static std::mutex mu;
+    static unsigned char *addr[1024] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 1024) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_lc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_light_curves_noalloc(const Geo &g, const uint32_t *cu, const float *cf,
+                                        double scale, const double *tracks_host, int n_tracks,
+                                        int n_samples, double sigma_px, float *out, cudaStream_t s)
+{
+    float taps[129];
+    int h = gaussian_taps(sigma_px, taps);
+    if (h < 0 || n_tracks > ML_NOALLOC_MAX_TRACKS) return cudaErrorInvalidValue;
+    unsigned char *base = nullptr;
+    cudaError_t e = lc_scratch_address(&base);
+    if (e != cudaSuccess) return e;
+    float *d_taps = reinterpret_cast<float *>(base);
+    double *d_tracks = reinterpret_cast<double *>(base + LC_TAPS_BYTES);
+    e = cudaMemcpyAsync(d_taps, taps, sizeof(float) * (2 * h + 1), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_tracks, tracks_host, sizeof(double) * 4 * (size_t)n_tracks,
+                        cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    int64_t n = (int64_t)n_tracks * n_samples;
+    k_light_curves<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, cu, cf, scale, d_tracks, n_tracks,
+                                                               n_samples, h, d_taps, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *cf, double scale,
