@@ -268,6 +268,53 @@ ml_status ml_field_abort(ml_field *f, int32_t on);
 /* ml_field_destroy - free the field and its device memory.  NULL is a no-op. */
 ml_status ml_field_destroy(ml_field *f);
 
+/*
+ * Batched maps (many heterogeneous magnification maps in one persistent
+ * launch; the paper's statistics use 80 maps and 800 light curves, §4.2).
+ *
+ * ml_batch_create - create n fields from descs[0..n) (ML_PREC_MIXED and
+ * ML_DEPOSIT_NGP only).  Each field's Taylor order is planned from its own
+ * truncation bound; all are then built with the largest, so that one kernel
+ * serves every map (a higher order only lowers the error).  With
+ * tracks_per_map > 0, `tracks` (host, n x tracks_per_map x 4, map pixel
+ * coordinates) are kept on the device for the light curves of each run.
+ * Synchronises `stream`.  Errors as ml_field_create, plus ML_ERR_UNSUPPORTED
+ * for other modes.
+ */
+typedef struct ml_batch ml_batch;
+ml_status ml_batch_create(const ml_field_desc *descs, int32_t n, int32_t tracks_per_map,
+                          const double *tracks, int32_t n_samples, double sigma_px, void *stream,
+                          ml_batch **out);
+
+/*
+ * ml_batch_run - one step of the whole batch, ordered on `stream`: zero all
+ * maps and counters, shoot every ray of every map in ONE persistent kernel
+ * launch (warps take tasks of all maps from one queue), convert every map to
+ * mu (Eq. 12) into the batch's buffers and compute the light curves.  With
+ * use_graph != 0 the step is captured once into a CUDA graph on the batch's
+ * internal stream and replayed by every later call.
+ */
+ml_status ml_batch_run(ml_batch *b, int32_t use_graph, void *stream);
+
+/* ml_batch_field - borrowed handle of map i (owned by the batch: do not
+ * destroy it); usable with ml_field_stats, ml_field_info, ml_trace_rays,
+ * ml_magnification_map, ml_light_curves. */
+ml_status ml_batch_field(ml_batch *b, int32_t i, ml_field **out);
+
+/* ml_batch_mu - copy map i's mu (float32, from the last run) into out
+ * (device or host memory; host output synchronises `stream`). */
+ml_status ml_batch_mu(ml_batch *b, int32_t i, float *out, int32_t out_is_device, void *stream);
+
+/* ml_batch_curves - copy all light curves of the last run, n x
+ * tracks_per_map x n_samples float32, into out (device or host). */
+ml_status ml_batch_curves(ml_batch *b, float *out, int32_t out_is_device, void *stream);
+
+/* ml_batch_abort - raise or lower the batch's abort flag (see ml_field_abort). */
+ml_status ml_batch_abort(ml_batch *b, int32_t on);
+
+/* ml_batch_destroy - free the batch and its fields.  NULL is a no-op. */
+ml_status ml_batch_destroy(ml_batch *b);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *ml_last_error(void);
 

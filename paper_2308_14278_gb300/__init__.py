@@ -37,7 +37,8 @@ STATUS = {0: "ML_OK", 1: "ML_ERR_INVALID_ARG", 2: "ML_ERR_OOM", 3: "ML_ERR_CUDA"
 EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays",
            "ml_magnification_map", "ml_light_curves", "ml_trace_rays", "ml_field_clear",
            "ml_field_stats", "ml_field_info", "ml_field_abort", "ml_field_destroy",
-           "ml_light_curves_noalloc")
+           "ml_light_curves_noalloc", "ml_batch_create", "ml_batch_run", "ml_batch_field",
+           "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -112,6 +113,14 @@ def load(path: str | None = None):
         "ml_light_curves": ([V, V, C.c_int32, C.c_int32, C.c_double, V, C.c_int32, V], st),
         "ml_trace_rays": ([V, V, C.c_int64, V, V, V], st),
         "ml_light_curves_noalloc": ([V, V, C.c_int32, C.c_int32, C.c_double, V, V], st),
+        "ml_batch_create": ([P(FieldDesc), C.c_int32, C.c_int32, V, C.c_int32, C.c_double, V,
+                             P(V)], st),
+        "ml_batch_run": ([V, C.c_int32, V], st),
+        "ml_batch_field": ([V, C.c_int32, P(V)], st),
+        "ml_batch_mu": ([V, C.c_int32, V, C.c_int32, V], st),
+        "ml_batch_curves": ([V, V, C.c_int32, V], st),
+        "ml_batch_abort": ([V, C.c_int32], st),
+        "ml_batch_destroy": ([V], st),
         "ml_field_clear": ([V, V], st),
         "ml_field_stats": ([V, P(C.c_uint64), V], st),
         "ml_field_info": ([V, P(FieldParams)], st),
@@ -313,6 +322,76 @@ class Field:
     def close(self):
         if self.h is not None:
             ml_field_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many maps shot in one persistent launch (ml_batch_*); fields are views."""
+
+    def __init__(self, descs, tracks=None, n_samples=0, sigma_px=0.5, stream=None):
+        arr = (FieldDesc * len(descs))(*descs)
+        self._descs = descs
+        tpm = 0
+        tr_ptr = None
+        if tracks is not None:
+            tr = np.ascontiguousarray(tracks, np.float64)
+            tpm = tr.shape[1]
+            self._tracks = tr
+            tr_ptr = tr.ctypes.data
+        h = C.c_void_p()
+        _check(load().ml_batch_create(arr, len(descs), tpm, tr_ptr, n_samples, sigma_px,
+                                      _stream(stream), C.byref(h)))
+        self.h = h
+        self.n = len(descs)
+        self.tpm = tpm
+        self.n_samples = n_samples
+        self.fields = []
+        for i in range(self.n):
+            fh = C.c_void_p()
+            _check(load().ml_batch_field(h, i, C.byref(fh)))
+            self.fields.append(fh)
+
+    def run(self, use_graph=True, stream=None):
+        _check(load().ml_batch_run(self.h, 1 if use_graph else 0, _stream(stream)))
+
+    def info(self, i):
+        return ml_field_info(self.fields[i])
+
+    def stats(self, i, stream=None):
+        return ml_field_stats(self.fields[i], stream)[0]
+
+    def counts(self, i, stream=None):
+        import torch
+        inf = self.info(i)
+        out = torch.empty((inf["map_ny"], inf["map_nx"]), dtype=torch.int32, device="cuda")
+        ml_magnification_map(self.fields[i], MAP_COUNTS_U32, out, stream)
+        return out
+
+    def mu(self, i, stream=None):
+        import torch
+        inf = self.info(i)
+        out = torch.empty((inf["map_ny"], inf["map_nx"]), dtype=torch.float32, device="cuda")
+        _check(load().ml_batch_mu(self.h, i, _dptr(out), 1, _stream(stream)))
+        return out
+
+    def curves(self, stream=None):
+        import torch
+        out = torch.empty((self.n, self.tpm, self.n_samples), dtype=torch.float32, device="cuda")
+        _check(load().ml_batch_curves(self.h, _dptr(out), 1, _stream(stream)))
+        return out
+
+    def abort(self, on=True):
+        _check(load().ml_batch_abort(self.h, 1 if on else 0))
+
+    def close(self):
+        if self.h is not None:
+            _check(load().ml_batch_destroy(self.h))
             self.h = None
 
     def __del__(self):

@@ -7,7 +7,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 using namespace ml;
@@ -47,6 +49,8 @@ struct ml_field {
     uint64_t rays_asked = 0, launches = 0;
     int64_t n_lens = 0;
     int32_t tuned = 0;
+    ml_field_desc desc{};            // parameters (lens pointers cleared)
+    std::vector<double> worst;       // truncation bound per Taylor order (worst level-1 cell)
     // device buffers
     double *d_x = nullptr, *d_y = nullptr, *d_m = nullptr;
     int32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_cursor = nullptr;
@@ -221,7 +225,153 @@ bool rays_inside_sheet(const Geo &g)
     return true;
 }
 
-ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
+// ---- level-2 grid autotuner --------------------------------------------------
+//
+// The paper fixes L2 = L1 / 20.  A finer level-2 grid along the long side of
+// the level-1 cells shrinks the expansion radius, so a lower Taylor order meets
+// the same truncation bound, at the price of more nodes to build.  The tuner
+// evaluates a few (l2_sub_x, l2_sub_y) candidates with their rigorous bound
+// (one p_bound launch each) and a cost model of GB300 measurements:
+//   time = rays * ray_cost(P) + nodes * (P + 1) * node_cost.
+
+// Shooting cost per ray of the mixed kernel on the whole GB300 (ns), by the
+// compiled Taylor order P, measured at the paper-scale field (1.36 near lenses
+// per ray) for P = 4, 5, 8 and interpolated/extrapolated linearly elsewhere.
+double ray_cost_ns(int P)
+{
+    switch (P) {
+    case 1: return 1.60;
+    case 2: return 1.62;
+    case 3: return 1.64;
+    case 4: return 1.655;
+    case 5: return 1.68;
+    case 6: return 1.76;
+    case 8: return 1.915;
+    case 10: return 2.07;
+    case 12: return 2.23;
+    default: return 2.55;
+    }
+}
+constexpr double kNodeCostNs = 1.1;   // hierarchical build and node record, per node and coefficient
+
+struct GridChoice {
+    int sx = 20, sy = 20, p = 0;
+    double cost = 0.0;
+};
+
+uint64_t mix64(uint64_t h, uint64_t v)
+{
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
+uint64_t tune_key(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
+                  const std::vector<double> &hm)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mixd = [&](double v) { uint64_t u; memcpy(&u, &v, 8); h = mix64(h, u); };
+    mixd(d.kappa); mixd(d.gamma); mixd(d.kappa_star); mixd(d.sheet_cx); mixd(d.sheet_cy);
+    mixd(d.sheet_radius); mixd(d.ray_x0); mixd(d.ray_y0); mixd(d.ray_x1); mixd(d.ray_y1);
+    mixd(d.n_av); mixd(d.map_x0); mixd(d.map_y0); mixd(d.map_x1); mixd(d.map_y1);
+    mixd(d.l1_x); mixd(d.l1_y); mixd(d.far_tol);
+    h = mix64(h, (uint64_t)d.n_rays_x); h = mix64(h, (uint64_t)d.n_rays_y);
+    h = mix64(h, (uint64_t)d.map_nx); h = mix64(h, (uint64_t)d.map_ny);
+    h = mix64(h, (uint64_t)d.taylor_p); h = mix64(h, (uint64_t)hx.size());
+    for (size_t k = 0; k < hx.size(); ++k) { mixd(hx[k]); mixd(hy[k]); mixd(hm[k]); }
+    return h;
+}
+
+std::mutex g_tune_mu;
+std::unordered_map<uint64_t, GridChoice> g_tune_cache;
+
+ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
+                    const std::vector<double> &hm, const double *dx, const double *dy, const double *dm,
+                    cudaStream_t s, GridChoice &best)
+{
+    const uint64_t key = tune_key(d, hx, hy, hm);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { best = it->second; return ML_OK; }
+    }
+    const int64_t n = (int64_t)hx.size();
+    Geo g0;
+    ml_status st = derive_geometry(d, hx, hy, g0);
+    if (st != ML_OK) return st;
+    const bool xlong = g0.l1x >= g0.l1y;
+    static const int fine[] = {20, 40, 60, 80};
+    static const int coarse[] = {10, 20};
+    struct Cand { int sx, sy; Geo g; int32_t *cells; int32_t *counts; double *bound; };
+    std::vector<Cand> cands;
+    cudaError_t e = cudaSuccess;
+    for (int a : fine)
+        for (int b : coarse) {
+            Cand c{};
+            c.sx = xlong ? a : b;
+            c.sy = xlong ? b : a;
+            ml_field_desc dc = d;
+            dc.l2_sub_x = c.sx;
+            dc.l2_sub_y = c.sy;
+            if (derive_geometry(dc, hx, hy, c.g) != ML_OK) continue;
+            if (c.g.n2x < 2 || c.g.n2y < 1 || c.g.N2x * c.g.N2y > ((int64_t)1 << 26)) continue;
+            if (c.g.NEx * c.g.NEy >= ((int64_t)1 << 30)) continue;
+            const int64_t NE = c.g.NEx * c.g.NEy;
+            e = cudaMallocAsync((void **)&c.cells, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1), s);
+            if (e == cudaSuccess) e = cudaMallocAsync((void **)&c.counts, sizeof(int32_t) * (size_t)(NE + 1), s);
+            if (e == cudaSuccess)
+                e = cudaMallocAsync((void **)&c.bound, sizeof(double) * (size_t)(c.g.N1x * c.g.N1y * PMAX), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c.counts, 0, sizeof(int32_t) * (size_t)(NE + 1), s);
+            if (e == cudaSuccess) e = launch_lens_cells(c.g, dx, dy, n, c.cells, c.counts, s);
+            if (e == cudaSuccess) {
+                LensTable L;
+                L.x = dx; L.y = dy; L.m = dm; L.cell = c.cells; L.start = nullptr; L.n = n;
+                c.g.p = 1;
+                e = launch_p_bound(c.g, L, c.bound, s);
+            }
+            cands.push_back(c);
+            if (e != cudaSuccess) break;
+        }
+    const double tol = d.far_tol > 0.0 ? d.far_tol : 1e-7;
+    const double rays = (double)g0.n3x * (double)g0.n3y;
+    bool found = false;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (Cand &c : cands) {
+        if (e != cudaSuccess) break;
+        std::vector<double> bound((size_t)(c.g.N1x * c.g.N1y * PMAX));
+        e = cudaMemcpy(bound.data(), c.bound, bound.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) break;
+        int p = d.taylor_p;
+        if (p == 0) {
+            p = PMAX;
+            for (int q = 1; q <= PMAX; ++q) {
+                double w = 0.0;
+                for (size_t k = 0; k < bound.size() / PMAX; ++k) w = std::max(w, bound[k * PMAX + q - 1]);
+                if (w <= tol) { p = q; break; }
+            }
+        }
+        const int P = mixed_p_supported(p);
+        const double nodes = (double)c.g.N2x * (double)c.g.N2y;
+        const double cost = rays * ray_cost_ns(P) + nodes * (P + 1) * kNodeCostNs;
+        if (!found || cost < best.cost) {
+            best.sx = c.sx; best.sy = c.sy; best.p = P; best.cost = cost;
+            found = true;
+        }
+    }
+    for (Cand &c : cands) {
+        if (c.cells) cudaFreeAsync(c.cells, s);
+        if (c.counts) cudaFreeAsync(c.counts, s);
+        if (c.bound) cudaFreeAsync(c.bound, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "grid autotuner");
+    if (!found) { best = GridChoice(); return ML_OK; }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+    return ML_OK;
+}
+
+// Plan: device check, lenses, (tuned) geometry, binning, near-list size and
+// the truncation bound of every Taylor order; f->worst holds the bound.
+ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
 {
     ML_CK(cudaGetDevice(&f->device));
     cudaDeviceProp prop;
@@ -230,6 +380,8 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
         return fail(ML_ERR_CUDA, "this library is built for sm_103a (GB300); device is sm_" +
                                      std::to_string(prop.major) + std::to_string(prop.minor));
     f->num_sms = prop.multiProcessorCount;
+    f->desc = *d_in;
+    ml_field_desc *d = &f->desc;
 
     const int64_t n = d->n_lens;
     f->n_lens = n;
@@ -248,6 +400,23 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
             if (!is_fin(hx[k]) || !is_fin(hy[k]) || !is_fin(hm[k]))
                 return fail(ML_ERR_INVALID_ARG, "lens " + std::to_string(k) + " is not finite");
     }
+    d->lens_x = d->lens_y = d->lens_m = nullptr;   // copied; the desc keeps only parameters
+    ML_CK(f->alloc(&f->d_x, n, s));
+    ML_CK(f->alloc(&f->d_y, n, s));
+    ML_CK(f->alloc(&f->d_m, n, s));
+    if (n > 0) {
+        ML_CK(cudaMemcpyAsync(f->d_x, hx.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        ML_CK(cudaMemcpyAsync(f->d_y, hy.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        ML_CK(cudaMemcpyAsync(f->d_m, hm.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    if (d->tune && d->precision == ML_PREC_MIXED && d->l2_sub_x == 0 && d->l2_sub_y == 0) {
+        GridChoice gc;
+        ml_status st = tune_grid(*d, hx, hy, hm, f->d_x, f->d_y, f->d_m, s, gc);
+        if (st != ML_OK) return st;
+        d->l2_sub_x = gc.sx;
+        d->l2_sub_y = gc.sy;
+        f->tuned = 1;
+    }
     ml_status st = derive_geometry(*d, hx, hy, f->g);
     if (st != ML_OK) return st;
     Geo &g = f->g;
@@ -264,9 +433,6 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
 
     // lenses, binning (§3.2 Level 1)
     const int64_t NE = g.NEx * g.NEy;
-    ML_CK(f->alloc(&f->d_x, n, s));
-    ML_CK(f->alloc(&f->d_y, n, s));
-    ML_CK(f->alloc(&f->d_m, n, s));
     ML_CK(f->alloc(&f->d_cell, n, s));
     ML_CK(f->alloc(&f->d_count, NE + 1, s));
     ML_CK(f->alloc(&f->d_start, NE + 2, s));
@@ -281,11 +447,6 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
     ML_CK(cudaHostAlloc((void **)&f->h_abort, sizeof(int), cudaHostAllocMapped));
     *f->h_abort = 0;
     ML_CK(cudaHostGetDevicePointer((void **)&f->d_abort, f->h_abort, 0));
-    if (n > 0) {
-        ML_CK(cudaMemcpyAsync(f->d_x, hx.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
-        ML_CK(cudaMemcpyAsync(f->d_y, hy.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
-        ML_CK(cudaMemcpyAsync(f->d_m, hm.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
-    }
     ML_CK(cudaMemsetAsync(f->d_count, 0, (NE + 1) * sizeof(int32_t), s));
     ML_CK(cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s));
     ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
@@ -293,56 +454,72 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
     ML_CK(launch_scan(f->d_count, f->d_start, NE + 1, s));
     ML_CK(launch_scatter(f->d_x, f->d_y, f->d_m, f->d_cell, n, f->d_start, NE + 1, f->d_cursor,
                          f->d_sx, f->d_sy, f->d_sm, f->d_scell, s));
-    LensTable L = f->table();
+    if (!nearfar) return ML_OK;
 
-    if (nearfar) {
-        // largest near list: the 3 x 3 block of each level-1 cell
-        std::vector<int32_t> start(NE + 2);
-        ML_CK(cudaMemcpyAsync(start.data(), f->d_start, (NE + 2) * sizeof(int32_t),
-                              cudaMemcpyDeviceToHost, s));
-        ML_CK(cudaStreamSynchronize(s));
-        int32_t mx = 0;
-        for (int64_t cy = 0; cy < g.N1y; ++cy)
-            for (int64_t cx = 0; cx < g.N1x; ++cx) {
-                int32_t t = 0;
-                for (int64_t ey = cy; ey <= cy + 2; ++ey) {
-                    int64_t b = ey * g.NEx + cx;
-                    t += start[b + 3] - start[b];
-                }
-                mx = std::max(mx, t);
+    // largest near list: the 3 x 3 block of each level-1 cell
+    std::vector<int32_t> start(NE + 2);
+    ML_CK(cudaMemcpyAsync(start.data(), f->d_start, (NE + 2) * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, s));
+    ML_CK(cudaStreamSynchronize(s));
+    int32_t mx = 0;
+    for (int64_t cy = 0; cy < g.N1y; ++cy)
+        for (int64_t cx = 0; cx < g.N1x; ++cx) {
+            int32_t t = 0;
+            for (int64_t ey = cy; ey <= cy + 2; ++ey) {
+                int64_t b = ey * g.NEx + cx;
+                t += start[b + 3] - start[b];
             }
-        f->max_near = mx;
-        if (d->precision == ML_PREC_MIXED && (int64_t)mx * WARPS_PER_CTA * 24 > 200 * 1024)
-            return fail(ML_ERR_UNSUPPORTED, "a level-1 cell has " + std::to_string(mx) +
-                                                " near lenses; use a finer level-1 grid (l1_x, l1_y)");
-
-        // Taylor order: the smallest whose truncation bound meets far_tol
-        std::vector<double> bound((size_t)(g.N1x * g.N1y) * PMAX);
-        double *d_bound = nullptr;
-        ML_CK(cudaMallocAsync((void **)&d_bound, bound.size() * sizeof(double), s));
-        g.p = 1;
-        cudaError_t e = launch_p_bound(g, L, d_bound, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bound.data(), d_bound, bound.size() * sizeof(double),
-                                cudaMemcpyDeviceToHost, s);
-        cudaFreeAsync(d_bound, s);
-        if (e != cudaSuccess) return cuda_fail(e, "truncation bound");
-        ML_CK(cudaStreamSynchronize(s));
-        std::vector<double> worst(PMAX, 0.0);
-        for (size_t c = 0; c < bound.size() / PMAX; ++c)
-            for (int q = 0; q < PMAX; ++q) worst[q] = std::max(worst[q], bound[c * PMAX + q]);
-        int p = d->taylor_p;
-        if (p == 0) {
-            double tol = d->far_tol > 0.0 ? d->far_tol : 1e-7;
-            p = PMAX;
-            for (int q = 1; q <= PMAX; ++q)
-                if (worst[q - 1] <= tol) { p = q; break; }
+            mx = std::max(mx, t);
         }
-        if (d->precision == ML_PREC_MIXED) p = mixed_p_supported(p);
-        g.p = p;
-        f->far_bound = worst[p - 1];
+    f->max_near = mx;
+    if (d->precision == ML_PREC_MIXED && (int64_t)mx * WARPS_PER_CTA * 24 > 200 * 1024)
+        return fail(ML_ERR_UNSUPPORTED, "a level-1 cell has " + std::to_string(mx) +
+                                            " near lenses; use a finer level-1 grid (l1_x, l1_y)");
 
-        // far-field Taylor coefficients at the level-2 nodes (§3.2 Level 2)
+    // truncation bound of every Taylor order, worst level-1 cell
+    std::vector<double> bound((size_t)(g.N1x * g.N1y) * PMAX);
+    double *d_bound = nullptr;
+    ML_CK(cudaMallocAsync((void **)&d_bound, bound.size() * sizeof(double), s));
+    g.p = 1;
+    cudaError_t e = launch_p_bound(g, f->table(), d_bound, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bound.data(), d_bound, bound.size() * sizeof(double),
+                            cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d_bound, s);
+    if (e != cudaSuccess) return cuda_fail(e, "truncation bound");
+    ML_CK(cudaStreamSynchronize(s));
+    f->worst.assign(PMAX, 0.0);
+    for (size_t c = 0; c < bound.size() / PMAX; ++c)
+        for (int q = 0; q < PMAX; ++q) f->worst[q] = std::max(f->worst[q], bound[c * PMAX + q]);
+    return ML_OK;
+}
+
+// The Taylor order the plan's bound asks for (far_tol), rounded up to a
+// compiled order in the mixed mode.
+int planned_order(const ml_field *f)
+{
+    const ml_field_desc *d = &f->desc;
+    int p = d->taylor_p;
+    if (p == 0) {
+        double tol = d->far_tol > 0.0 ? d->far_tol : 1e-7;
+        p = PMAX;
+        for (int q = 1; q <= PMAX; ++q)
+            if (f->worst[q - 1] <= tol) { p = q; break; }
+    }
+    if (d->precision == ML_PREC_MIXED) p = mixed_p_supported(p);
+    return p;
+}
+
+// Finish: far-field coefficients of order p at every level-2 node (§3.2
+// Level 2), node records, zeroed map.
+ml_status create_finish(ml_field *f, int p, cudaStream_t s)
+{
+    const ml_field_desc *d = &f->desc;
+    Geo &g = f->g;
+    if (d->precision != ML_PREC_DIRECT64) {
+        g.p = p;
+        f->far_bound = f->worst[p - 1];
+        const LensTable L = f->table();
         const int64_t nodes = g.N2x * g.N2y;
         ML_CK(f->alloc(&f->d_coef64, (size_t)nodes * (p + 1) * 2, s));
         f->build_used = ML_BUILD_DIRECT;
@@ -352,7 +529,7 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
             if (ns > 0) {
                 double *scratch = nullptr;
                 ML_CK(cudaMallocAsync((void **)&scratch, ns * sizeof(double), s));
-                e = launch_coeffs_hier(g, L, f->d_coef64, scratch, ns, s);
+                cudaError_t e = launch_coeffs_hier(g, L, f->d_coef64, scratch, ns, s);
                 cudaFreeAsync(scratch, s);
                 if (e != cudaSuccess) return cuda_fail(e, "hierarchical coefficient build");
                 f->build_used = ML_BUILD_HIERARCHICAL;
@@ -369,7 +546,6 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
     } else {
         g.p = 0;
     }
-
     const size_t npix = (size_t)g.mnx * g.mny;
     if (d->deposit == ML_DEPOSIT_NGP) {
         ML_CK(f->alloc(&f->d_map_u32, npix, s));
@@ -381,6 +557,13 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
     ML_CK(cudaStreamSynchronize(s));
     ML_CK(cudaGetLastError());
     return ML_OK;
+}
+
+ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
+{
+    ml_status st = create_plan(d, s, f);
+    if (st != ML_OK) return st;
+    return create_finish(f, d->precision == ML_PREC_DIRECT64 ? 0 : planned_order(f), s);
 }
 
 ShootArgs make_args(const ml_field *f)
@@ -416,9 +599,299 @@ ShootArgs make_args(const ml_field *f)
     return a;
 }
 
+// Task decomposition of rays [b, e) for the mixed kernel.
+void set_tasks(ShootArgs &a, const Geo &g, int64_t b, int64_t e)
+{
+    a.ray_begin = b;
+    a.ray_end = e;
+    const int64_t gpb = (g.n1y + 31) / 32;
+    const int64_t l2_per_cc = std::max<int64_t>(1, std::min<int64_t>(g.l2sx, (2048 + g.n2x - 1) / g.n2x));
+    const int64_t cc_per_l1 = (g.l2sx + l2_per_cc - 1) / l2_per_cc;
+    const int64_t jb = b / g.n3x, je = (e - 1) / g.n3x;
+    auto rg = [&](int64_t j) { return (j / g.n1y) * gpb + (j % g.n1y) / 32; };
+    a.groups_per_band = gpb;
+    a.rg_first = rg(jb);
+    a.n_rg = rg(je) - a.rg_first + 1;
+    a.l2_per_cc = l2_per_cc;
+    a.cc_per_l1 = cc_per_l1;
+    a.n_cc = g.N1x * cc_per_l1;
+    a.n_tasks = a.n_rg * a.n_cc;
+}
+
+}  // namespace
+
+// Many maps run as one: fields, their kernel arguments on the device, the
+// task prefix sums, and the buffers of the step's outputs.
+struct ml_batch {
+    int device = 0, num_sms = 0, p = 0, near_cap = 1;
+    std::vector<ml_field *> fields;
+    std::vector<size_t> mu_off;
+    ShootArgs *d_args = nullptr;
+    int64_t *d_base = nullptr;
+    int64_t total_tasks = 0;
+    unsigned long long *d_work = nullptr;
+    unsigned int *d_status = nullptr;
+    int *h_abort = nullptr, *d_abort = nullptr;
+    float *d_mu = nullptr;
+    int tpm = 0, n_samples = 0, taps_h = 0;
+    double *d_tracks = nullptr;
+    float *d_taps = nullptr, *d_curves = nullptr;
+    cudaStream_t s_int = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void *> owned;
+
+    template <class T>
+    cudaError_t alloc(T **ptr, size_t count, cudaStream_t s)
+    {
+        *ptr = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMallocAsync((void **)ptr, count * sizeof(T), s);
+        if (e == cudaSuccess) owned.push_back(*ptr);
+        return e;
+    }
+    void release()
+    {
+        cudaDeviceSynchronize();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (s_int) cudaStreamDestroy(s_int);
+        exec = nullptr; graph = nullptr; ev_in = ev_out = nullptr; s_int = nullptr;
+        for (void *q : owned) cudaFree(q);
+        owned.clear();
+        if (h_abort) cudaFreeHost(h_abort);
+        h_abort = nullptr;
+        for (ml_field *f : fields) {
+            if (!f) continue;
+            f->release();
+            delete f;
+        }
+        fields.clear();
+    }
+};
+
+namespace {
+
+// The whole batch step on stream s (recorded into a graph when capturing).
+cudaError_t batch_enqueue(ml_batch *b, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    for (ml_field *f : b->fields) {
+        const size_t npix = (size_t)f->g.mnx * f->g.mny;
+        if ((e = cudaMemsetAsync(f->d_map_u32, 0, npix * sizeof(uint32_t), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    BatchArgs ba;
+    ba.args = b->d_args;
+    ba.task_base = b->d_base;
+    ba.n_maps = (int)b->fields.size();
+    ba.near_cap = b->near_cap;
+    ba.total_tasks = b->total_tasks;
+    ba.work = b->d_work;
+    ba.abort_flag = b->d_abort;
+    ba.status = b->d_status;
+    if ((e = launch_batch(ba, b->p, b->num_sms, s)) != cudaSuccess) return e;
+    for (size_t i = 0; i < b->fields.size(); ++i) {
+        const ml_field *f = b->fields[i];
+        const Geo &g = f->g;
+        const double scale = (g.l3x * g.l3y) / (g.dpx * g.dpy);
+        if ((e = launch_mu(g, f->d_map_u32, nullptr, ML_MAP_MU_F32, b->d_mu + b->mu_off[i], scale, s)) !=
+            cudaSuccess)
+            return e;
+        if (b->tpm > 0) {
+            e = launch_light_curves_dev(g, f->d_map_u32, nullptr, scale, b->d_tracks + 4 * i * b->tpm,
+                                        b->tpm, b->n_samples, b->taps_h, b->d_taps,
+                                        b->d_curves + i * (size_t)b->tpm * b->n_samples, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, const double *tracks,
+                            int32_t n_samples, double sigma_px, cudaStream_t s, ml_batch *b)
+{
+    ML_CK(cudaGetDevice(&b->device));
+    for (int32_t i = 0; i < n; ++i) {
+        ml_status st = validate(&descs[i]);
+        if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
+        if (descs[i].precision != ML_PREC_MIXED || descs[i].deposit != ML_DEPOSIT_NGP)
+            return fail(ML_ERR_UNSUPPORTED, "batches take ML_PREC_MIXED with ML_DEPOSIT_NGP");
+    }
+    // plan every map, then build all with the largest planned order
+    b->fields.assign(n, nullptr);
+    int P = 1;
+    for (int32_t i = 0; i < n; ++i) {
+        b->fields[i] = new (std::nothrow) ml_field();
+        if (!b->fields[i]) return fail(ML_ERR_OOM, "host allocation failed");
+        ml_status st = create_plan(&descs[i], s, b->fields[i]);
+        if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
+        P = std::max(P, planned_order(b->fields[i]));
+    }
+    b->p = P;
+    std::vector<ShootArgs> args(n);
+    std::vector<int64_t> base(n + 1, 0);
+    size_t mu_total = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        ml_field *f = b->fields[i];
+        ml_status st = create_finish(f, P, s);
+        if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
+        args[i] = make_args(f);
+        set_tasks(args[i], f->g, 0, f->g.n3x * f->g.n3y);
+        b->near_cap = std::max(b->near_cap, args[i].near_cap);
+        base[i + 1] = base[i] + args[i].n_tasks;
+        b->mu_off.push_back(mu_total);
+        mu_total += (size_t)f->g.mnx * f->g.mny;
+    }
+    b->num_sms = b->fields.empty() ? 1 : b->fields[0]->num_sms;
+    b->total_tasks = base[n];
+    ML_CK(b->alloc(&b->d_args, n, s));
+    ML_CK(b->alloc(&b->d_base, n + 1, s));
+    ML_CK(b->alloc(&b->d_work, 1, s));
+    ML_CK(b->alloc(&b->d_status, 1, s));
+    ML_CK(b->alloc(&b->d_mu, mu_total, s));
+    ML_CK(cudaMemcpyAsync(b->d_args, args.data(), sizeof(ShootArgs) * n, cudaMemcpyHostToDevice, s));
+    ML_CK(cudaMemcpyAsync(b->d_base, base.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
+    ML_CK(cudaHostAlloc((void **)&b->h_abort, sizeof(int), cudaHostAllocMapped));
+    *b->h_abort = 0;
+    ML_CK(cudaHostGetDevicePointer((void **)&b->d_abort, b->h_abort, 0));
+    if (tpm > 0) {
+        float taps[129];
+        b->taps_h = light_curve_taps(sigma_px, taps);
+        b->tpm = tpm;
+        b->n_samples = n_samples;
+        ML_CK(b->alloc(&b->d_taps, 2 * b->taps_h + 1, s));
+        ML_CK(b->alloc(&b->d_tracks, (size_t)4 * n * tpm, s));
+        ML_CK(b->alloc(&b->d_curves, (size_t)n * tpm * n_samples, s));
+        ML_CK(cudaMemcpyAsync(b->d_taps, taps, sizeof(float) * (2 * b->taps_h + 1),
+                              cudaMemcpyHostToDevice, s));
+        ML_CK(cudaMemcpyAsync(b->d_tracks, tracks, sizeof(double) * 4 * (size_t)n * tpm,
+                              cudaMemcpyHostToDevice, s));
+    }
+    ML_CK(cudaStreamCreateWithFlags(&b->s_int, cudaStreamNonBlocking));
+    ML_CK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    ML_CK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+    ML_CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+ml_status ml_batch_create(const ml_field_desc *descs, int32_t n, int32_t tracks_per_map,
+                          const double *tracks, int32_t n_samples, double sigma_px, void *stream,
+                          ml_batch **out)
+{
+    if (!out) return fail(ML_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!descs || n < 1) return fail(ML_ERR_INVALID_ARG, "need n >= 1 descriptors");
+    if (tracks_per_map < 0 || (tracks_per_map > 0 && (!tracks || n_samples < 1 ||
+                                                      !(sigma_px > 0.0) || sigma_px > 16.0)))
+        return fail(ML_ERR_INVALID_ARG, "bad light-curve arguments");
+    ml_batch *b = new (std::nothrow) ml_batch();
+    if (!b) return fail(ML_ERR_OOM, "host allocation failed");
+    ml_status st = batch_create_impl(descs, n, tracks_per_map, tracks, n_samples, sigma_px,
+                                     (cudaStream_t)stream, b);
+    if (st != ML_OK) {
+        std::string keep = g_err;
+        b->release();
+        delete b;
+        cudaGetLastError();
+        g_err = keep;
+        return st;
+    }
+    *out = b;
+    return ML_OK;
+}
+
+ml_status ml_batch_run(ml_batch *b, int32_t use_graph, void *stream)
+{
+    if (!b) return fail(ML_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    ML_CK(cudaEventRecord(b->ev_in, s));
+    ML_CK(cudaStreamWaitEvent(b->s_int, b->ev_in, 0));
+    if (use_graph) {
+        if (!b->exec) {
+            ML_CK(cudaStreamBeginCapture(b->s_int, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = batch_enqueue(b, b->s_int);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(b->s_int, &graph);
+            if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "batch capture"); }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "batch capture");
+            b->graph = graph;
+            ML_CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        }
+        ML_CK(cudaGraphLaunch(b->exec, b->s_int));
+    } else {
+        ML_CK(batch_enqueue(b, b->s_int));
+    }
+    ML_CK(cudaEventRecord(b->ev_out, b->s_int));
+    ML_CK(cudaStreamWaitEvent(s, b->ev_out, 0));
+    for (ml_field *f : b->fields) {
+        f->launches = 1;
+        f->rays_asked = (uint64_t)f->g.n3x * (uint64_t)f->g.n3y;
+    }
+    return ML_OK;
+}
+
+ml_status ml_batch_field(ml_batch *b, int32_t i, ml_field **out)
+{
+    if (!b || !out || i < 0 || i >= (int32_t)b->fields.size())
+        return fail(ML_ERR_INVALID_ARG, "bad batch index");
+    *out = b->fields[i];
+    return ML_OK;
+}
+
+ml_status ml_batch_mu(ml_batch *b, int32_t i, float *out, int32_t out_is_device, void *stream)
+{
+    if (!b || !out || i < 0 || i >= (int32_t)b->fields.size())
+        return fail(ML_ERR_INVALID_ARG, "bad batch index");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ml_field *f = b->fields[i];
+    const size_t npix = (size_t)f->g.mnx * f->g.mny;
+    ML_CK(cudaMemcpyAsync(out, b->d_mu + b->mu_off[i], npix * sizeof(float),
+                          out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!out_is_device) ML_CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
+ml_status ml_batch_curves(ml_batch *b, float *out, int32_t out_is_device, void *stream)
+{
+    if (!b || !out) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (b->tpm == 0) return fail(ML_ERR_STATE, "the batch has no tracks");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cnt = b->fields.size() * (size_t)b->tpm * b->n_samples;
+    ML_CK(cudaMemcpyAsync(out, b->d_curves, cnt * sizeof(float),
+                          out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!out_is_device) ML_CK(cudaStreamSynchronize(s));
+    return ML_OK;
+}
+
+ml_status ml_batch_abort(ml_batch *b, int32_t on)
+{
+    if (!b) return fail(ML_ERR_INVALID_ARG, "batch is NULL");
+    *(volatile int *)b->h_abort = on ? 1 : 0;
+    return ML_OK;
+}
+
+ml_status ml_batch_destroy(ml_batch *b)
+{
+    if (!b) return ML_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(b->device);
+    b->release();
+    cudaSetDevice(cur);
+    delete b;
+    return ML_OK;
+}
 
 int32_t ml_abi_version(void) { return ML_ABI_VERSION; }
 
@@ -456,23 +929,12 @@ ml_status ml_shoot_rays(ml_field *f, uint64_t ray_begin, uint64_t ray_end, void 
                                             std::to_string(total) + ")");
     cudaStream_t s = (cudaStream_t)stream;
     ShootArgs a = make_args(f);
-    const int64_t gpb = (g.n1y + 31) / 32;
-    const int64_t l2_per_cc = std::max<int64_t>(1, std::min<int64_t>(g.l2sx, (2048 + g.n2x - 1) / g.n2x));
-    const int64_t cc_per_l1 = (g.l2sx + l2_per_cc - 1) / l2_per_cc;
     for (uint64_t b = ray_begin; b < ray_end;) {
         uint64_t e = std::min<uint64_t>(ray_end, b + f->max_launch_rays);
         a.ray_begin = (int64_t)b;
         a.ray_end = (int64_t)e;
         if (g.precision == ML_PREC_MIXED) {
-            int64_t jb = a.ray_begin / g.n3x, je = (a.ray_end - 1) / g.n3x;
-            auto rg = [&](int64_t j) { return (j / g.n1y) * gpb + (j % g.n1y) / 32; };
-            a.groups_per_band = gpb;
-            a.rg_first = rg(jb);
-            a.n_rg = rg(je) - a.rg_first + 1;
-            a.l2_per_cc = l2_per_cc;
-            a.cc_per_l1 = cc_per_l1;
-            a.n_cc = g.N1x * cc_per_l1;
-            a.n_tasks = a.n_rg * a.n_cc;
+            set_tasks(a, g, (int64_t)b, (int64_t)e);
             ML_CK(cudaMemsetAsync(f->d_work, 0, sizeof(unsigned long long), s));
         }
         ML_CK(launch_shoot(a, f->num_sms, s));

@@ -74,6 +74,19 @@ struct ShootArgs {
     double rho_y;                   // (1-kappa+gamma+kappa_*) * l3y / dpy
 };
 
+// Many maps in one persistent launch: per-map arguments (device array) and
+// the prefix sums of their task counts.
+struct BatchArgs {
+    const ShootArgs *args;
+    const int64_t *task_base;       // n_maps + 1 entries
+    int n_maps;
+    int near_cap;                   // largest near_cap of the maps
+    int64_t total_tasks;
+    unsigned long long *work;
+    const volatile int *abort_flag;
+    unsigned int *status;           // bit 1: aborted
+};
+
 // ---- launch wrappers (defined in the .cu files) ----
 cudaError_t launch_lens_cells(const Geo &g, const double *x, const double *y, int64_t n,
                               int32_t *cell, int32_t *count, cudaStream_t s);
@@ -92,6 +105,7 @@ cudaError_t launch_node_finalize(const Geo &g, const double *coef64, unsigned ch
 cudaError_t launch_shoot(const ShootArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_trace(const ShootArgs &a, const int64_t *idx, int64_t n, double *beta,
                          int32_t *pix, cudaStream_t s);
+cudaError_t launch_batch(const BatchArgs &b, int p, int num_sms, cudaStream_t s);
 cudaError_t launch_mu(const Geo &g, const uint32_t *cu, const float *cf, int want, void *out,
                       double scale, cudaStream_t s);
 cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *cf, double scale,
@@ -100,6 +114,10 @@ cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *c
 cudaError_t launch_light_curves_noalloc(const Geo &g, const uint32_t *cu, const float *cf,
                                         double scale, const double *tracks_host, int n_tracks,
                                         int n_samples, double sigma_px, float *out, cudaStream_t s);
+int light_curve_taps(double sigma_px, float taps[129]);
+cudaError_t launch_light_curves_dev(const Geo &g, const uint32_t *cu, const float *cf, double scale,
+                                    const double *d_tracks, int n_tracks, int n_samples, int h,
+                                    const float *d_taps, float *out, cudaStream_t s);
 int mixed_p_supported(int p);     // the Taylor order the mixed kernel will use for p
 
 // ---- shared device arithmetic ---------------------------------------------

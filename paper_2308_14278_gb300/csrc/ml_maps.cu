@@ -231,4 +231,30 @@ cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *c
     return e;
 }
 
+// Light curves with the taps and tracks already on the device (the batched
+// step, which is captured in a CUDA graph and must not allocate).
+int light_curve_taps(double sigma_px, float taps[129])
+{
+    int h = (int)floor(4.0 * sigma_px);
+    if (h > 64) return -1;
+    double sum = 0.0, w[129];
+    for (int t = -h; t <= h; ++t) {
+        w[t + h] = exp(-0.5 * ((double)t / sigma_px) * ((double)t / sigma_px));
+        sum += w[t + h];
+    }
+    for (int t = 0; t <= 2 * h; ++t) taps[t] = (float)(w[t] / sum);
+    return h;
+}
+
+cudaError_t launch_light_curves_dev(const Geo &g, const uint32_t *cu, const float *cf, double scale,
+                                    const double *d_tracks, int n_tracks, int n_samples, int h,
+                                    const float *d_taps, float *out, cudaStream_t s)
+{
+    int64_t n = (int64_t)n_tracks * n_samples;
+    if (n == 0) return cudaSuccess;
+    k_light_curves<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, cu, cf, scale, d_tracks, n_tracks,
+                                                               n_samples, h, d_taps, out);
+    return cudaGetLastError();
+}
+
 }  // namespace ml

@@ -484,6 +484,67 @@ __device__ __forceinline__ float pin(float v)
     return v;
 }
 
+// One warp task of the mixed kernel (NGP deposit): stage the near list, then
+// walk each level-2 column of the task.  Shared by the single-map and the
+// batched persistent kernels.
+template <int P>
+__device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4 *near, float2 *nlo,
+                                           int lane, float dyl, float dyl_lo, RunState &rs,
+                                           unsigned &drop, unsigned long long &pairs,
+                                           unsigned long long &tasks)
+{
+    const Geo &g = a.g;
+    TaskShape ts;
+    if (!decode_task(a, t, ts)) return;
+    ++tasks;
+    const SmemNear nl{near, nlo};
+    const int64_t jb = a.ray_begin / g.n3x, ib = a.ray_begin % g.n3x;
+    const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
+    const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
+    const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
+    const int nn = stage_near_y(a, nr, yref, near, nlo, lane);
+    const int64_t j = ts.row0 + lane;
+    const bool active = j < ts.rows_end && j >= jb && j <= je;
+    const int64_t c2y = j / g.n2y;
+    const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
+    for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
+        stage_near_x(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
+        const int64_t i0 = c2x * g.n2x;
+        int k0 = 0, k1 = (int)(min(i0 + g.n2x, g.n3x) - i0);
+        if (j == jb) k0 = max(k0, (int)max((int64_t)0, ib - i0));
+        if (j == je) k1 = min(k1, (int)max((int64_t)0, ie - i0));
+        if (!active || k0 >= k1) { k0 = 0; k1 = 0; }
+        // warp-uniform walk range: the union of the lanes' ranges
+        const int kbeg = __reduce_min_sync(0xffffffffu, k1 > k0 ? k0 : 0x7fffffff);
+        const int kend = __reduce_max_sync(0xffffffffu, k1);
+        if (kbeg >= kend) continue;
+        RowPoly<P> rp;
+        row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
+        pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
+        const bool on = k1 > k0;
+        const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
+        if (uniform && nn <= 4) {
+            switch (nn) {
+            case 0: walk_fixed<P, 0>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+            case 1: walk_fixed<P, 1>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+            case 2: walk_fixed<P, 2>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+            case 3: walk_fixed<P, 3>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+            default: walk_fixed<P, 4>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+            }
+        } else {
+            walk_any<P>(rp, a, nl, nn, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop);
+        }
+    }
+}
+
+// Lane offset from a task's first row, l3y * lane rounded once from FP64.
+__device__ __forceinline__ void lane_dy(double l3y, int lane, float &dyl, float &dyl_lo)
+{
+    const double d = (double)lane * l3y;
+    dyl = pin((float)d);
+    dyl_lo = pin((float)(d - (double)(float)d));
+}
+
 template <int P>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mixed(ShootArgs a)
 {
@@ -491,66 +552,82 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4 *near = smem + wid * a.near_cap;
     float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * a.near_cap) + wid * a.near_cap;
-    const SmemNear nl{near, nlo};
-    const Geo &g = a.g;
-    const int64_t jb = a.ray_begin / g.n3x, ib = a.ray_begin % g.n3x;
-    const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
-
     RunState rs{-1, -1, 0u, 0u, 0u, 0u, 0u, 0u};
     unsigned drop = 0;
     unsigned long long pairs = 0, tasks = 0;
-    // lane offset from the task's first row (FP64 product rounded once)
-    const double dyl_d = (double)lane * g.l3y;
-    const float dyl = pin((float)dyl_d);
-    const float dyl_lo = pin((float)(dyl_d - (double)(float)dyl_d));
-
+    float dyl, dyl_lo;
+    lane_dy(a.g.l3y, lane, dyl, dyl_lo);
     for (;;) {
         bool stop;
         const int64_t t = fetch_task(a, lane, stop);
         if (stop || t >= a.n_tasks) break;
-        TaskShape ts;
-        if (!decode_task(a, t, ts)) continue;
-        ++tasks;
-        const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
-        const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
-        const int nn = stage_near_y(a, nr, yref, near, nlo, lane);
-        const int64_t j = ts.row0 + lane;
-        const bool active = j < ts.rows_end && j >= jb && j <= je;
-        const int64_t c2y = j / g.n2y;
-        const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
-        for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
-            stage_near_x(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
-            const int64_t i0 = c2x * g.n2x;
-            int k0 = 0, k1 = (int)(min(i0 + g.n2x, g.n3x) - i0);
-            if (j == jb) k0 = max(k0, (int)max((int64_t)0, ib - i0));
-            if (j == je) k1 = min(k1, (int)max((int64_t)0, ie - i0));
-            if (!active || k0 >= k1) { k0 = 0; k1 = 0; }
-            // warp-uniform walk range: the union of the lanes' ranges
-            const int kbeg = __reduce_min_sync(0xffffffffu, k1 > k0 ? k0 : 0x7fffffff);
-            const int kend = __reduce_max_sync(0xffffffffu, k1);
-            if (kbeg >= kend) continue;
-            RowPoly<P> rp;
-            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
-            pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
-            const bool on = k1 > k0;
-            const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
-            if (uniform && nn <= 4) {
-                switch (nn) {
-                case 0: walk_fixed<P, 0>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-                case 1: walk_fixed<P, 1>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-                case 2: walk_fixed<P, 2>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-                case 3: walk_fixed<P, 3>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-                default: walk_fixed<P, 4>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-                }
-            } else {
-                walk_any<P>(rp, a, nl, nn, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop);
-            }
-        }
+        shoot_task<P>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks);
     }
-    run_flush(rs, a.map_u32, g.mnx, g.mny);
+    run_flush(rs, a.map_u32, a.g.mnx, a.g.mny);
     rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
     // dropped rays were sent to (-1, -1) and counted as out above
     flush_stats(a, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, rs.ovf);
+}
+
+// Batched persistent kernel: one launch over the tasks of many maps (all
+// built with the same Taylor order P).  Global task t belongs to the map m
+// with task_base[m] <= t < task_base[m+1]; a warp flushes its runs and
+// counters into a map's buffers when it moves on to another map.
+template <int P>
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_batch(BatchArgs b)
+{
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float4 *near = smem + wid * b.near_cap;
+    float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * b.near_cap) + wid * b.near_cap;
+    RunState rs{-1, -1, 0u, 0u, 0u, 0u, 0u, 0u};
+    unsigned drop = 0;
+    unsigned long long pairs = 0, tasks = 0;
+    float dyl = 0.f, dyl_lo = 0.f;
+    int cur = -1;
+    const int64_t total = b.task_base[b.n_maps];
+    for (;;) {
+        long long t = 0;
+        int ab = 0;
+        if (lane == 0) {
+            t = (long long)atomicAdd(b.work, 1ull);
+            ab = *b.abort_flag;
+        }
+        t = __shfl_sync(0xffffffffu, t, 0);
+        ab = __shfl_sync(0xffffffffu, ab, 0);
+        if (ab) {
+            if (lane == 0) atomicOr(b.status, 2u);
+            break;
+        }
+        if (t >= total) break;
+        int lo = 0, hi = b.n_maps;            // last m with task_base[m] <= t
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (b.task_base[mid] <= t) lo = mid; else hi = mid;
+        }
+        if (lo != cur) {
+            if (cur >= 0) {
+                const ShootArgs &ac = b.args[cur];
+                run_flush(rs, ac.map_u32, ac.g.mnx, ac.g.mny);
+                rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
+                flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, rs.ovf);
+                rs = RunState{-1, -1, 0u, 0u, 0u, 0u, 0u, 0u};
+                drop = 0;
+                pairs = 0;
+                tasks = 0;
+            }
+            cur = lo;
+            lane_dy(b.args[cur].g.l3y, lane, dyl, dyl_lo);
+        }
+        shoot_task<P>(b.args[cur], t - b.task_base[cur], near, nlo, lane, dyl, dyl_lo, rs, drop,
+                      pairs, tasks);
+    }
+    if (cur >= 0) {
+        const ShootArgs &ac = b.args[cur];
+        run_flush(rs, ac.map_u32, ac.g.mnx, ac.g.mny);
+        rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
+        flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, rs.ovf);
+    }
 }
 
 // Cloud-in-cell variant: a float map, four weighted atomics per ray.
@@ -786,6 +863,45 @@ cudaError_t launch_shoot(const ShootArgs &a, int num_sms, cudaStream_t s)
     else
         k_shoot_fp64<false><<<(unsigned)blocks, 256, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_batch_p(const BatchArgs &b, int num_sms, cudaStream_t s)
+{
+    size_t smem = (size_t)b.near_cap * WARPS_PER_CTA * (sizeof(float4) + sizeof(float2));
+    auto kern = k_shoot_batch<P>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                                  WARPS_PER_CTA * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)num_sms * per_sm;
+    int64_t need = (b.total_tasks + WARPS_PER_CTA - 1) / WARPS_PER_CTA;
+    if (need < blocks) blocks = need > 0 ? need : 1;
+    kern<<<(unsigned)blocks, WARPS_PER_CTA * 32, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs &b, int p, int num_sms, cudaStream_t s)
+{
+    switch (p) {
+    case 1: return launch_batch_p<1>(b, num_sms, s);
+    case 2: return launch_batch_p<2>(b, num_sms, s);
+    case 3: return launch_batch_p<3>(b, num_sms, s);
+    case 4: return launch_batch_p<4>(b, num_sms, s);
+    case 5: return launch_batch_p<5>(b, num_sms, s);
+    case 6: return launch_batch_p<6>(b, num_sms, s);
+    case 8: return launch_batch_p<8>(b, num_sms, s);
+    case 10: return launch_batch_p<10>(b, num_sms, s);
+    case 12: return launch_batch_p<12>(b, num_sms, s);
+    case 16: return launch_batch_p<16>(b, num_sms, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_trace(const ShootArgs &a, const int64_t *idx, int64_t n, double *beta,
