@@ -244,6 +244,34 @@ ml_status ml_trace_rays(ml_field *f, const int64_t *ray_idx, int64_t n, double *
                         int32_t *pix, void *stream);
 
 /*
+ * ml_cic_forward - the differentiable map: clears the field, shoots all its
+ * rays and writes M = (S_I / S_S) * cloud-in-cell weights (Eq. 12 with
+ * bilinear weights to the four nearest pixel centres) as float32.
+ *  mu: device, map_ny x map_nx float32, 16-byte aligned; caller-owned.
+ * Stream-ordered.  Errors: ML_ERR_STATE unless the field is ML_DEPOSIT_CIC
+ * and ML_PREC_MIXED; ML_ERR_INVALID_ARG; ML_ERR_CUDA.
+ */
+ml_status ml_cic_forward(ml_field *f, float *mu, void *stream);
+
+/*
+ * ml_cic_backward - gradient of a loss of the cloud-in-cell magnification
+ * map M = (S_I / S_S) * CIC weights (Eq. 12 with bilinear weights), given
+ * G = dLoss/dM, with respect to every lens position and mass and to kappa,
+ * gamma and kappa_* (the terms of Eq. 6).  Deflections are recomputed by the
+ * forward's own arithmetic, not stored; the lens terms use the exact
+ * point-mass derivatives (the forward's far series differs from them only
+ * by its truncation, far_bound).  The field must be ML_DEPOSIT_CIC and
+ * ML_PREC_MIXED, and M must come from shooting all its rays.
+ *  dL_dM:       device, map_ny x map_nx float32.
+ *  grad_lens:   device, n_lens x 3 float64 (d/dx_k, d/dy_k, d/dm_k) in the
+ *               order the lenses were given; overwritten.
+ *  grad_params: device, 3 float64 (d/dkappa, d/dgamma, d/dkappa_*); overwritten.
+ * Errors: ML_ERR_STATE for other field modes; ML_ERR_INVALID_ARG; ML_ERR_CUDA.
+ */
+ml_status ml_cic_backward(ml_field *f, const float *dL_dM, double *grad_lens, double *grad_params,
+                          void *stream);
+
+/*
  * ml_field_clear - zero the map and the counters (stream-ordered).
  */
 ml_status ml_field_clear(ml_field *f, void *stream);

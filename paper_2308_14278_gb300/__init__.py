@@ -38,7 +38,8 @@ EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays"
            "ml_magnification_map", "ml_light_curves", "ml_trace_rays", "ml_field_clear",
            "ml_field_stats", "ml_field_info", "ml_field_abort", "ml_field_destroy",
            "ml_light_curves_noalloc", "ml_batch_create", "ml_batch_run", "ml_batch_field",
-           "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy")
+           "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy",
+           "ml_cic_forward", "ml_cic_backward")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -121,6 +122,8 @@ def load(path: str | None = None):
         "ml_batch_curves": ([V, V, C.c_int32, V], st),
         "ml_batch_abort": ([V, C.c_int32], st),
         "ml_batch_destroy": ([V], st),
+        "ml_cic_forward": ([V, V, V], st),
+        "ml_cic_backward": ([V, V, V, V, V], st),
         "ml_field_clear": ([V, V], st),
         "ml_field_stats": ([V, P(C.c_uint64), V], st),
         "ml_field_info": ([V, P(FieldParams)], st),
@@ -194,6 +197,17 @@ def ml_light_curves_noalloc(field, tracks, n_samples: int, sigma_px: float, out,
     tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
     _check(load().ml_light_curves_noalloc(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
                                           _dptr(out), _stream(stream)))
+
+
+def ml_cic_forward(field, mu, stream=None):
+    """Differentiable CIC magnification map into a device float32 tensor (see ml.h)."""
+    _check(load().ml_cic_forward(field, _dptr(mu), _stream(stream)))
+
+
+def ml_cic_backward(field, dL_dM, grad_lens, grad_params, stream=None):
+    """Adjoint of the CIC magnification map (see ml.h); device tensors."""
+    _check(load().ml_cic_backward(field, _dptr(dL_dM), _dptr(grad_lens), _dptr(grad_params),
+                                  _stream(stream)))
 
 
 def ml_trace_rays(field, ray_idx, beta, pix, stream=None):

@@ -259,6 +259,18 @@ struct GridChoice {
     double cost = 0.0;
 };
 
+// One candidate level-2 grid of a field: its subdivisions, the compiled
+// Taylor order its truncation bound needs, and its size.
+struct TuneCand {
+    int sx, sy, P;
+    double nodes, rays;
+};
+
+double cand_cost(const TuneCand &c, int P)
+{
+    return c.rays * ray_cost_ns(P) + c.nodes * (P + 1) * kNodeCostNs;
+}
+
 uint64_t mix64(uint64_t h, uint64_t v)
 {
     h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
@@ -282,17 +294,20 @@ uint64_t tune_key(const ml_field_desc &d, const std::vector<double> &hx, const s
 }
 
 std::mutex g_tune_mu;
-std::unordered_map<uint64_t, GridChoice> g_tune_cache;
+std::unordered_map<uint64_t, std::vector<TuneCand>> g_tune_cache;
 
-ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
-                    const std::vector<double> &hm, const double *dx, const double *dy, const double *dm,
-                    cudaStream_t s, GridChoice &best)
+// Feasible candidate grids of a field (cached per process by a hash of the
+// descriptor's parameters and the lens arrays).
+ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
+                          const std::vector<double> &hy, const std::vector<double> &hm,
+                          const double *dx, const double *dy, const double *dm, cudaStream_t s,
+                          std::vector<TuneCand> &out)
 {
     const uint64_t key = tune_key(d, hx, hy, hm);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) { best = it->second; return ML_OK; }
+        if (it != g_tune_cache.end()) { out = it->second; return ML_OK; }
     }
     const int64_t n = (int64_t)hx.size();
     Geo g0;
@@ -332,9 +347,8 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
             if (e != cudaSuccess) break;
         }
     const double tol = d.far_tol > 0.0 ? d.far_tol : 1e-7;
-    const double rays = (double)g0.n3x * (double)g0.n3y;
-    bool found = false;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    std::vector<TuneCand> res;
     for (Cand &c : cands) {
         if (e != cudaSuccess) break;
         std::vector<double> bound((size_t)(c.g.N1x * c.g.N1y * PMAX));
@@ -349,13 +363,8 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
                 if (w <= tol) { p = q; break; }
             }
         }
-        const int P = mixed_p_supported(p);
-        const double nodes = (double)c.g.N2x * (double)c.g.N2y;
-        const double cost = rays * ray_cost_ns(P) + nodes * (P + 1) * kNodeCostNs;
-        if (!found || cost < best.cost) {
-            best.sx = c.sx; best.sy = c.sy; best.p = P; best.cost = cost;
-            found = true;
-        }
+        res.push_back(TuneCand{c.sx, c.sy, mixed_p_supported(p), (double)c.g.N2x * (double)c.g.N2y,
+                               (double)c.g.n3x * (double)c.g.n3y});
     }
     for (Cand &c : cands) {
         if (c.cells) cudaFreeAsync(c.cells, s);
@@ -363,9 +372,54 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
         if (c.bound) cudaFreeAsync(c.bound, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grid autotuner");
-    if (!found) { best = GridChoice(); return ML_OK; }
+    out = res;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = best;
+    g_tune_cache[key] = res;
+    return ML_OK;
+}
+
+// Cheapest candidate of a single field (its own order).
+GridChoice best_single(const std::vector<TuneCand> &cands)
+{
+    GridChoice best;
+    bool found = false;
+    for (const TuneCand &c : cands) {
+        double cost = cand_cost(c, c.P);
+        if (!found || cost < best.cost) {
+            best.sx = c.sx; best.sy = c.sy; best.p = c.P; best.cost = cost;
+            found = true;
+        }
+    }
+    return best;
+}
+
+ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
+                    const std::vector<double> &hm, const double *dx, const double *dy, const double *dm,
+                    cudaStream_t s, GridChoice &best)
+{
+    std::vector<TuneCand> cands;
+    ml_status st = tune_candidates(d, hx, hy, hm, dx, dy, dm, s, cands);
+    if (st != ML_OK) return st;
+    best = cands.empty() ? GridChoice() : best_single(cands);
+    return ML_OK;
+}
+
+// Lens arrays of a descriptor on the host.
+ml_status load_lenses(const ml_field_desc &d, std::vector<double> &hx, std::vector<double> &hy,
+                      std::vector<double> &hm)
+{
+    const int64_t n = d.n_lens;
+    hx.resize(n); hy.resize(n); hm.resize(n);
+    if (n == 0) return ML_OK;
+    if (d.lens_mem_is_device) {
+        ML_CK(cudaMemcpy(hx.data(), d.lens_x, n * sizeof(double), cudaMemcpyDeviceToHost));
+        ML_CK(cudaMemcpy(hy.data(), d.lens_y, n * sizeof(double), cudaMemcpyDeviceToHost));
+        ML_CK(cudaMemcpy(hm.data(), d.lens_m, n * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(hx.data(), d.lens_x, n * sizeof(double));
+        memcpy(hy.data(), d.lens_y, n * sizeof(double));
+        memcpy(hm.data(), d.lens_m, n * sizeof(double));
+    }
     return ML_OK;
 }
 
@@ -724,14 +778,69 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
         if (descs[i].precision != ML_PREC_MIXED || descs[i].deposit != ML_DEPOSIT_NGP)
             return fail(ML_ERR_UNSUPPORTED, "batches take ML_PREC_MIXED with ML_DEPOSIT_NGP");
     }
+    // Tuned maps: choose one Taylor order for the launch jointly.  For every
+    // compiled order P each map takes its cheapest grid whose order is <= P;
+    // the order with the smallest summed predicted time wins.
+    std::vector<ml_field_desc> plan(descs, descs + n);
+    std::vector<std::vector<TuneCand>> cands(n);
+    bool any_tuned = false;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!(plan[i].tune && plan[i].l2_sub_x == 0 && plan[i].l2_sub_y == 0)) continue;
+        std::vector<double> hx, hy, hm;
+        ml_status st = load_lenses(plan[i], hx, hy, hm);
+        if (st != ML_OK) return st;
+        const size_t nl = std::max<size_t>(hx.size(), 1);
+        double *dx = nullptr, *dy = nullptr, *dm = nullptr;
+        ML_CK(cudaMallocAsync((void **)&dx, nl * sizeof(double), s));
+        ML_CK(cudaMallocAsync((void **)&dy, nl * sizeof(double), s));
+        ML_CK(cudaMallocAsync((void **)&dm, nl * sizeof(double), s));
+        cudaError_t e = cudaSuccess;
+        if (!hx.empty()) {
+            e = cudaMemcpyAsync(dx, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dy, hy.data(), hy.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dm, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+        }
+        if (e == cudaSuccess) st = tune_candidates(plan[i], hx, hy, hm, dx, dy, dm, s, cands[i]);
+        cudaFreeAsync(dx, s);
+        cudaFreeAsync(dy, s);
+        cudaFreeAsync(dm, s);
+        if (e != cudaSuccess) return cuda_fail(e, "batch tuner");
+        if (st != ML_OK) return st;
+        any_tuned = any_tuned || !cands[i].empty();
+    }
+    if (any_tuned) {
+        static const int orders[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+        double best_total = -1.0;
+        int best_P = 0;
+        for (int P : orders) {
+            double total = 0.0;
+            bool ok = true;
+            for (int32_t i = 0; i < n && ok; ++i) {
+                if (cands[i].empty()) continue;
+                double m = -1.0;
+                for (const TuneCand &c : cands[i])
+                    if (c.P <= P && (m < 0.0 || cand_cost(c, P) < m)) m = cand_cost(c, P);
+                if (m < 0.0) ok = false; else total += m;
+            }
+            if (ok && (best_total < 0.0 || total < best_total)) { best_total = total; best_P = P; }
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            if (cands[i].empty()) continue;
+            const TuneCand *pick = nullptr;
+            for (const TuneCand &c : cands[i])
+                if (c.P <= best_P && (!pick || cand_cost(c, best_P) < cand_cost(*pick, best_P))) pick = &c;
+            if (pick) { plan[i].l2_sub_x = pick->sx; plan[i].l2_sub_y = pick->sy; }
+        }
+    }
     // plan every map, then build all with the largest planned order
     b->fields.assign(n, nullptr);
     int P = 1;
     for (int32_t i = 0; i < n; ++i) {
         b->fields[i] = new (std::nothrow) ml_field();
         if (!b->fields[i]) return fail(ML_ERR_OOM, "host allocation failed");
-        ml_status st = create_plan(&descs[i], s, b->fields[i]);
+        ml_status st = create_plan(&plan[i], s, b->fields[i]);
         if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
+        if (!cands[i].empty()) b->fields[i]->tuned = 1;
         P = std::max(P, planned_order(b->fields[i]));
     }
     b->p = P;
@@ -1035,6 +1144,37 @@ ml_status ml_light_curves_noalloc(ml_field *f, const double *tracks, int32_t n_t
     const double scale = (g.l3x * g.l3y) / (g.dpx * g.dpy);
     ML_CK(launch_light_curves_noalloc(g, f->d_map_u32, f->d_map_f32, scale, tracks, n_tracks,
                                       n_samples, sigma_px, out, (cudaStream_t)stream));
+    return ML_OK;
+}
+
+ml_status ml_cic_forward(ml_field *f, float *mu, void *stream)
+{
+    if (!f || !mu) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (f->g.deposit != ML_DEPOSIT_CIC || f->g.precision != ML_PREC_MIXED)
+        return fail(ML_ERR_STATE, "the differentiable map needs ML_DEPOSIT_CIC and ML_PREC_MIXED");
+    ml_status st = ml_field_clear(f, stream);
+    if (st != ML_OK) return st;
+    st = ml_shoot_rays(f, 0, (uint64_t)f->g.n3x * (uint64_t)f->g.n3y, stream);
+    if (st != ML_OK) return st;
+    return ml_magnification_map(f, ML_MAP_MU_F32, mu, 1, stream);
+}
+
+ml_status ml_cic_backward(ml_field *f, const float *dL_dM, double *grad_lens, double *grad_params,
+                          void *stream)
+{
+    if (!f || !dL_dM || !grad_lens || !grad_params) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (f->g.deposit != ML_DEPOSIT_CIC || f->g.precision != ML_PREC_MIXED)
+        return fail(ML_ERR_STATE, "the adjoint needs a field with ML_DEPOSIT_CIC and ML_PREC_MIXED");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geo &g = f->g;
+    ShootArgs a = make_args(f);
+    a.ray_begin = 0;
+    a.ray_end = g.n3x * g.n3y;
+    const double scale = (g.l3x * g.l3y) / (g.dpx * g.dpy);
+    ML_CK(cudaMemsetAsync(grad_lens, 0, sizeof(double) * 3 * (size_t)std::max<int64_t>(f->n_lens, 0), s));
+    ML_CK(cudaMemsetAsync(grad_params, 0, sizeof(double) * 3, s));
+    ML_CK(launch_cic_adjoint(a, dL_dM, f->d_x, f->d_y, f->d_m, f->n_lens, grad_lens, grad_params, scale,
+                             f->num_sms, s));
     return ML_OK;
 }
 

@@ -106,6 +106,9 @@ cudaError_t launch_shoot(const ShootArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_trace(const ShootArgs &a, const int64_t *idx, int64_t n, double *beta,
                          int32_t *pix, cudaStream_t s);
 cudaError_t launch_batch(const BatchArgs &b, int p, int num_sms, cudaStream_t s);
+cudaError_t launch_cic_adjoint(const ShootArgs &a, const float *G, const double *lx, const double *ly,
+                               const double *lm, int64_t n_lens, double *glens, double *gpar,
+                               double scale, int num_sms, cudaStream_t s);
 cudaError_t launch_mu(const Geo &g, const uint32_t *cu, const float *cf, int want, void *out,
                       double scale, cudaStream_t s);
 cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *cf, double scale,
