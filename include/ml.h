@@ -258,10 +258,12 @@ ml_status ml_cic_forward(ml_field *f, float *mu, void *stream);
  * map M = (S_I / S_S) * CIC weights (Eq. 12 with bilinear weights), given
  * G = dLoss/dM, with respect to every lens position and mass and to kappa,
  * gamma and kappa_* (the terms of Eq. 6).  Deflections are recomputed by the
- * forward's own arithmetic, not stored; the lens terms use the exact
- * point-mass derivatives (the forward's far series differs from them only
- * by its truncation, far_bound).  The field must be ML_DEPOSIT_CIC and
- * ML_PREC_MIXED, and M must come from shooting all its rays.
+ * forward's own arithmetic, not stored.  Near lenses take the exact
+ * point-mass derivatives; far lenses act through the node series of Eq. 9,
+ * so the result is the gradient of the forward as computed (it differs from
+ * the derivative of the direct sum by the series truncation, far_bound).
+ * The field must be ML_DEPOSIT_CIC and ML_PREC_MIXED.  Uses the field's task
+ * counter: do not run it concurrently with ml_shoot_rays on the same field.
  *  dL_dM:       device, map_ny x map_nx float32.
  *  grad_lens:   device, n_lens x 3 float64 (d/dx_k, d/dy_k, d/dm_k) in the
  *               order the lenses were given; overwritten.
@@ -270,6 +272,26 @@ ml_status ml_cic_forward(ml_field *f, float *mu, void *stream);
  */
 ml_status ml_cic_backward(ml_field *f, const float *dL_dM, double *grad_lens, double *grad_params,
                           void *stream);
+
+/* Adjoint methods of ml_cic_backward_ex. */
+enum {
+    ML_ADJOINT_NEARFAR = 0, /* transpose of the near/far scheme (Eq. 9): near lenses pair by pair,
+                               far lenses through moments of each level-2 node; the exact gradient
+                               of the forward as computed.  Cost ~ rays (near + p) + nodes x lenses. */
+    ML_ADJOINT_DIRECT = 1   /* every ray against every lens with the exact point-mass derivatives;
+                               cost rays x lenses (a cross-check) */
+};
+
+/*
+ * ml_cic_backward_ex - ml_cic_backward with a choice of method (above).
+ * ml_cic_backward is ml_cic_backward_ex(..., ML_ADJOINT_NEARFAR, ...).
+ * The near/far method allocates its scratch (3 doubles per lens and
+ * 2 (p + 1) doubles per level-2 node) stream-ordered and frees it before
+ * returning.  Errors as ml_cic_backward, and ML_ERR_INVALID_ARG for an
+ * unknown method.
+ */
+ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens, double *grad_params,
+                             int32_t method, void *stream);
 
 /*
  * ml_field_clear - zero the map and the counters (stream-ordered).

@@ -227,6 +227,8 @@ def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, ma
 
 def geometry_of(w, **kw) -> Geometry:
     """derive_geometry for a paper_2308_14278_gb300.inputs.Workload."""
+    if getattr(w, "l1", None) is not None and "l1" not in kw:
+        kw["l1"] = w.l1
     return derive_geometry(w.kappa, w.gamma, w.kappa_star, w.lenses.x, w.lenses.y, w.sheet,
                            w.map_box, w.map_n, ray_box=w.ray_box, ray_n=w.ray_n,
                            n_av=w.n_av, **kw)

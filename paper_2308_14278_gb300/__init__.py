@@ -39,7 +39,7 @@ EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays"
            "ml_field_stats", "ml_field_info", "ml_field_abort", "ml_field_destroy",
            "ml_light_curves_noalloc", "ml_batch_create", "ml_batch_run", "ml_batch_field",
            "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy",
-           "ml_cic_forward", "ml_cic_backward")
+           "ml_cic_forward", "ml_cic_backward", "ml_cic_backward_ex")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -124,6 +124,7 @@ def load(path: str | None = None):
         "ml_batch_destroy": ([V], st),
         "ml_cic_forward": ([V, V, V], st),
         "ml_cic_backward": ([V, V, V, V, V], st),
+        "ml_cic_backward_ex": ([V, V, V, V, C.c_int32, V], st),
         "ml_field_clear": ([V, V], st),
         "ml_field_stats": ([V, P(C.c_uint64), V], st),
         "ml_field_info": ([V, P(FieldParams)], st),
@@ -204,10 +205,13 @@ def ml_cic_forward(field, mu, stream=None):
     _check(load().ml_cic_forward(field, _dptr(mu), _stream(stream)))
 
 
-def ml_cic_backward(field, dL_dM, grad_lens, grad_params, stream=None):
+ADJOINT_NEARFAR, ADJOINT_DIRECT = 0, 1
+
+
+def ml_cic_backward(field, dL_dM, grad_lens, grad_params, stream=None, method=ADJOINT_NEARFAR):
     """Adjoint of the CIC magnification map (see ml.h); device tensors."""
-    _check(load().ml_cic_backward(field, _dptr(dL_dM), _dptr(grad_lens), _dptr(grad_params),
-                                  _stream(stream)))
+    _check(load().ml_cic_backward_ex(field, _dptr(dL_dM), _dptr(grad_lens), _dptr(grad_params),
+                                     method, _stream(stream)))
 
 
 def ml_trace_rays(field, ray_idx, beta, pix, stream=None):
@@ -269,6 +273,8 @@ def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_A
     d.n_av = w.n_av
     d.map_x0, d.map_y0, d.map_x1, d.map_y1 = w.map_box
     d.map_nx, d.map_ny = w.map_n
+    if l1 is None:
+        l1 = getattr(w, "l1", None)
     if l1 is not None:
         d.l1_x, d.l1_y = l1
     d.l2_sub_x, d.l2_sub_y = l2_sub

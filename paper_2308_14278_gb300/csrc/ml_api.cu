@@ -56,6 +56,7 @@ struct ml_field {
     int32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_cursor = nullptr;
     double *d_sx = nullptr, *d_sy = nullptr, *d_sm = nullptr;
     int32_t *d_scell = nullptr;
+    int32_t *d_perm = nullptr;       // sorted position -> index in the caller's lens arrays
     double *d_coef64 = nullptr;
     unsigned char *d_nodes = nullptr;
     uint32_t *d_map_u32 = nullptr;
@@ -495,6 +496,7 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     ML_CK(f->alloc(&f->d_sy, n, s));
     ML_CK(f->alloc(&f->d_sm, n, s));
     ML_CK(f->alloc(&f->d_scell, n, s));
+    ML_CK(f->alloc(&f->d_perm, n, s));
     ML_CK(f->alloc(&f->d_stats, 8, s));
     ML_CK(f->alloc(&f->d_work, 1, s));
     ML_CK(f->alloc(&f->d_status, 1, s));
@@ -507,7 +509,7 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     ML_CK(launch_lens_cells(g, f->d_x, f->d_y, n, f->d_cell, f->d_count, s));
     ML_CK(launch_scan(f->d_count, f->d_start, NE + 1, s));
     ML_CK(launch_scatter(f->d_x, f->d_y, f->d_m, f->d_cell, n, f->d_start, NE + 1, f->d_cursor,
-                         f->d_sx, f->d_sy, f->d_sm, f->d_scell, s));
+                         f->d_sx, f->d_sy, f->d_sm, f->d_scell, f->d_perm, s));
     if (!nearfar) return ML_OK;
 
     // largest near list: the 3 x 3 block of each level-1 cell
@@ -1159,23 +1161,50 @@ ml_status ml_cic_forward(ml_field *f, float *mu, void *stream)
     return ml_magnification_map(f, ML_MAP_MU_F32, mu, 1, stream);
 }
 
-ml_status ml_cic_backward(ml_field *f, const float *dL_dM, double *grad_lens, double *grad_params,
-                          void *stream)
+ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens, double *grad_params,
+                             int32_t method, void *stream)
 {
     if (!f || !dL_dM || !grad_lens || !grad_params) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (method != ML_ADJOINT_NEARFAR && method != ML_ADJOINT_DIRECT)
+        return fail(ML_ERR_INVALID_ARG, "unknown adjoint method");
     if (f->g.deposit != ML_DEPOSIT_CIC || f->g.precision != ML_PREC_MIXED)
         return fail(ML_ERR_STATE, "the adjoint needs a field with ML_DEPOSIT_CIC and ML_PREC_MIXED");
     cudaStream_t s = (cudaStream_t)stream;
     const Geo &g = f->g;
+    const int64_t n = std::max<int64_t>(f->n_lens, 0);
     ShootArgs a = make_args(f);
-    a.ray_begin = 0;
-    a.ray_end = g.n3x * g.n3y;
     const double scale = (g.l3x * g.l3y) / (g.dpx * g.dpy);
-    ML_CK(cudaMemsetAsync(grad_lens, 0, sizeof(double) * 3 * (size_t)std::max<int64_t>(f->n_lens, 0), s));
+    ML_CK(cudaMemsetAsync(grad_lens, 0, sizeof(double) * 3 * (size_t)n, s));
     ML_CK(cudaMemsetAsync(grad_params, 0, sizeof(double) * 3, s));
-    ML_CK(launch_cic_adjoint(a, dL_dM, f->d_x, f->d_y, f->d_m, f->n_lens, grad_lens, grad_params, scale,
-                             f->num_sms, s));
+    if (method == ML_ADJOINT_DIRECT) {
+        a.ray_begin = 0;
+        a.ray_end = g.n3x * g.n3y;
+        ML_CK(launch_cic_adjoint_direct(a, dL_dM, f->d_x, f->d_y, f->d_m, f->n_lens, grad_lens,
+                                        grad_params, scale, f->num_sms, s));
+        return ML_OK;
+    }
+    set_tasks(a, g, 0, g.n3x * g.n3y);
+    const size_t n_mom = (size_t)(g.N2x * g.N2y) * (size_t)(g.p + 1);
+    double *gs = nullptr;
+    double2 *mom = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&gs, sizeof(double) * 3 * (size_t)std::max<int64_t>(n, 1), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&mom, sizeof(double2) * n_mom, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gs, 0, sizeof(double) * 3 * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mom, 0, sizeof(double2) * n_mom, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_work, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = launch_cic_adjoint_nearfar(a, dL_dM, gs, grad_params, mom, f->d_perm, grad_lens, scale,
+                                       f->num_sms, s);
+    if (gs) cudaFreeAsync(gs, s);
+    if (mom) cudaFreeAsync(mom, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint");
     return ML_OK;
+}
+
+ml_status ml_cic_backward(ml_field *f, const float *dL_dM, double *grad_lens, double *grad_params,
+                          void *stream)
+{
+    return ml_cic_backward_ex(f, dL_dM, grad_lens, grad_params, ML_ADJOINT_NEARFAR, stream);
 }
 
 ml_status ml_field_clear(ml_field *f, void *stream)

@@ -74,7 +74,8 @@ __global__ void k_scatter(const double *__restrict__ x, const double *__restrict
                           const double *__restrict__ m, const int32_t *__restrict__ cell, int64_t n,
                           const int32_t *__restrict__ start, int64_t nb, int32_t *cursor_g,
                           double *__restrict__ sx, double *__restrict__ sy,
-                          double *__restrict__ sm, int32_t *__restrict__ scell, int use_smem)
+                          double *__restrict__ sm, int32_t *__restrict__ scell,
+                          int32_t *__restrict__ perm, int use_smem)
 {
     extern __shared__ int32_t cur_s[];
     int32_t *cur = use_smem ? cur_s : cursor_g;
@@ -101,6 +102,7 @@ __global__ void k_scatter(const double *__restrict__ x, const double *__restrict
             sy[pos] = y[k];
             sm[pos] = m[k];
             scell[pos] = c;
+            perm[pos] = (int32_t)k;
         }
         __syncwarp();
     }
@@ -123,7 +125,7 @@ cudaError_t launch_scan(const int32_t *count, int32_t *start, int64_t nb, cudaSt
 cudaError_t launch_scatter(const double *x, const double *y, const double *m,
                            const int32_t *cell, int64_t n, const int32_t *start, int64_t nb,
                            int32_t *cursor, double *sx, double *sy, double *sm, int32_t *scell,
-                           cudaStream_t s)
+                           int32_t *perm, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     size_t smem = (size_t)nb * sizeof(int32_t);
@@ -134,7 +136,7 @@ cudaError_t launch_scatter(const double *x, const double *y, const double *m,
         if (e != cudaSuccess) return e;
     }
     k_scatter<<<1, 32, use_smem ? smem : 0, s>>>(x, y, m, cell, n, start, nb, cursor, sx, sy, sm,
-                                                 scell, use_smem);
+                                                 scell, perm, use_smem);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,7 @@ cudaError_t launch_scan(const int32_t *count, int32_t *start, int64_t nb, cudaSt
 cudaError_t launch_scatter(const double *x, const double *y, const double *m,
                            const int32_t *cell, int64_t n, const int32_t *start, int64_t nb,
                            int32_t *cursor, double *sx, double *sy, double *sm, int32_t *scell,
-                           cudaStream_t s);
+                           int32_t *perm, cudaStream_t s);
 cudaError_t launch_p_bound(const Geo &g, const LensTable &L, double *bound, cudaStream_t s);
 cudaError_t launch_coeffs_direct(const Geo &g, const LensTable &L, double *coef64, cudaStream_t s);
 cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64, double *scratch,
@@ -106,9 +106,13 @@ cudaError_t launch_shoot(const ShootArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_trace(const ShootArgs &a, const int64_t *idx, int64_t n, double *beta,
                          int32_t *pix, cudaStream_t s);
 cudaError_t launch_batch(const BatchArgs &b, int p, int num_sms, cudaStream_t s);
-cudaError_t launch_cic_adjoint(const ShootArgs &a, const float *G, const double *lx, const double *ly,
-                               const double *lm, int64_t n_lens, double *glens, double *gpar,
-                               double scale, int num_sms, cudaStream_t s);
+cudaError_t launch_cic_adjoint_direct(const ShootArgs &a, const float *G, const double *lx,
+                                      const double *ly, const double *lm, int64_t n_lens,
+                                      double *glens, double *gpar, double scale, int num_sms,
+                                      cudaStream_t s);
+cudaError_t launch_cic_adjoint_nearfar(const ShootArgs &a, const float *G, double *gs, double *gpar,
+                                       double2 *mom, const int32_t *perm, double *glens, double scale,
+                                       int num_sms, cudaStream_t s);
 cudaError_t launch_mu(const Geo &g, const uint32_t *cu, const float *cf, int want, void *out,
                       double scale, cudaStream_t s);
 cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *cf, double scale,

@@ -13,6 +13,7 @@
 //    reference-precision modes.
 //  - k_trace_*: the same arithmetic for listed rays, returning beta.
 #include "ml_internal.cuh"
+#include "ml_task.cuh"
 
 #include <math.h>
 
@@ -179,47 +180,6 @@ __global__ void __launch_bounds__(256) k_shoot_fp64(ShootArgs a)
 
 // ---- mixed precision: per-task staging and the walk --------------------------
 
-struct TaskShape {
-    int64_t row0, rows_end;         // ray rows of the task
-    int64_t c1x, c1y, c2a, c2b;     // level-1 cell, level-2 column range
-};
-
-__device__ __forceinline__ bool decode_task(const ShootArgs &a, int64_t t, TaskShape &ts)
-{
-    const Geo &g = a.g;
-    int64_t rg = a.rg_first + t / a.n_cc, cc = t % a.n_cc;
-    int64_t c1y = rg / a.groups_per_band, grp = rg % a.groups_per_band;
-    ts.c1y = c1y;
-    ts.row0 = c1y * g.n1y + 32 * grp;
-    ts.rows_end = min(min(ts.row0 + 32, (c1y + 1) * g.n1y), g.n3y);
-    ts.c1x = cc / a.cc_per_l1;
-    int64_t sub = cc % a.cc_per_l1;
-    ts.c2a = ts.c1x * g.l2sx + sub * a.l2_per_cc;
-    ts.c2b = min(min(ts.c2a + a.l2_per_cc, (ts.c1x + 1) * (int64_t)g.l2sx), g.N2x);
-    return ts.row0 < ts.rows_end && ts.c2a < ts.c2b;
-}
-
-// Near-lens list of level-1 cell (c1x, c1y): three runs of the sorted table.
-struct NearRuns {
-    int32_t s0, n0, s1, n1, s2, n2;
-    __device__ __forceinline__ int total() const { return n0 + n1 + n2; }
-    __device__ __forceinline__ int32_t index(int k) const
-    {
-        return k < n0 ? s0 + k : (k < n0 + n1 ? s1 + (k - n0) : s2 + (k - n0 - n1));
-    }
-};
-
-__device__ __forceinline__ NearRuns near_runs(const ShootArgs &a, int64_t c1x, int64_t c1y)
-{
-    NearRuns nr;
-    const int32_t *st = a.L.start;
-    int64_t b0 = c1y * a.g.NEx + c1x, b1 = b0 + a.g.NEx, b2 = b1 + a.g.NEx;
-    nr.s0 = st[b0]; nr.n0 = st[b0 + 3] - nr.s0;
-    nr.s1 = st[b1]; nr.n1 = st[b1 + 3] - nr.s1;
-    nr.s2 = st[b2]; nr.n2 = st[b2 + 3] - nr.s2;
-    return nr;
-}
-
 // Per-lane run-length state of the NGP deposit: consecutive rays of a lane's
 // walk usually land in the same pixel (the macro map compresses x), so counts
 // are merged and added with one atomic when the pixel changes.  The atomic's
@@ -270,52 +230,6 @@ __device__ __forceinline__ void finish_ray(const RowPoly<P> &rp, const ShootArgs
     Y = __fmaf_rn(-ay, a.ipy_f, Y);
     pixel_xy(X, Y, rp.bx, rp.by, gx, gy);
     if (!ok) { gx = -1; gy = -1; ++drop; }
-}
-
-// Task staging common to the mixed kernels: near lens list of the task's
-// level-1 cell as FP32 offsets from the first row (y) and, per level-2
-// column, from the node (x), with their rounding remainders.
-__device__ __forceinline__ int stage_near_y(const ShootArgs &a, const NearRuns &nr, double yref,
-                                            float4 *near, float2 *nlo, int lane)
-{
-    const int nn = nr.total();
-    __syncwarp();
-    for (int k = lane; k < nn; k += 32) {
-        int32_t idx = nr.index(k);
-        double dy = a.L.y[idx] - yref;
-        float hi = (float)dy;
-        near[k] = make_float4(0.f, hi, (float)a.L.m[idx], __int_as_float(idx));
-        nlo[k].y = (float)(dy - (double)hi);
-    }
-    return nn;
-}
-
-__device__ __forceinline__ void stage_near_x(const ShootArgs &a, int nn, double xnode,
-                                             float4 *near, float2 *nlo, int lane)
-{
-    __syncwarp();
-    for (int k = lane; k < nn; k += 32) {
-        double dx = a.L.x[__float_as_int(near[k].w)] - xnode;
-        float hi = (float)dx;
-        near[k].x = hi;
-        nlo[k].x = (float)(dx - (double)hi);
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ int64_t fetch_task(const ShootArgs &a, int lane, bool &stop)
-{
-    long long t = 0;
-    int ab = 0;
-    if (lane == 0) {
-        t = (long long)atomicAdd(a.work, 1ull);
-        ab = *a.abort_flag;
-    }
-    t = __shfl_sync(0xffffffffu, t, 0);
-    ab = __shfl_sync(0xffffffffu, ab, 0);
-    stop = ab != 0;
-    if (stop && lane == 0) atomicOr(a.status, 2u);
-    return t;
 }
 
 // Lane-valid ray of a warp-uniform walk position.
@@ -707,24 +621,6 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
     flush_stats(a, in, out, drop, pairs, lane == 0 ? tasks : 0, 0u);
 }
 
-// Near records computed from the FP64 lens table, for tracing single rays.
-struct GlobalNear {
-    const LensTable *L;
-    NearRuns nr;
-    double xnode, yref;
-    __device__ __forceinline__ float4 rec(int k) const
-    {
-        int32_t id = nr.index(k);
-        return make_float4((float)(L->x[id] - xnode), (float)(L->y[id] - yref), (float)L->m[id], 0.f);
-    }
-    __device__ __forceinline__ float2 lo(int k) const
-    {
-        int32_t id = nr.index(k);
-        double dx = L->x[id] - xnode, dy = L->y[id] - yref;
-        return make_float2((float)(dx - (double)(float)dx), (float)(dy - (double)(float)dy));
-    }
-};
-
 // ---- tracing: the same per-ray arithmetic for listed rays -------------------
 
 template <int P>
@@ -802,207 +698,6 @@ __global__ void k_trace_fp64(ShootArgs a, const int64_t *__restrict__ idx, int64
         pix[2 * q] = -1;
         pix[2 * q + 1] = -1;
     }
-}
-
-// ---- adjoint of the cloud-in-cell map --------------------------------------
-//
-// With M = (S_I / S_S) * CIC(rays) and G = dLoss/dM, each ray's dLoss/dbeta
-// follows from its four bilinear weights, and the chain rule through Eq. 6
-// gives (d = theta - theta_k, r^2 = |d|^2):
-//   dbeta/dkappa = (-theta_x, -theta_y),  dbeta/dgamma = (-theta_x, +theta_y),
-//   dbeta/dkappa_* = theta - c            (inside the sheet's disc),
-//   dbeta/dm_k = -d / r^2,  dbeta/dtheta_k = m_k (I r^2 - 2 d d^T) / r^4.
-// The lens terms use the exact point-mass derivative for every lens; the
-// forward's far series differs from the direct sum only by its truncation
-// (far_bound).  Rays are recomputed with the forward's own arithmetic.
-
-constexpr int ADJ_THREADS = 256;
-constexpr int ADJ_LPT = 4;                          // lenses per thread per pass
-
-// Position (pixel units) of ray r by exactly the mixed forward's arithmetic.
-template <int P>
-__device__ __forceinline__ bool forward_ray(const ShootArgs &a, int64_t r, float &X, float &Y, int &bx,
-                                            int &by)
-{
-    const Geo &g = a.g;
-    int64_t i = r % g.n3x, j = r / g.n3x;
-    int64_t c1x = i / g.n1x, c1y = j / g.n1y;
-    int64_t c2x = i / g.n2x, c2y = j / g.n2y;
-    int64_t row0 = c1y * g.n1y + 32 * ((j - c1y * g.n1y) / 32);
-    double yref = g.ry0 + ((double)row0 + 0.5) * g.l3y;
-    double xnode = g.rx0 + ((double)c2x + 0.5) * g.l2x;
-    const double dyl_d = (double)(j - row0) * g.l3y;
-    const float dyl = (float)dyl_d;
-    const float dyl_lo = (float)(dyl_d - (double)dyl);
-    float qf = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
-    RowPoly<P> rp;
-    row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), qf, a, rp);
-    float u = __fadd_rn((float)(i - c2x * g.n2x), a.c0_f);
-    float tt = __fmul_rn(u, a.l3x_f);
-    float ax, ay, mn;
-    row_eval<P>(rp, tt, X, Y);
-    const NearRuns nr = near_runs(a, c1x, c1y);
-    const GlobalNear nl{&a.L, nr, xnode, yref};
-    const int nn = nr.total();
-    near_sum_f32(nl, nn, tt, dyl, ax, ay, mn);
-    bool ok = true;
-    if (mn < a.rc2) ok = near_sum_hilo(nl, nn, u, tt, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
-    X = __fmaf_rn(-ax, a.ipx_f, X);
-    Y = __fmaf_rn(-ay, a.ipy_f, Y);
-    bx = rp.bx;
-    by = rp.by;
-    return ok;
-}
-
-// Grid (ray tiles, lens passes).  Pass y handles lenses [y * T * LPT, ...).
-template <int P>
-__global__ void __launch_bounds__(ADJ_THREADS) k_cic_adjoint(ShootArgs a, const float *__restrict__ G,
-                                                            const double *__restrict__ lx,
-                                                            const double *__restrict__ ly,
-                                                            const double *__restrict__ lm,
-                                                            int64_t n_lens, double *__restrict__ glens,
-                                                            double *__restrict__ gpar, double scale)
-{
-    __shared__ float4 rays[ADJ_THREADS];    // (theta - ref, dL/dbeta)
-    __shared__ int cnt;
-    __shared__ double red[3][ADJ_THREADS / 32];
-    const Geo &g = a.g;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t lens0 = (int64_t)blockIdx.y * ADJ_THREADS * ADJ_LPT;
-    double sx[ADJ_LPT], sy[ADJ_LPT], sm[ADJ_LPT];
-#pragma unroll
-    for (int q = 0; q < ADJ_LPT; ++q) { sx[q] = 0.0; sy[q] = 0.0; sm[q] = 0.0; }
-    double pk = 0.0, pg = 0.0, ps = 0.0;
-    // A tile is a segment of one lattice row, so ray offsets from its centre
-    // stay below 128 l3 and the FP32 differences theta - theta_k keep their
-    // relative precision down to the closest rays.
-    const int64_t nseg = (g.n3x + ADJ_THREADS - 1) / ADJ_THREADS;
-    const int64_t j_lo = a.ray_begin / g.n3x, j_hi = (a.ray_end - 1) / g.n3x;
-    const int64_t n_tiles = (j_hi - j_lo + 1) * nseg;
-    const float ipx = (float)(scale / g.dpx), ipy = (float)(scale / g.dpy);
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int64_t jt = j_lo + tile / nseg, i0 = (tile % nseg) * ADJ_THREADS;
-        const double refx = g.rx0 + ((double)i0 + (0.5 * ADJ_THREADS + 0.5)) * g.l3x;
-        const double refy = g.ry0 + ((double)jt + 0.5) * g.l3y;
-        if (tid == 0) cnt = 0;
-        __syncthreads();
-        // phase A: this thread's ray, its dLoss/dbeta, the parameter terms
-        const int64_t it = i0 + tid, r = jt * g.n3x + it;
-        float gbx = 0.f, gby = 0.f;
-        double tx = 0.0, ty = 0.0;
-        if (it < g.n3x && r >= a.ray_begin && r < a.ray_end) {
-            float X, Y;
-            int bxi, byi;
-            if (forward_ray<P>(a, r, X, Y, bxi, byi)) {
-                float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
-                float flx, fly;
-                int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
-                float wx = __fsub_rn(fx, flx), wy = __fsub_rn(fy, fly);
-                unsigned ix = (unsigned)bxi + (unsigned)kx, iy = (unsigned)byi + (unsigned)ky;
-                float Gv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    unsigned px = ix + (unsigned)(q & 1), py = iy + (unsigned)(q >> 1);
-                    Gv[q] = (px < (unsigned)g.mnx && py < (unsigned)g.mny)
-                                ? G[(size_t)py * (unsigned)g.mnx + px] : 0.f;
-                }
-                gbx = ipx * ((Gv[1] - Gv[0]) * (1.f - wy) + (Gv[3] - Gv[2]) * wy);
-                gby = ipy * ((Gv[2] - Gv[0]) * (1.f - wx) + (Gv[3] - Gv[1]) * wx);
-            }
-            tx = g.rx0 + ((double)it + 0.5) * g.l3x;
-            ty = refy;
-        }
-        const bool live = gbx != 0.f || gby != 0.f;
-        if (live && blockIdx.y == 0) {
-            pk += -(double)gbx * tx - (double)gby * ty;
-            pg += -(double)gbx * tx + (double)gby * ty;
-            ps += (double)gbx * (tx - g.sheet_cx) + (double)gby * (ty - g.sheet_cy);
-        }
-        // compact the live rays of the tile
-        const unsigned bal = __ballot_sync(0xffffffffu, live);
-        int wbase = 0;
-        if (lane == 0 && bal) wbase = atomicAdd(&cnt, __popc(bal));
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        if (live) {
-            int slot = wbase + __popc(bal & ((1u << lane) - 1u));
-            rays[slot] = make_float4((float)(tx - refx), (float)(ty - refy), gbx, gby);
-        }
-        __syncthreads();
-        // phase B: this thread's lenses against the tile's live rays
-        const int nlive = cnt;
-        if (nlive > 0) {
-            float ox[ADJ_LPT], oy[ADJ_LPT], ax[ADJ_LPT], ay[ADJ_LPT], am[ADJ_LPT];
-#pragma unroll
-            for (int q = 0; q < ADJ_LPT; ++q) {
-                int64_t k = lens0 + tid + (int64_t)q * ADJ_THREADS;
-                bool have = k < n_lens;
-                ox[q] = have ? (float)(lx[k] - refx) : 1.0e18f;
-                oy[q] = have ? (float)(ly[k] - refy) : 1.0e18f;
-                ax[q] = 0.f; ay[q] = 0.f; am[q] = 0.f;
-            }
-            for (int jr = 0; jr < nlive; ++jr) {
-                const float4 R = rays[jr];
-#pragma unroll
-                for (int q = 0; q < ADJ_LPT; ++q) {
-                    float dx = R.x - ox[q], dy = R.y - oy[q];
-                    float r2 = fmaf(dx, dx, dy * dy);
-                    float inv = rcp_approx(r2);
-                    float t = fmaf(R.z, dx, R.w * dy) * inv;       // (dL/dbeta . d) / r^2
-                    float u2 = 2.f * t * inv;
-                    am[q] += t;
-                    ax[q] += fmaf(R.z, inv, -dx * u2);
-                    ay[q] += fmaf(R.w, inv, -dy * u2);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < ADJ_LPT; ++q) { sx[q] += ax[q]; sy[q] += ay[q]; sm[q] += am[q]; }
-        }
-        __syncthreads();
-    }
-    // lens gradients: dL/dx_k = m_k * sum(...), dL/dm_k = -sum(t)
-#pragma unroll
-    for (int q = 0; q < ADJ_LPT; ++q) {
-        int64_t k = lens0 + tid + (int64_t)q * ADJ_THREADS;
-        if (k >= n_lens) continue;
-        atomicAdd(glens + 3 * k + 0, lm[k] * sx[q]);
-        atomicAdd(glens + 3 * k + 1, lm[k] * sy[q]);
-        atomicAdd(glens + 3 * k + 2, -sm[q]);
-    }
-    if (blockIdx.y == 0) {
-        for (int o = 16; o > 0; o >>= 1) {
-            pk += __shfl_down_sync(0xffffffffu, pk, o);
-            pg += __shfl_down_sync(0xffffffffu, pg, o);
-            ps += __shfl_down_sync(0xffffffffu, ps, o);
-        }
-        if (lane == 0) { red[0][wid] = pk; red[1][wid] = pg; red[2][wid] = ps; }
-        __syncthreads();
-        if (tid < 3) {
-            double v = 0.0;
-            for (int w = 0; w < ADJ_THREADS / 32; ++w) v += red[tid][w];
-            atomicAdd(gpar + tid, v);
-        }
-    }
-}
-
-cudaError_t launch_cic_adjoint(const ShootArgs &a, const float *G, const double *lx, const double *ly,
-                               const double *lm, int64_t n_lens, double *glens, double *gpar,
-                               double scale, int num_sms, cudaStream_t s)
-{
-    if (a.ray_end <= a.ray_begin) return cudaSuccess;
-    const int64_t tiles = ((a.ray_end - 1) / a.g.n3x - a.ray_begin / a.g.n3x + 1) *
-                          ((a.g.n3x + ADJ_THREADS - 1) / ADJ_THREADS);
-    int64_t bx = std::min<int64_t>(tiles, (int64_t)num_sms * 8);
-    int64_t by = std::max<int64_t>(1, (n_lens + ADJ_THREADS * ADJ_LPT - 1) / (ADJ_THREADS * ADJ_LPT));
-    if (by > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)bx, (unsigned)by);
-    switch (a.g.p) {
-#define ML_ADJ_CASE(PP) case PP: k_cic_adjoint<PP><<<grid, ADJ_THREADS, 0, s>>>(a, G, lx, ly, lm, n_lens, glens, gpar, scale); break;
-    ML_ADJ_CASE(1) ML_ADJ_CASE(2) ML_ADJ_CASE(3) ML_ADJ_CASE(4) ML_ADJ_CASE(5)
-    ML_ADJ_CASE(6) ML_ADJ_CASE(8) ML_ADJ_CASE(10) ML_ADJ_CASE(12) ML_ADJ_CASE(16)
-#undef ML_ADJ_CASE
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
 }
 
 // ---- dispatch ----------------------------------------------------------------
