@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "batched", "differentiable"],
+                    help="paper: one 1e11-ray map (the headline line); batched: 80 maps in one "
+                         "graph-captured persistent launch against the same maps one at a time; "
+                         "differentiable: CIC forward + adjoint of 1,000 lenses and 4e8 rays")
     ap.add_argument("--rays", type=float, default=1e11)
     ap.add_argument("--map-px", type=int, default=8192)
     ap.add_argument("--no-e2e", action="store_true")
@@ -347,6 +351,324 @@ def cpu_baseline(w, target_s: float = 12.0):
 
 
 # ---------------------------------------------------------------------------
+# batched maps: one graph-captured persistent launch over 80 maps
+# ---------------------------------------------------------------------------
+
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def run_batched(args, rank, world, local):
+    """80 heterogeneous maps (2,000-20,000 lenses, 1e9-1e10 rays, 4096^2) and
+    their 800 light curves as one CUDA-graph replay of the batched launch,
+    next to the same maps shot one at a time with their own default grids."""
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2308_14278_gb300 as ml
+    from paper_2308_14278_gb300 import inputs
+    ml.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n_maps, tpm, map_px = 80, 10, 4096
+    ws = inputs.batched_maps(n_maps=n_maps, seed=rank, map_px=map_px, ray_range=(1e9, 1e10),
+                             tracks_per_map=tpm)
+    tracks = np.stack([inputs.tracks(tpm, map_px, map_px, 4 * SIGMA_PX + 1, seed=500 + 100 * rank + i)
+                       for i in range(n_maps)])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    t0 = time.perf_counter()
+    descs = [ml.make_desc(w, precision=ml.PREC_MIXED, tune=True) for w in ws]
+    b = ml.Batch(descs, tracks=tracks, n_samples=TRACK_SAMPLES, sigma_px=SIGMA_PX)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    infos = [b.info(i) for i in range(n_maps)]
+    rays = sum(i["n_rays_x"] * i["n_rays_y"] for i in infos)
+    orders = sorted({i["taylor_p"] for i in infos})
+    for _ in range(args.warmup):
+        b.run(use_graph=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e = _events(torch, 2)
+            e[0].record(stream)
+            b.run(use_graph=True)
+            e[1].record(stream)
+            times.append(e)
+        torch.cuda.synchronize()
+    step_ms = float(np.mean([a.elapsed_time(c) for a, c in times]))
+    stats = [b.stats(i) for i in range(n_maps)]
+    t_local = step_ms
+    if dist:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_local = float(t.item())
+    value = rays * world / (t_local / 1e3)
+
+    # the same maps one at a time: own field, own default grid and order
+    fields = [ml.Field(w, precision=ml.PREC_MIXED) for w in ws]
+    mu1 = torch.empty((map_px, map_px), dtype=torch.float32, device="cuda")
+    lc1 = torch.empty((tpm, TRACK_SAMPLES), dtype=torch.float32, device="cuda")
+
+    def one_at_a_time():
+        for f, tr in zip(fields, tracks):
+            f.clear(stream)
+            f.shoot(stream=stream)
+            ml.ml_magnification_map(f.h, ml.MAP_MU_F32, mu1, stream)
+            ml.ml_light_curves(f.h, tr, TRACK_SAMPLES, SIGMA_PX, lc1, stream)
+
+    one_at_a_time()
+    single = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush.zero_()
+        e = _events(torch, 2)
+        e[0].record(stream)
+        one_at_a_time()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        single.append(e[0].elapsed_time(e[1]))
+    single_ms = float(np.mean(single))
+    single_p = sorted({f.info["taylor_p"] for f in fields})
+    for f in fields:
+        f.close()
+
+    flops = sum(11.0 * st["near_pairs"] + (4.0 * i["taylor_p"] + 6.0) * i["n_rays_x"] * i["n_rays_y"]
+                for st, i in zip(stats, infos))
+    achieved = flops / (step_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out = {
+        "metric": "rays/s of 80 batched maps on 1 GB300 (one CUDA graph, a persistent launch per Taylor order)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_local, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 near sum + f64 nodes", "data": "synthetic (seeded lognormal lens discs; no dataset)",
+        "config": {"workload": f"batched: {n_maps} maps, 2,000-20,000 lenses, kappa_* in "
+                               f"{{0.002, 0.005, 0.01}}, kappa+gamma 0.95-0.99, 1e9-1e10 rays each, "
+                               f"{map_px}^2 uint32, {n_maps * tpm} light curves x {TRACK_SAMPLES}",
+                   "total_rays": int(rays), "taylor_p": orders, "tuned_grids": True,
+                   "launches_per_step": len(orders),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"independent batches per GPU x{world}"},
+        "create_s": create_s,
+        "one_map_at_a_time": {"ms_per_step": single_ms, "value": rays / (single_ms / 1e3),
+                              "taylor_p": single_p, "speedup_of_batched": single_ms / step_ms},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_shoot_batch",
+                     "note": "whole graph step time (clear, shoot, mu, curves) as the kernel time",
+                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+        "rays_check": {"conserved": all(st["rays_in"] + st["rays_out"] + st["rays_dropped"] ==
+                                        i["n_rays_x"] * i["n_rays_y"] for st, i in zip(stats, infos))},
+        "gpu_launches": int(args.steps * (len(orders) + 2 * n_maps)),
+    }
+    clk_sum = clk.summary()
+    if clk_sum:
+        out["clocks"] = clk_sum
+    if not args.no_e2e:
+        # through the public API from host buffers: create from host lens arrays,
+        # run, read the 800 light curves back to pinned host memory
+        curves_h = torch.empty((n_maps, tpm, TRACK_SAMPLES), dtype=torch.float32).pin_memory()
+        b.close()
+        te = []
+        for _ in range(max(1, min(args.steps, 2))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bb = ml.Batch([ml.make_desc(w, precision=ml.PREC_MIXED, tune=True) for w in ws],
+                          tracks=tracks, n_samples=TRACK_SAMPLES, sigma_px=SIGMA_PX)
+            bb.run(use_graph=True)
+            ml._check(ml.load().ml_batch_curves(bb.h, curves_h.numpy().ctypes.data, 0, None))
+            torch.cuda.synchronize()
+            te.append(time.perf_counter() - t0)
+            bb.close()
+        t = float(np.mean(te))
+        out["e2e"] = {"value": rays / t, "unit": UNIT, "ms_per_step": t * 1e3,
+                      "h2d_bytes_per_step": int(sum(24 * w.lenses.n for w in ws) + tracks.nbytes),
+                      "d2h_bytes_per_step": int(4 * n_maps * tpm * TRACK_SAMPLES),
+                      "note": "includes batch creation (tuned grids cached per process)"}
+    else:
+        b.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(ws[0], target_s=10.0)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# differentiable map: CIC forward + hand-written adjoint
+# ---------------------------------------------------------------------------
+
+def run_differentiable(args, rank, world, local):
+    """One optimisation step of a lens field against a target map: create the
+    field from device lens arrays, the CIC map (ml_cic_forward), dL/dM of
+    L = |M - T|^2, and the adjoint (ml_cic_backward) to d/d(x_k, y_k, m_k,
+    kappa, gamma, kappa_*).  1,000 lenses, 4e8 rays, 1024^2 float32."""
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2308_14278_gb300 as ml
+    from paper_2308_14278_gb300 import inputs
+    ml.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = inputs.differentiable_field(seed=rank)
+    wt = inputs.differentiable_field(seed=rank + 1000)        # target from a perturbed seed
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    ny, nx = w.map_n[1], w.map_n[0]
+    T = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    ft = ml.Field(wt, precision=ml.PREC_MIXED, deposit=ml.DEPOSIT_CIC)
+    ml.ml_cic_forward(ft.h, T)
+    ft.close()
+    lens_dev = [torch.from_numpy(a).to(dev) for a in (w.lenses.x, w.lenses.y, w.lenses.m)]
+    mu = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    G = torch.empty_like(mu)
+    gl = torch.empty((w.lenses.n, 3), dtype=torch.float64, device=dev)
+    gp = torch.empty(3, dtype=torch.float64, device=dev)
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def desc():
+        d = ml.make_desc(w, precision=ml.PREC_MIXED, deposit=ml.DEPOSIT_CIC)
+        d.lens_x, d.lens_y, d.lens_m = (t.data_ptr() for t in lens_dev)
+        d.lens_mem_is_device = 1
+        return d
+
+    hold = {}
+
+    def step(e=None):
+        if e: e[0].record(stream)
+        h = ml.ml_field_create(desc(), stream)
+        if e: e[1].record(stream)
+        ml.ml_cic_forward(h, mu, stream)
+        if e: e[2].record(stream)
+        torch.sub(mu, T, out=G)                       # dL/dM = 2 (M - T), the caller's loss
+        torch.sum(G.double() ** 2, dim=(0, 1), out=loss)
+        G.mul_(2.0)
+        if e: e[3].record(stream)
+        ml.ml_cic_backward(h, G, gl, gp, stream)
+        if e: e[4].record(stream)
+        hold["info"] = ml.ml_field_info(h)
+        hold["stats"] = ml.ml_field_stats(h, stream)[0]
+        ml.ml_field_destroy(h)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    timers = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e = _events(torch, 5)
+            step(e)
+            timers.append(e)
+        torch.cuda.synchronize()
+    per = np.array([[a.elapsed_time(c) for a, c in zip(e[:-1], e[1:])] for e in timers])
+    step_ms = float(per.sum(axis=1).mean())
+    info, stats = hold["info"], hold["stats"]
+    n_rays = info["n_rays_x"] * info["n_rays_y"]
+    t_local = step_ms
+    if dist:
+        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_local = float(t.item())
+    value = n_rays * world / (t_local / 1e3)
+    p = info["taylor_p"]
+    bw_ms = float(per[:, 3].mean())
+    live = stats["rays_in"] / max(1, n_rays)
+    pairs = stats["near_pairs"]
+    # adjoint work: the forward recomputed (11 per near pair + 4p + 6 per ray),
+    # then per live ray the CIC gradient and node moments (5p + 25) and 15 per
+    # near pair in the near pass
+    flops = 11.0 * pairs + (4.0 * p + 6.0) * n_rays + live * (15.0 * pairs + (5.0 * p + 25.0) * n_rays)
+    achieved = flops / (bw_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out = {
+        "metric": "rays/s of a CIC forward + adjoint step (1,000 lenses, 4e8 rays) on 1 GB300",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_local, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 near sum + f64 nodes, f64 gradient sums",
+        "data": "synthetic (seeded lognormal lens disc; target map from seed + 1000)",
+        "config": {"workload": w.name + ", loss |M - T|^2, gradient w.r.t. all lenses, kappa, gamma, "
+                               "kappa_*", "n_lenses": int(w.lenses.n), "n_rays": int(n_rays),
+                   "taylor_p": p, "far_bound_theta_e": info["far_bound"],
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"independent fields per GPU x{world}"},
+        "breakdown_ms": {"create": float(per[:, 0].mean()), "forward": float(per[:, 1].mean()),
+                         "loss": float(per[:, 2].mean()), "backward": bw_ms},
+        "loss": float(loss.item()),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_adj_rays + k_adj_far",
+                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+        "gpu_launches": int(args.steps * 14),
+    }
+    clk_sum = clk.summary()
+    if clk_sum:
+        out["clocks"] = clk_sum
+    if not args.no_e2e:
+        host = (w.lenses.x, w.lenses.y, w.lenses.m)
+        gl_h = torch.empty((w.lenses.n, 3), dtype=torch.float64).pin_memory()
+        gp_h = torch.empty(3, dtype=torch.float64).pin_memory()
+        te = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = ml.ml_field_create(ml.make_desc(w, precision=ml.PREC_MIXED, deposit=ml.DEPOSIT_CIC,
+                                                lens_arrays=host), stream)
+            ml.ml_cic_forward(h, mu, stream)
+            torch.sub(mu, T, out=G)
+            torch.sum(G.double() ** 2, dim=(0, 1), out=loss)
+            G.mul_(2.0)
+            ml.ml_cic_backward(h, G, gl, gp, stream)
+            gl_h.copy_(gl, non_blocking=True)
+            gp_h.copy_(gp, non_blocking=True)
+            lv = float(loss.item())
+            ml.ml_field_destroy(h)
+            torch.cuda.synchronize()
+            te.append(time.perf_counter() - t0)
+        t = float(np.mean(te))
+        out["e2e"] = {"value": n_rays / t, "unit": UNIT, "ms_per_step": t * 1e3,
+                      "h2d_bytes_per_step": int(24 * w.lenses.n),
+                      "d2h_bytes_per_step": int(gl_h.numel() * 8 + 24 + 8), "loss": lv}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_grad(w, ml)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline_grad(w, ml, target_s: float = 10.0):
+    """The oracle's FP64 CIC gradient (every ray against every lens) on all
+    host cores, on a contiguous block of rays of the same lattice."""
+    import oracle
+    g = oracle.geometry_of(w)
+    threads = oracle.default_threads()
+    T = np.zeros((g.mny, g.mnx))
+    r0 = (g.n3y // 2) * g.n3x
+    n = 200000
+    t0 = time.perf_counter()
+    oracle.cic_grad(g, w.lenses.x, w.lenses.y, w.lenses.m, T, r0, r0 + n, threads)
+    dt = time.perf_counter() - t0
+    n2 = int(min(5e7, max(n, n * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.cic_grad(g, w.lenses.x, w.lenses.y, w.lenses.m, T, r0, r0 + n2, threads)
+    dt = time.perf_counter() - t0
+    return {"value": n2 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n2} consecutive rays of the {g.n_rays:.3g}-ray lattice: CIC map and "
+                      f"FP64 gradient against all {w.lenses.n} lenses", "seconds": dt}
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
 
@@ -396,6 +718,10 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "batched":
+        out = run_batched(args, rank, world, local)
+    elif args.workload == "differentiable":
+        out = run_differentiable(args, rank, world, local)
     else:
         out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

@@ -319,13 +319,15 @@ ml_status ml_field_abort(ml_field *f, int32_t on);
 ml_status ml_field_destroy(ml_field *f);
 
 /*
- * Batched maps (many heterogeneous magnification maps in one persistent
- * launch; the paper's statistics use 80 maps and 800 light curves, §4.2).
+ * Batched maps (many heterogeneous magnification maps in one CUDA graph of
+ * persistent launches; the paper's statistics use 80 maps and 800 light
+ * curves, §4.2).
  *
  * ml_batch_create - create n fields from descs[0..n) (ML_PREC_MIXED and
  * ML_DEPOSIT_NGP only).  Each field's Taylor order is planned from its own
- * truncation bound; all are then built with the largest, so that one kernel
- * serves every map (a higher order only lowers the error).  With
+ * truncation bound; a field with tune != 0 (and no level-2 subdivision given)
+ * first takes the level-2 grid the autotuner's cost model ranks first for it.
+ * Maps of one compiled order share one persistent launch.  With
  * tracks_per_map > 0, `tracks` (host, n x tracks_per_map x 4, map pixel
  * coordinates) are kept on the device for the light curves of each run.
  * Synchronises `stream`.  Errors as ml_field_create, plus ML_ERR_UNSUPPORTED
@@ -338,8 +340,9 @@ ml_status ml_batch_create(const ml_field_desc *descs, int32_t n, int32_t tracks_
 
 /*
  * ml_batch_run - one step of the whole batch, ordered on `stream`: zero all
- * maps and counters, shoot every ray of every map in ONE persistent kernel
- * launch (warps take tasks of all maps from one queue), convert every map to
+ * maps and counters, shoot every ray of every map with one persistent kernel
+ * launch per Taylor order present (its warps take tasks of all its maps from
+ * one queue), convert every map to
  * mu (Eq. 12) into the batch's buffers and compute the light curves.  With
  * use_graph != 0 the step is captured once into a CUDA graph on the batch's
  * internal stream and replayed by every later call.

@@ -679,13 +679,19 @@ void set_tasks(ShootArgs &a, const Geo &g, int64_t b, int64_t e)
 // Many maps run as one: fields, their kernel arguments on the device, the
 // task prefix sums, and the buffers of the step's outputs.
 struct ml_batch {
-    int device = 0, num_sms = 0, p = 0, near_cap = 1;
+    // maps that share a Taylor order run in one persistent launch
+    struct Group {
+        int p = 0, near_cap = 1;
+        std::vector<int> maps;
+        ShootArgs *d_args = nullptr;
+        int64_t *d_base = nullptr;
+        unsigned long long *d_work = nullptr;
+        int64_t total_tasks = 0;
+    };
+    int device = 0, num_sms = 0;
+    std::vector<Group> groups;
     std::vector<ml_field *> fields;
     std::vector<size_t> mu_off;
-    ShootArgs *d_args = nullptr;
-    int64_t *d_base = nullptr;
-    int64_t total_tasks = 0;
-    unsigned long long *d_work = nullptr;
     unsigned int *d_status = nullptr;
     int *h_abort = nullptr, *d_abort = nullptr;
     float *d_mu = nullptr;
@@ -741,18 +747,20 @@ cudaError_t batch_enqueue(ml_batch *b, cudaStream_t s)
         if ((e = cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     }
-    if ((e = cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-    BatchArgs ba;
-    ba.args = b->d_args;
-    ba.task_base = b->d_base;
-    ba.n_maps = (int)b->fields.size();
-    ba.near_cap = b->near_cap;
-    ba.total_tasks = b->total_tasks;
-    ba.work = b->d_work;
-    ba.abort_flag = b->d_abort;
-    ba.status = b->d_status;
-    if ((e = launch_batch(ba, b->p, b->num_sms, s)) != cudaSuccess) return e;
+    for (const ml_batch::Group &gr : b->groups) {
+        if ((e = cudaMemsetAsync(gr.d_work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+        BatchArgs ba;
+        ba.args = gr.d_args;
+        ba.task_base = gr.d_base;
+        ba.n_maps = (int)gr.maps.size();
+        ba.near_cap = gr.near_cap;
+        ba.total_tasks = gr.total_tasks;
+        ba.work = gr.d_work;
+        ba.abort_flag = b->d_abort;
+        ba.status = b->d_status;
+        if ((e = launch_batch(ba, gr.p, b->num_sms, s)) != cudaSuccess) return e;
+    }
     for (size_t i = 0; i < b->fields.size(); ++i) {
         const ml_field *f = b->fields[i];
         const Geo &g = f->g;
@@ -780,12 +788,10 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
         if (descs[i].precision != ML_PREC_MIXED || descs[i].deposit != ML_DEPOSIT_NGP)
             return fail(ML_ERR_UNSUPPORTED, "batches take ML_PREC_MIXED with ML_DEPOSIT_NGP");
     }
-    // Tuned maps: choose one Taylor order for the launch jointly.  For every
-    // compiled order P each map takes its cheapest grid whose order is <= P;
-    // the order with the smallest summed predicted time wins.
+    // Tuned maps take the grid the cost model ranks first for them, each
+    // with its own Taylor order; maps of one order share a persistent launch.
     std::vector<ml_field_desc> plan(descs, descs + n);
-    std::vector<std::vector<TuneCand>> cands(n);
-    bool any_tuned = false;
+    std::vector<char> tuned(n, 0);
     for (int32_t i = 0; i < n; ++i) {
         if (!(plan[i].tune && plan[i].l2_sub_x == 0 && plan[i].l2_sub_y == 0)) continue;
         std::vector<double> hx, hy, hm;
@@ -802,73 +808,70 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
             if (e == cudaSuccess) e = cudaMemcpyAsync(dy, hy.data(), hy.size() * sizeof(double), cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(dm, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, s);
         }
-        if (e == cudaSuccess) st = tune_candidates(plan[i], hx, hy, hm, dx, dy, dm, s, cands[i]);
+        GridChoice best;
+        if (e == cudaSuccess) st = tune_grid(plan[i], hx, hy, hm, dx, dy, dm, s, best);
         cudaFreeAsync(dx, s);
         cudaFreeAsync(dy, s);
         cudaFreeAsync(dm, s);
         if (e != cudaSuccess) return cuda_fail(e, "batch tuner");
         if (st != ML_OK) return st;
-        any_tuned = any_tuned || !cands[i].empty();
-    }
-    if (any_tuned) {
-        static const int orders[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
-        double best_total = -1.0;
-        int best_P = 0;
-        for (int P : orders) {
-            double total = 0.0;
-            bool ok = true;
-            for (int32_t i = 0; i < n && ok; ++i) {
-                if (cands[i].empty()) continue;
-                double m = -1.0;
-                for (const TuneCand &c : cands[i])
-                    if (c.P <= P && (m < 0.0 || cand_cost(c, P) < m)) m = cand_cost(c, P);
-                if (m < 0.0) ok = false; else total += m;
-            }
-            if (ok && (best_total < 0.0 || total < best_total)) { best_total = total; best_P = P; }
-        }
-        for (int32_t i = 0; i < n; ++i) {
-            if (cands[i].empty()) continue;
-            const TuneCand *pick = nullptr;
-            for (const TuneCand &c : cands[i])
-                if (c.P <= best_P && (!pick || cand_cost(c, best_P) < cand_cost(*pick, best_P))) pick = &c;
-            if (pick) { plan[i].l2_sub_x = pick->sx; plan[i].l2_sub_y = pick->sy; }
+        if (best.p > 0) {
+            plan[i].l2_sub_x = best.sx;
+            plan[i].l2_sub_y = best.sy;
+            tuned[i] = 1;
         }
     }
-    // plan every map, then build all with the largest planned order
     b->fields.assign(n, nullptr);
-    int P = 1;
+    std::vector<int> order(n);
     for (int32_t i = 0; i < n; ++i) {
         b->fields[i] = new (std::nothrow) ml_field();
         if (!b->fields[i]) return fail(ML_ERR_OOM, "host allocation failed");
         ml_status st = create_plan(&plan[i], s, b->fields[i]);
         if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
-        if (!cands[i].empty()) b->fields[i]->tuned = 1;
-        P = std::max(P, planned_order(b->fields[i]));
+        b->fields[i]->tuned = tuned[i];
+        order[i] = planned_order(b->fields[i]);
+        st = create_finish(b->fields[i], order[i], s);
+        if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
     }
-    b->p = P;
-    std::vector<ShootArgs> args(n);
-    std::vector<int64_t> base(n + 1, 0);
+    b->num_sms = b->fields[0]->num_sms;
     size_t mu_total = 0;
     for (int32_t i = 0; i < n; ++i) {
-        ml_field *f = b->fields[i];
-        ml_status st = create_finish(f, P, s);
-        if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
-        args[i] = make_args(f);
-        set_tasks(args[i], f->g, 0, f->g.n3x * f->g.n3y);
-        b->near_cap = std::max(b->near_cap, args[i].near_cap);
-        base[i + 1] = base[i] + args[i].n_tasks;
         b->mu_off.push_back(mu_total);
-        mu_total += (size_t)f->g.mnx * f->g.mny;
+        mu_total += (size_t)b->fields[i]->g.mnx * b->fields[i]->g.mny;
     }
-    b->num_sms = b->fields.empty() ? 1 : b->fields[0]->num_sms;
-    b->total_tasks = base[n];
-    ML_CK(b->alloc(&b->d_args, n, s));
-    ML_CK(b->alloc(&b->d_base, n + 1, s));
-    ML_CK(b->alloc(&b->d_work, 1, s));
+    for (int32_t i = 0; i < n; ++i) {
+        const int P = b->fields[i]->g.p;
+        auto it = std::find_if(b->groups.begin(), b->groups.end(),
+                               [P](const ml_batch::Group &gr) { return gr.p == P; });
+        if (it == b->groups.end()) {
+            b->groups.emplace_back();
+            b->groups.back().p = P;
+            it = b->groups.end() - 1;
+        }
+        it->maps.push_back(i);
+    }
+    for (ml_batch::Group &gr : b->groups) {
+        const size_t m = gr.maps.size();
+        std::vector<ShootArgs> args(m);
+        std::vector<int64_t> base(m + 1, 0);
+        for (size_t q = 0; q < m; ++q) {
+            ml_field *f = b->fields[gr.maps[q]];
+            args[q] = make_args(f);
+            set_tasks(args[q], f->g, 0, f->g.n3x * f->g.n3y);
+            gr.near_cap = std::max(gr.near_cap, args[q].near_cap);
+            base[q + 1] = base[q] + args[q].n_tasks;
+        }
+        gr.total_tasks = base[m];
+        ML_CK(b->alloc(&gr.d_args, m, s));
+        ML_CK(b->alloc(&gr.d_base, m + 1, s));
+        ML_CK(b->alloc(&gr.d_work, 1, s));
+        ML_CK(cudaMemcpyAsync(gr.d_args, args.data(), sizeof(ShootArgs) * m, cudaMemcpyHostToDevice, s));
+        ML_CK(cudaMemcpyAsync(gr.d_base, base.data(), sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, s));
+        // the host copies must outlive the asynchronous transfers
+        ML_CK(cudaStreamSynchronize(s));
+    }
     ML_CK(b->alloc(&b->d_status, 1, s));
     ML_CK(b->alloc(&b->d_mu, mu_total, s));
-    ML_CK(cudaMemcpyAsync(b->d_args, args.data(), sizeof(ShootArgs) * n, cudaMemcpyHostToDevice, s));
-    ML_CK(cudaMemcpyAsync(b->d_base, base.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s));
     ML_CK(cudaHostAlloc((void **)&b->h_abort, sizeof(int), cudaHostAllocMapped));
     *b->h_abort = 0;
     ML_CK(cudaHostGetDevicePointer((void **)&b->d_abort, b->h_abort, 0));

@@ -28,10 +28,9 @@ def test_batch_matches_single_maps_bitwise(ml):
     b = ml.Batch(descs, tracks=tracks, n_samples=200, sigma_px=0.5)
     b.run(use_graph=True)
     curves = b.curves().cpu().numpy()
-    P = b.info(0)["taylor_p"]
     for i, w in enumerate(ws):
         info = b.info(i)
-        assert info["taylor_p"] == P                      # one order for the launch
+        P = info["taylor_p"]                              # each map keeps its own order
         st = b.stats(i)
         n = info["n_rays_x"] * info["n_rays_y"]
         assert st["rays_in"] + st["rays_out"] + st["rays_dropped"] == n
@@ -46,6 +45,23 @@ def test_batch_matches_single_maps_bitwise(ml):
         assert np.array_equal(mu, f.mu("f32").cpu().numpy())
         lc = f.light_curves(tracks[i], 200, 0.5).cpu().numpy()
         assert np.allclose(curves[i], lc, rtol=2e-6, atol=1e-6 * np.abs(lc).max())
+        f.close()
+    b.close()
+
+
+def test_tuned_batch_groups_orders_and_matches_single_maps(ml):
+    """Tuned maps may need different Taylor orders: each runs with its own in
+    the launch of its order, bit for bit as the same map shot alone."""
+    ws, descs, tracks = _small_batch(ml, n_maps=6, tune=True)
+    b = ml.Batch(descs)
+    b.run(use_graph=True)
+    for i, w in enumerate(ws):
+        info = b.info(i)
+        assert info["tuned"] == 1 and info["far_bound"] <= 1e-7
+        f = ml.Field(w, precision=ml.PREC_MIXED, taylor_p=info["taylor_p"],
+                     l2_sub=(info["l2_sub_x"], info["l2_sub_y"]))
+        f.shoot()
+        assert np.array_equal(b.counts(i).cpu().numpy(), f.counts().cpu().numpy()), i
         f.close()
     b.close()
 
