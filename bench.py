@@ -37,10 +37,10 @@ N_TRACKS, TRACK_SAMPLES, SIGMA_PX = 10, 4096, 0.5
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per ray of the shooting kernel, from the ncu capture summarised in
 # profiles/k_shoot_mixed_paper-map-2e10-ray-slice.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 450.4 MB for 2.0e10 rays), valid for the kernel
-# sources with these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = 450.413056e6 / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "26dd64ff", "ml_internal.cuh": "9b6a32ff"}
+# dram__bytes_write.sum = 461.6 MB for 2.0e10 rays, tuned grid, p = 4), valid
+# for the kernel sources with these sha1 prefixes only.
+TRAFFIC_BYTES_PER_RAY = 461.583616e6 / 2.0e10
+TRAFFIC_SOURCES = {"ml_shoot.cu": "a9c2bb2a", "ml_internal.cuh": "fffb9df2", "ml_task.cuh": "99f52f61"}
 
 
 def traffic_per_launch(rays_per_launch: float):
@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="the paper's level-2 grid (L2 = L1/20) instead of the autotuned one")
     ap.add_argument("--shoot-rays", type=float, default=0,
                     help="profiling: shoot only this many rays (a centred slice of the lattice) "
                          "per step; the default shoots them all")
@@ -166,7 +168,7 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
 
     def make_desc(device_lenses: bool, host_lenses=None):
-        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host_lenses)
+        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host_lenses, tune=not args.no_tune)
         if device_lenses:
             d.lens_x, d.lens_y, d.lens_m = (t.data_ptr() for t in lens_dev)
             d.lens_mem_is_device = 1
@@ -245,6 +247,7 @@ def run_ours(args, rank, world, local):
                    "n_lenses": int(w.lenses.n), "n_rays": int(n_rays),
                    "map": f"{w.map_n[0]}x{w.map_n[1]} uint32", "precision": "mixed",
                    "taylor_p": p, "far_bound_theta_e": info["far_bound"],
+                   "l2_sub": [info["l2_sub_x"], info["l2_sub_y"]], "tuned_grid": bool(info["tuned"]),
                    "coefficient_build": {1: "direct", 2: "hierarchical"}.get(info["build"]),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent maps per GPU x{world}"},
@@ -270,7 +273,7 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e(ml, w, torch, dev, stream, tracks, args, flush)
 
     if rank == 0 and not args.no_parity:
-        out["map_l1_vs_oracle"] = parity_stripe(ml, w, stream)
+        out["map_l1_vs_oracle"] = parity_stripe(ml, w, stream, tune=not args.no_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
@@ -289,7 +292,7 @@ def e2e(ml, w, torch, dev, stream, tracks, args, flush):
     lc_h = torch.empty((N_TRACKS, TRACK_SAMPLES), dtype=torch.float32).pin_memory().numpy()
 
     def step():
-        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host)
+        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host, tune=not args.no_tune)
         h = ml.ml_field_create(d, stream)
         info = ml.ml_field_info(h)
         ml.ml_shoot_rays(h, 0, info["n_rays_x"] * info["n_rays_y"], stream)
@@ -313,11 +316,13 @@ def e2e(ml, w, torch, dev, stream, tracks, args, flush):
             "d2h_bytes_per_step": int(4 * w.map_n[0] * w.map_n[1] + 4 * N_TRACKS * TRACK_SAMPLES)}
 
 
-def parity_stripe(ml, w, stream):
-    """Map relative L1 error vs the FP64 oracle on a stripe of 1e6 rays shot alone."""
+def parity_stripe(ml, w, stream, tune=False):
+    """Map relative L1 error vs the FP64 oracle on a stripe of 1e6 rays shot
+    alone, with the benchmark's level-2 grid."""
     import oracle
-    f = ml.Field(w, precision=ml.PREC_MIXED)
-    g = oracle.geometry_of(w, p=f.info["taylor_p"])
+    f = ml.Field(w, precision=ml.PREC_MIXED, tune=tune)
+    g = oracle.geometry_of(w, p=f.info["taylor_p"], l2_sub=f.info["l2_sub_x"],
+                           l2_sub_y=f.info["l2_sub_y"])
     r0 = (g.n3y // 2) * g.n3x + 777
     r1 = r0 + 1_000_000
     f.shoot(r0, r1)

@@ -361,8 +361,13 @@ __host__ __device__ inline size_t adj_smem_f4(int cap)
 //  - the moments of its level-2 node (FP32 t-power sums per lane, converted
 //    and reduced over the lanes of one node, FP64 atomics),
 //  - the near-lens pair terms (near_pass, FP64 per warp, FP64 atomics per task).
+#ifndef ML_ADJ_LOWP_BLOCKS
+#define ML_ADJ_LOWP_BLOCKS 2
+#endif
+
 template <int P>
-__global__ void __launch_bounds__(WARPS_PER_CTA * 32, 2) k_adj_rays(ShootArgs a, AdjArgs d)
+__global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOCKS : 2))
+    k_adj_rays(ShootArgs a, AdjArgs d)
 {
     extern __shared__ float4 smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -233,12 +233,14 @@ bool rays_inside_sheet(const Geo &g)
 // the same truncation bound, at the price of more nodes to build.  The tuner
 // evaluates a few (l2_sub_x, l2_sub_y) candidates with their rigorous bound
 // (one p_bound launch each) and a cost model of GB300 measurements:
-//   time = rays * ray_cost(P) + nodes * (P + 1) * node_cost.
+//   time = rays * ray_cost(P) + nodes * (P + 1) * node_cost,
+// the field's build plus one shot of all its rays.
 
-// Shooting cost per ray of the mixed kernel on the whole GB300 (ns), by the
-// compiled Taylor order P, measured at the paper-scale field (1.36 near lenses
-// per ray) for P = 4, 5, 8 and interpolated/extrapolated linearly elsewhere.
-double ray_cost_ns(int P)
+// Shooting time per ray of the mixed kernel on the whole GB300, in
+// picoseconds (1.92 ps per ray is 5.2e11 rays/s), measured at the paper-scale
+// field (1.36 near lenses per ray) for P = 4, 5, 8 and interpolated or
+// extrapolated linearly elsewhere.
+double ray_cost_ps(int P)
 {
     switch (P) {
     case 1: return 1.60;
@@ -253,7 +255,9 @@ double ray_cost_ns(int P)
     default: return 2.55;
     }
 }
-constexpr double kNodeCostNs = 1.1;   // hierarchical build and node record, per node and coefficient
+// hierarchical build and node record, nanoseconds per node and coefficient
+// (k_node_shift: 6.3 ms for 1.38e6 nodes x 5 coefficients)
+constexpr double kNodeCostNs = 1.1;
 
 struct GridChoice {
     int sx = 20, sy = 20, p = 0;
@@ -269,7 +273,7 @@ struct TuneCand {
 
 double cand_cost(const TuneCand &c, int P)
 {
-    return c.rays * ray_cost_ns(P) + c.nodes * (P + 1) * kNodeCostNs;
+    return c.rays * ray_cost_ps(P) * 1e-3 + c.nodes * (P + 1) * kNodeCostNs;   // ns
 }
 
 uint64_t mix64(uint64_t h, uint64_t v)
