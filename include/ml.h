@@ -244,6 +244,33 @@ ml_status ml_trace_rays(ml_field *f, const int64_t *ray_idx, int64_t n, double *
                         int32_t *pix, void *stream);
 
 /*
+ * ml_map_light_curves - the light curves of ml_light_curves (§4.1: Gaussian
+ * source, taps at integer offsets |t| <= floor(4 sigma) normalised to 1,
+ * bilinear sampling between pixel centres, n_samples equally spaced points
+ * from (x0, y0) to (x1, y1) inclusive) evaluated on a caller's map.
+ *  mu:     device, ny x nx float32 (any map: mu, or a dLoss-weighted map).
+ *  tracks: host, n_tracks x (x0, y0, x1, y1) in map pixel coordinates.
+ *  out:    device, n_tracks x n_samples float32.
+ * Stream-ordered.  Errors: ML_ERR_INVALID_ARG (NULL, sizes, sigma outside
+ * (0, 16], non-finite tracks); ML_ERR_CUDA.
+ */
+ml_status ml_map_light_curves(const float *mu, int32_t nx, int32_t ny, const double *tracks,
+                              int32_t n_tracks, int32_t n_samples, double sigma_px, float *out,
+                              void *stream);
+
+/*
+ * ml_map_light_curves_backward - the transpose of ml_map_light_curves: given
+ * dL_dcurves (device, n_tracks x n_samples float32), writes dL_dmu (device,
+ * ny x nx float32, overwritten) = sum over samples of the sample's gradient
+ * times its bilinear and Gaussian weights.  With ml_cic_backward it gives the
+ * gradient of a light-curve loss with respect to the lens field.
+ * Stream-ordered; errors as ml_map_light_curves.
+ */
+ml_status ml_map_light_curves_backward(int32_t nx, int32_t ny, const double *tracks, int32_t n_tracks,
+                                       int32_t n_samples, double sigma_px, const float *dL_dcurves,
+                                       float *dL_dmu, void *stream);
+
+/*
  * ml_cic_forward - the differentiable map: clears the field, shoots all its
  * rays and writes M = (S_I / S_S) * cloud-in-cell weights (Eq. 12 with
  * bilinear weights to the four nearest pixel centres) as float32.

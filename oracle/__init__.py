@@ -438,6 +438,23 @@ def cic_loss(g: Geometry, x, y, m, target, ray_begin=0, ray_end=None, threads=No
     return float(np.sum((M - target) ** 2)), M
 
 
+def cic_grad_dM(g: Geometry, x, y, m, dL_dM, ray_begin=0, ray_end=None, threads=None):
+    """FP64 gradient of any loss of the CIC magnification map M given its
+    dL/dM (mny x mnx): (dL/dlens (n, 3), dL/d(kappa, gamma, kappa_*))."""
+    x, y, m = _lens_arrays(x, y, m)
+    if ray_end is None:
+        ray_end = g.n_rays
+    G = np.ascontiguousarray(dL_dM, np.float64)
+    gl = np.zeros((len(x), 3))
+    gp = np.zeros(3)
+    gg = g.c_geom()
+    lib().orc_cic_grad(C.byref(gg), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                       _ptr(m, C.c_double), len(x), int(ray_begin), int(ray_end),
+                       _ptr(G, C.c_double), cic_mu_scale(g), _ptr(gl, C.c_double),
+                       _ptr(gp, C.c_double), threads or default_threads())
+    return gl, gp
+
+
 def cic_grad(g: Geometry, x, y, m, target, ray_begin=0, ray_end=None, threads=None):
     """FP64 reference gradient of cic_loss: (dL/dlens (n, 3), dL/d(kappa,
     gamma, kappa_*))."""

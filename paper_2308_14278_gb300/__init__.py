@@ -39,7 +39,8 @@ EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays"
            "ml_field_stats", "ml_field_info", "ml_field_abort", "ml_field_destroy",
            "ml_light_curves_noalloc", "ml_batch_create", "ml_batch_run", "ml_batch_field",
            "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy",
-           "ml_cic_forward", "ml_cic_backward", "ml_cic_backward_ex")
+           "ml_cic_forward", "ml_cic_backward", "ml_cic_backward_ex", "ml_map_light_curves",
+           "ml_map_light_curves_backward")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -125,6 +126,8 @@ def load(path: str | None = None):
         "ml_cic_forward": ([V, V, V], st),
         "ml_cic_backward": ([V, V, V, V, V], st),
         "ml_cic_backward_ex": ([V, V, V, V, C.c_int32, V], st),
+        "ml_map_light_curves": ([V, C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V], st),
+        "ml_map_light_curves_backward": ([C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V, V], st),
         "ml_field_clear": ([V, V], st),
         "ml_field_stats": ([V, P(C.c_uint64), V], st),
         "ml_field_info": ([V, P(FieldParams)], st),
@@ -206,6 +209,27 @@ def ml_cic_forward(field, mu, stream=None):
 
 
 ADJOINT_NEARFAR, ADJOINT_DIRECT = 0, 1
+
+
+def _tracks_host(tracks):
+    tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
+    return tr, tr.ctypes.data
+
+
+def ml_map_light_curves(mu, tracks, n_samples, sigma_px, out, stream=None):
+    """Light curves of a device float32 map (see ml.h)."""
+    tr, ptr = _tracks_host(tracks)
+    ny, nx = mu.shape
+    _check(load().ml_map_light_curves(_dptr(mu), nx, ny, ptr, len(tr), n_samples, sigma_px,
+                                      _dptr(out), _stream(stream)))
+
+
+def ml_map_light_curves_backward(dL_dcurves, tracks, n_samples, sigma_px, dL_dmu, stream=None):
+    """Transpose of ml_map_light_curves into dL_dmu (device float32, overwritten)."""
+    tr, ptr = _tracks_host(tracks)
+    ny, nx = dL_dmu.shape
+    _check(load().ml_map_light_curves_backward(nx, ny, ptr, len(tr), n_samples, sigma_px,
+                                               _dptr(dL_dcurves), _dptr(dL_dmu), _stream(stream)))
 
 
 def ml_cic_backward(field, dL_dM, grad_lens, grad_params, stream=None, method=ADJOINT_NEARFAR):

@@ -1,4 +1,4 @@
-"""Differentiable cloud-in-cell magnification map.
+"""Differentiable cloud-in-cell magnification map and light curves.
 
 CICMagnification.apply(x, y, m, kappa, gamma, kappa_star, spec) returns the
 float32 magnification map M = (S_I / S_S) * CIC ray weights of a lens field
@@ -12,7 +12,10 @@ from __future__ import annotations
 
 import torch
 
-from . import (DEPOSIT_CIC, PREC_MIXED, Field, make_desc, ml_cic_backward, ml_cic_forward)
+import numpy as np
+
+from . import (DEPOSIT_CIC, PREC_MIXED, Field, make_desc, ml_cic_backward, ml_cic_forward,
+               ml_map_light_curves, ml_map_light_curves_backward)
 from .inputs import LensField, Workload
 
 
@@ -58,3 +61,29 @@ class CICMagnification(torch.autograd.Function):
         gl = glens.to(dev_lens)
         gp = gpar.to(dev_par) if dev_par is not None else gpar
         return gl[:, 0], gl[:, 1], gl[:, 2], gp[0], gp[1], gp[2], None
+
+
+class LightCurves(torch.autograd.Function):
+    """Gaussian-source light curves of a map (ml_map_light_curves), with the
+    transpose (ml_map_light_curves_backward) as backward.  Composes with
+    CICMagnification for a light-curve loss:
+        mu = CICMagnification.apply(x, y, m, kappa, gamma, kappa_star, spec)
+        curves = LightCurves.apply(mu, tracks, n_samples, sigma_px)
+    tracks: n x (x0, y0, x1, y1) in map pixel coordinates (host array)."""
+
+    @staticmethod
+    def forward(ctx, mu, tracks, n_samples, sigma_px):
+        tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
+        mu = mu.detach().contiguous().float()
+        out = torch.empty((len(tr), n_samples), dtype=torch.float32, device=mu.device)
+        ml_map_light_curves(mu, tr, n_samples, sigma_px, out)
+        ctx.args = (tr, n_samples, sigma_px, tuple(mu.shape))
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_curves):
+        tr, n_samples, sigma_px, shape = ctx.args
+        g = torch.empty(shape, dtype=torch.float32, device=grad_curves.device)
+        ml_map_light_curves_backward(grad_curves.detach().contiguous().float(), tr, n_samples,
+                                     sigma_px, g)
+        return g, None, None, None

@@ -1137,6 +1137,60 @@ ml_status ml_light_curves(ml_field *f, const double *tracks, int32_t n_tracks, i
     return ML_OK;
 }
 
+namespace {
+
+ml_status map_lc_args(const void *a, const void *b, const double *tracks, int32_t nx, int32_t ny,
+                      int32_t n_tracks, int32_t n_samples, double sigma_px)
+{
+    if (!a || !b || !tracks) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (nx < 1 || ny < 1) return fail(ML_ERR_INVALID_ARG, "map size must be positive");
+    if (n_tracks < 1 || n_samples < 1) return fail(ML_ERR_INVALID_ARG, "need >= 1 track and sample");
+    if (!(sigma_px > 0.0) || sigma_px > 16.0) return fail(ML_ERR_INVALID_ARG, "sigma_px must be in (0, 16]");
+    for (int q = 0; q < 4 * n_tracks; ++q)
+        if (!is_fin(tracks[q])) return fail(ML_ERR_INVALID_ARG, "track coordinates must be finite");
+    return ML_OK;
+}
+
+}  // namespace
+
+ml_status ml_map_light_curves(const float *mu, int32_t nx, int32_t ny, const double *tracks,
+                              int32_t n_tracks, int32_t n_samples, double sigma_px, float *out,
+                              void *stream)
+{
+    ml_status st = map_lc_args(mu, out, tracks, nx, ny, n_tracks, n_samples, sigma_px);
+    if (st != ML_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Geo g{};
+    g.mnx = nx;
+    g.mny = ny;
+    double *d_tr = nullptr;
+    ML_CK(cudaMallocAsync((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
+    cudaError_t e = cudaMemcpyAsync(d_tr, tracks, sizeof(double) * 4 * n_tracks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_light_curves(g, nullptr, mu, 1.0, d_tr, n_tracks, n_samples, sigma_px, out, s);
+    cudaFreeAsync(d_tr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "map light curves");
+    return ML_OK;
+}
+
+ml_status ml_map_light_curves_backward(int32_t nx, int32_t ny, const double *tracks, int32_t n_tracks,
+                                       int32_t n_samples, double sigma_px, const float *dL_dcurves,
+                                       float *dL_dmu, void *stream)
+{
+    ml_status st = map_lc_args(dL_dcurves, dL_dmu, tracks, nx, ny, n_tracks, n_samples, sigma_px);
+    if (st != ML_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *d_tr = nullptr;
+    ML_CK(cudaMemsetAsync(dL_dmu, 0, sizeof(float) * (size_t)nx * (size_t)ny, s));
+    ML_CK(cudaMallocAsync((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
+    cudaError_t e = cudaMemcpyAsync(d_tr, tracks, sizeof(double) * 4 * n_tracks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_light_curves_adj(nx, ny, d_tr, n_tracks, n_samples, sigma_px, dL_dcurves, dL_dmu, s);
+    cudaFreeAsync(d_tr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "light-curve adjoint");
+    return ML_OK;
+}
+
 ml_status ml_light_curves_noalloc(ml_field *f, const double *tracks, int32_t n_tracks,
                                   int32_t n_samples, double sigma_px, float *out, void *stream)
 {

@@ -122,6 +122,9 @@ cudaError_t launch_light_curves_noalloc(const Geo &g, const uint32_t *cu, const 
                                         double scale, const double *tracks_host, int n_tracks,
                                         int n_samples, double sigma_px, float *out, cudaStream_t s);
 int light_curve_taps(double sigma_px, float taps[129]);
+cudaError_t launch_light_curves_adj(int mnx, int mny, const double *d_tracks, int n_tracks,
+                                    int n_samples, double sigma_px, const float *dl, float *gmap,
+                                    cudaStream_t s);
 cudaError_t launch_light_curves_dev(const Geo &g, const uint32_t *cu, const float *cf, double scale,
                                     const double *d_tracks, int n_tracks, int n_samples, int h,
                                     const float *d_taps, float *out, cudaStream_t s);

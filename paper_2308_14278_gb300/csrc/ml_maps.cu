@@ -257,4 +257,69 @@ cudaError_t launch_light_curves_dev(const Geo &g, const uint32_t *cu, const floa
     return cudaGetLastError();
 }
 
+// ---- adjoint of the light curves ---------------------------------------------
+//
+// A light-curve sample is L = sum_c w_c sum_{dx,dy} taps[dx] taps[dy] M[p_c + (dx, dy)]
+// over the four bilinear corners p_c (k_light_curves), a linear map of the
+// magnification map M.  Its transpose adds, for every sample with incoming
+// gradient g, g w_c taps[dx] taps[dy] to the same pixels, skipping exactly the
+// corners and taps the forward skips.
+__global__ void k_light_curves_adj(int mnx, int mny, const double *__restrict__ tracks, int n_tracks,
+                                   int n_samples, int h, const float *__restrict__ taps_g,
+                                   const float *__restrict__ dl, float *__restrict__ gmap)
+{
+    __shared__ float taps[129];
+    for (int t = threadIdx.x; t <= 2 * h; t += blockDim.x) taps[t] = taps_g[t];
+    __syncthreads();
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n_tracks * n_samples) return;
+    const float gq = dl[q];
+    if (gq == 0.f) return;
+    int tr = (int)(q / n_samples), k = (int)(q % n_samples);
+    const double *T = tracks + 4 * tr;
+    double t = n_samples > 1 ? (double)k / (double)(n_samples - 1) : 0.0;
+    double u = T[0] + t * (T[2] - T[0]) - 0.5;
+    double v = T[1] + t * (T[3] - T[1]) - 0.5;
+    double fu = floor(u), fv = floor(v);
+    double wx = u - fu, wy = v - fv;
+    int i0 = (int)fu, j0 = (int)fv;
+    for (int c = 0; c < 4; ++c) {
+        int pi = i0 + (c & 1), pj = j0 + (c >> 1);
+        double wc = ((c & 1) ? wx : 1.0 - wx) * ((c >> 1) ? wy : 1.0 - wy);
+        if (pi < 0 || pi >= mnx || pj < 0 || pj >= mny || wc == 0.0) continue;
+        const float gw = (float)((double)gq * wc);
+        for (int dy = -h; dy <= h; ++dy) {
+            int yy = pj + dy;
+            if (yy < 0 || yy >= mny) continue;
+            const float gy = gw * taps[dy + h];
+            for (int dx = -h; dx <= h; ++dx) {
+                int xx = pi + dx;
+                if (xx < 0 || xx >= mnx) continue;
+                atomicAdd(gmap + (int64_t)yy * mnx + xx, gy * taps[dx + h]);
+            }
+        }
+    }
+}
+
+cudaError_t launch_light_curves_adj(int mnx, int mny, const double *d_tracks, int n_tracks,
+                                    int n_samples, double sigma_px, const float *dl, float *gmap,
+                                    cudaStream_t s)
+{
+    float taps[129];
+    const int h = gaussian_taps(sigma_px, taps);
+    if (h < 0) return cudaErrorInvalidValue;
+    float *d_taps = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d_taps, sizeof(float) * (2 * h + 1), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d_taps, taps, sizeof(float) * (2 * h + 1), cudaMemcpyHostToDevice, s);
+    const int64_t n = (int64_t)n_tracks * n_samples;
+    if (e == cudaSuccess && n > 0) {
+        k_light_curves_adj<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(mnx, mny, d_tracks, n_tracks,
+                                                                        n_samples, h, d_taps, dl, gmap);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(d_taps, s);
+    return e;
+}
+
 }  // namespace ml

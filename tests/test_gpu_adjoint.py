@@ -194,3 +194,93 @@ def test_nearfar_adjoint_agrees_with_direct_at_full_size(ml):
     # the sheet is centred on the origin: dL/dkappa = -dL/dkappa_*
     assert abs(pa[0] + pa[2]) <= 1e-9 * abs(pa[0])
     f.close()
+
+
+# -- light-curve loss ---------------------------------------------------------
+
+def _lc_case(seed=21, nx=40, ny=30, n_tracks=5, n_samples=60, sigma=0.8):
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(0.5, 3.0, (ny, nx))
+    tracks = np.column_stack([rng.uniform(-2, nx + 1, n_tracks), rng.uniform(-2, ny + 1, n_tracks),
+                              rng.uniform(-2, nx + 1, n_tracks), rng.uniform(-2, ny + 1, n_tracks)])
+    return mu, tracks, n_samples, sigma
+
+
+def test_map_light_curves_match_oracle(ml):
+    import torch
+    mu, tracks, ns, sigma = _lc_case()
+    out = torch.empty((len(tracks), ns), dtype=torch.float32, device="cuda")
+    ml.ml_map_light_curves(torch.as_tensor(mu, dtype=torch.float32).cuda(), tracks, ns, sigma, out)
+    ref = oracle.light_curves(mu.astype(np.float32).astype(np.float64), tracks, ns, sigma)
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
+
+
+def test_light_curve_adjoint_is_the_transpose_of_the_oracle_operator(ml):
+    """Brute force: the oracle's light-curve operator J (samples x pixels),
+    column by column on unit maps; the GPU backward must return J^T w."""
+    import torch
+    mu, tracks, ns, sigma = _lc_case(nx=20, ny=14, n_tracks=3, n_samples=25)
+    ny, nx = mu.shape
+    J = np.zeros((len(tracks) * ns, ny * nx))
+    for p in range(ny * nx):
+        e = np.zeros(ny * nx)
+        e[p] = 1.0
+        J[:, p] = oracle.light_curves(e.reshape(ny, nx), tracks, ns, sigma).ravel()
+    w = np.random.default_rng(4).standard_normal(len(tracks) * ns)
+    g = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+    ml.ml_map_light_curves_backward(torch.as_tensor(w.reshape(len(tracks), ns), dtype=torch.float32).cuda(),
+                                    tracks, ns, sigma, g)
+    ref = (J.T @ w).reshape(ny, nx)
+    assert np.abs(g.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert np.count_nonzero(ref) > 0
+
+
+def test_light_curve_loss_gradient_matches_oracle(ml):
+    """L = sum (curves - c_target)^2 with curves = LightCurves(CICMagnification):
+    the autograd gradient (GPU light-curve transpose, GPU near/far adjoint)
+    against the oracle's FP64 CIC gradient of the same dL/dM, where dL/dM is the
+    oracle operator's transpose applied to dL/dcurves."""
+    import torch
+    from paper_2308_14278_gb300.autograd import CICMagnification, LightCurves
+    w = _case()
+    probe = _field(ml, w)
+    info = probe.info
+    spec = dict(sheet=w.sheet, map_box=w.map_box, map_n=w.map_n, ray_box=w.ray_box, ray_n=w.ray_n,
+                taylor_p=info["taylor_p"], l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]),
+                l2_sub=(info["l2_sub_x"], info["l2_sub_y"]))
+    probe.close()
+    g = oracle.geometry_of(w, p=info["taylor_p"], l1=spec["l1"], l2_sub=info["l2_sub_x"],
+                           l2_sub_y=info["l2_sub_y"])
+    nx, ny = w.map_n
+    rng = np.random.default_rng(9)
+    tracks = np.column_stack([rng.uniform(3, nx - 3, 6), rng.uniform(3, ny - 3, 6),
+                              rng.uniform(3, nx - 3, 6), rng.uniform(3, ny - 3, 6)])
+    ns, sigma = 80, 0.7
+    target = rng.uniform(1.0, 3.0, (6, ns))
+    x = torch.tensor(w.lenses.x, requires_grad=True)
+    y = torch.tensor(w.lenses.y, requires_grad=True)
+    m = torch.tensor(w.lenses.m, requires_grad=True)
+    par = [torch.tensor(v, dtype=torch.float64, requires_grad=True)
+           for v in (w.kappa, w.gamma, w.kappa_star)]
+    mu = CICMagnification.apply(x, y, m, *par, spec)
+    curves = LightCurves.apply(mu, tracks, ns, sigma)
+    loss = ((curves.double() - torch.as_tensor(target).cuda()) ** 2).sum()
+    loss.backward()
+    # oracle: M, curves, dL/dcurves, J^T, FP64 CIC gradient
+    M = oracle.cic_mu_scale(g) * oracle.cic_forward(g, w.lenses.x, w.lenses.y, w.lenses.m)
+    c_ref = oracle.light_curves(M, tracks, ns, sigma)
+    assert np.abs(curves.detach().cpu().numpy() - c_ref).max() <= 1e-4 * np.abs(c_ref).max()
+    dl = 2.0 * (c_ref - target)
+    J = np.zeros((6 * ns, ny * nx))
+    for p in range(ny * nx):
+        e = np.zeros(ny * nx)
+        e[p] = 1.0
+        J[:, p] = oracle.light_curves(e.reshape(ny, nx), tracks, ns, sigma).ravel()
+    dM = (J.T @ dl.ravel()).reshape(ny, nx)
+    gl, gp = oracle.cic_grad_dM(g, w.lenses.x, w.lenses.y, w.lenses.m, dM)
+    got = np.column_stack([x.grad.numpy(), y.grad.numpy(), m.grad.numpy()])
+    for c in range(3):
+        scale = np.abs(gl[:, c]).max()
+        assert np.abs(got[:, c] - gl[:, c]).max() <= 1e-3 * scale, (c, np.abs(got[:, c] - gl[:, c]).max() / scale)
+    gpar = np.array([p_.grad.item() for p_ in par])
+    assert np.all(np.abs(gpar - gp) <= 1e-3 * np.abs(gp)), (gpar, gp)
