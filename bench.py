@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: shoot ONE paper-scale map across the ranks (contiguous level-1 "
+                         "bands per rank, integer map sum over NCCL; strong scaling) instead of "
+                         "one independent map per rank (weak scaling)")
     ap.add_argument("--no-tune", action="store_true",
                     help="the paper's level-2 grid (L2 = L1/20) instead of the autotuned one")
     ap.add_argument("--shoot-rays", type=float, default=0,
@@ -150,15 +154,20 @@ def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
     import paper_2308_14278_gb300 as ml
-    from paper_2308_14278_gb300 import inputs
+    from paper_2308_14278_gb300 import inputs, shard
     ml.load()
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    # weak scaling: every rank makes its own map (own seed) of the same size
-    w = inputs.paper_map(seed=rank, n_rays=args.rays, map_px=args.map_px, n_tracks=N_TRACKS)
+    # weak scaling: every rank makes its own map (own seed) of the same size;
+    # --shard: all ranks share one map and each shoots its part of the lattice
+    sharded = bool(args.shard and world > 1)
+    w = inputs.paper_map(seed=0 if sharded else rank, n_rays=args.rays, map_px=args.map_px,
+                         n_tracks=N_TRACKS)
+    counts_buf = (torch.empty((w.map_n[1], w.map_n[0]), dtype=torch.int32, device=f"cuda:{local}")
+                  if sharded else None)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     lens_dev = [torch.from_numpy(a).to(dev) for a in (w.lenses.x, w.lenses.y, w.lenses.m)]
@@ -186,7 +195,14 @@ def run_ours(args, rank, world, local):
         n_all = info["n_rays_x"] * info["n_rays_y"]
         n_shoot = int(min(args.shoot_rays, n_all)) if args.shoot_rays else n_all
         r0 = (n_all - n_shoot) // 2
-        ml.ml_shoot_rays(h, r0, r0 + n_shoot, stream)
+        if sharded:
+            a, b = shard.ray_ranges(info["n_rays_x"], info["n_rays_y"], info["n1y"], world)[rank]
+            ml.ml_shoot_rays(h, a, b, stream)
+            ml.ml_magnification_map(h, ml.MAP_COUNTS_U32, counts_buf, stream)
+            shard.reduce_counts(counts_buf)          # NCCL integer sum on the current stream
+            ml.ml_field_set_counts(h, counts_buf, stream)
+        else:
+            ml.ml_shoot_rays(h, r0, r0 + n_shoot, stream)
         if e: e[2].record(stream)
         ml.ml_magnification_map(h, ml.MAP_MU_F32, mu_out, stream)
         if e: e[3].record(stream)
@@ -226,22 +242,28 @@ def run_ours(args, rank, world, local):
         t = torch.tensor([t_local], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_local = float(t.item())
-    value = n_rays * world / (t_local / 1e3)
+    value = n_rays * (1 if sharded else world) / (t_local / 1e3)
 
     # roofline of the dominant kernel (the shooting kernel): algorithmic FP32
     # work per ray of this algorithm = 11 per near pair + 4p (two real Horner
     # polynomials of degree p) + 6 (near fold, binning)
     p = info["taylor_p"]
     shoot_ms = float(per[:, 1].mean())
-    flops = 11.0 * stats["near_pairs"] + (4.0 * p + 6.0) * n_rays
+    n_local = stats["rays_in"] + stats["rays_out"] + stats["rays_dropped"]   # this rank's rays
+    expected_local = n_rays
+    if sharded:
+        a, b = shard.ray_ranges(info["n_rays_x"], info["n_rays_y"], info["n1y"], world)[rank]
+        expected_local = b - a
+    flops = 11.0 * stats["near_pairs"] + (4.0 * p + 6.0) * n_local
     achieved = flops / (shoot_ms / 1e3) / 1e12
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    survey_flops = 11.0 * stats["near_pairs"] + (8.0 * p + 10.0) * n_rays
+    survey_flops = 11.0 * stats["near_pairs"] + (8.0 * p + 10.0) * n_local
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_local, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 near sum + f64 nodes",
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+        "dtype": "f32 near sum + f64 nodes",
         "data": "synthetic (seeded lognormal lens disc; no dataset)",
         "config": {"workload": w.name + f", {N_TRACKS} light curves x {TRACK_SAMPLES}",
                    "n_lenses": int(w.lenses.n), "n_rays": int(n_rays),
@@ -250,19 +272,20 @@ def run_ours(args, rank, world, local):
                    "l2_sub": [info["l2_sub_x"], info["l2_sub_y"]], "tuned_grid": bool(info["tuned"]),
                    "coefficient_build": {1: "direct", 2: "hierarchical"}.get(info["build"]),
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"independent maps per GPU x{world}"},
+                   "parallelism": (f"one map sharded over {world} GPUs (level-1 bands, integer "
+                                   f"map sum)" if sharded else f"independent maps per GPU x{world}")},
         "breakdown_ms": {"create": float(per[:, 0].mean()), "shoot": shoot_ms,
                          "mu": float(per[:, 2].mean()), "light_curves": float(per[:, 3].mean())},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": traffic_per_launch(n_rays / max(1, stats["launches"])),
+                     "traffic": traffic_per_launch(n_local / max(1, stats["launches"])),
                      "kernel": "k_shoot_mixed", "flops_per_launch_survey_convention":
                          survey_flops / max(1, stats["launches"]),
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
         "shoot_rays_override": bool(args.shoot_rays),
         "rays_check": {"in": stats["rays_in"], "out": stats["rays_out"],
-                       "dropped": stats["rays_dropped"], "total": n_rays,
-                       "conserved": stats["rays_in"] + stats["rays_out"] + stats["rays_dropped"] == n_rays},
+                       "dropped": stats["rays_dropped"], "total": n_local,
+                       "conserved": n_local == expected_local},
         "gpu_launches": int(args.steps * (6 + stats["launches"] + 2)),
     }
     clk_sum = clk.summary()

@@ -321,6 +321,17 @@ ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens,
                              int32_t method, void *stream);
 
 /*
+ * ml_field_set_counts - replace the field's integer count map (NGP fields)
+ * with `counts` (map_ny x map_nx uint32, device or host), stream-ordered.
+ * For a map shot in shards on several GPUs: each GPU shoots its ray range,
+ * the count maps are summed (integer addition, exact), and the sum is set
+ * back before ml_magnification_map and ml_light_curves.  The counters
+ * (ml_field_stats) are left as they are.  Errors: ML_ERR_STATE for a CIC
+ * field; ML_ERR_INVALID_ARG; ML_ERR_CUDA.
+ */
+ml_status ml_field_set_counts(ml_field *f, const uint32_t *counts, int32_t in_is_device, void *stream);
+
+/*
  * ml_field_clear - zero the map and the counters (stream-ordered).
  */
 ml_status ml_field_clear(ml_field *f, void *stream);

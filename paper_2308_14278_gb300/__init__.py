@@ -40,7 +40,7 @@ EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays"
            "ml_light_curves_noalloc", "ml_batch_create", "ml_batch_run", "ml_batch_field",
            "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy",
            "ml_cic_forward", "ml_cic_backward", "ml_cic_backward_ex", "ml_map_light_curves",
-           "ml_map_light_curves_backward")
+           "ml_map_light_curves_backward", "ml_field_set_counts")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -126,6 +126,7 @@ def load(path: str | None = None):
         "ml_cic_forward": ([V, V, V], st),
         "ml_cic_backward": ([V, V, V, V, V], st),
         "ml_cic_backward_ex": ([V, V, V, V, C.c_int32, V], st),
+        "ml_field_set_counts": ([V, V, C.c_int32, V], st),
         "ml_map_light_curves": ([V, C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V], st),
         "ml_map_light_curves_backward": ([C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V, V], st),
         "ml_field_clear": ([V, V], st),
@@ -214,6 +215,11 @@ ADJOINT_NEARFAR, ADJOINT_DIRECT = 0, 1
 def _tracks_host(tracks):
     tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
     return tr, tr.ctypes.data
+
+
+def ml_field_set_counts(field, counts, stream=None):
+    """Replace the field's count map with a device int32/uint32 tensor (see ml.h)."""
+    _check(load().ml_field_set_counts(field, _dptr(counts), 1, _stream(stream)))
 
 
 def ml_map_light_curves(mu, tracks, n_samples, sigma_px, out, stream=None):

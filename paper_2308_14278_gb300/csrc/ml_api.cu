@@ -1268,6 +1268,17 @@ ml_status ml_cic_backward(ml_field *f, const float *dL_dM, double *grad_lens, do
     return ml_cic_backward_ex(f, dL_dM, grad_lens, grad_params, ML_ADJOINT_NEARFAR, stream);
 }
 
+ml_status ml_field_set_counts(ml_field *f, const uint32_t *counts, int32_t in_is_device, void *stream)
+{
+    if (!f || !counts) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (!f->d_map_u32) return fail(ML_ERR_STATE, "a CIC field has no integer counts");
+    const size_t npix = (size_t)f->g.mnx * f->g.mny;
+    ML_CK(cudaMemcpyAsync(f->d_map_u32, counts, npix * sizeof(uint32_t),
+                          in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          (cudaStream_t)stream));
+    return ML_OK;
+}
+
 ml_status ml_field_clear(ml_field *f, void *stream)
 {
     if (!f) return fail(ML_ERR_INVALID_ARG, "field is NULL");
