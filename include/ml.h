@@ -326,8 +326,9 @@ ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens,
  * For a map shot in shards on several GPUs: each GPU shoots its ray range,
  * the count maps are summed (integer addition, exact), and the sum is set
  * back before ml_magnification_map and ml_light_curves.  The counters
- * (ml_field_stats) are left as they are.  Errors: ML_ERR_STATE for a CIC
- * field; ML_ERR_INVALID_ARG; ML_ERR_CUDA.
+ * (ml_field_stats) are left as they are; the new map's sum becomes the base
+ * of the wrap-around check.  Synchronises `stream`.  Errors: ML_ERR_STATE for
+ * a CIC field; ML_ERR_INVALID_ARG; ML_ERR_CUDA.
  */
 ml_status ml_field_set_counts(ml_field *f, const uint32_t *counts, int32_t in_is_device, void *stream);
 
@@ -338,8 +339,11 @@ ml_status ml_field_clear(ml_field *f, void *stream);
 
 /*
  * ml_field_stats - synchronise `stream` and copy the field's counters
- * (ML_STAT_* indices) into out[8] (host).  Returns ML_ERR_OVERFLOW or
- * ML_ERR_ABORTED when the corresponding flag is set, after filling out.
+ * (ML_STAT_* indices) into out[8] (host).  For a uint32 count map it also
+ * sums the map in 64 bits (one pass over the map): a pixel that wrapped
+ * makes that sum fall short of the in-map ray count, which sets flag bit 0.
+ * Returns ML_ERR_OVERFLOW or ML_ERR_ABORTED when the corresponding flag is
+ * set, after filling out.
  */
 ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream);
 

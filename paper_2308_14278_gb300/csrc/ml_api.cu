@@ -61,7 +61,10 @@ struct ml_field {
     unsigned char *d_nodes = nullptr;
     uint32_t *d_map_u32 = nullptr;
     float *d_map_f32 = nullptr;
-    unsigned long long *d_stats = nullptr, *d_work = nullptr;
+    unsigned long long *d_stats = nullptr, *d_work = nullptr, *d_sum = nullptr;
+    // map sum bookkeeping for the wrap-around check: the map's 64-bit sum
+    // must equal map_base + (rays_in - in_at_set)
+    uint64_t map_base = 0, in_at_set = 0;
     unsigned int *d_status = nullptr;
     int *h_abort = nullptr, *d_abort = nullptr;
     std::vector<void *> owned;       // device allocations to free
@@ -237,27 +240,35 @@ bool rays_inside_sheet(const Geo &g)
 // the field's build plus one shot of all its rays.
 
 // Shooting time per ray of the mixed kernel on the whole GB300, in
-// picoseconds (1.92 ps per ray is 5.2e11 rays/s), measured at the paper-scale
-// field (1.36 near lenses per ray) for P = 4, 5, 8 and interpolated or
-// extrapolated linearly elsewhere.
-double ray_cost_ps(int P)
+// picoseconds, against the Taylor order P, measured at a fixed level-2 grid
+// on three fields: the paper-scale field (1.36 near lenses per ray) and two
+// of the batched maps (2.36 and 3.29), which also have shorter pixel runs.
+// Fields in between are interpolated linearly in the mean near count,
+// fields outside take the nearest curve.  The grid ranking depends on the
+// differences between orders and their size against the node cost.
+constexpr int kCostOrders[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+constexpr double kCostNear[3] = {1.36, 2.36, 3.29};
+constexpr double kCostPs[3][10] = {
+    {1.13, 1.20, 1.25, 1.32, 1.38, 1.44, 1.58, 1.76, 1.92, 2.40},
+    {1.98, 2.01, 2.07, 2.23, 2.30, 2.45, 2.84, 3.26, 3.53, 4.31},
+    {2.11, 2.18, 2.26, 2.39, 2.50, 2.62, 3.25, 3.72, 4.02, 4.79},
+};
+
+double ray_cost_ps(int P, double near_per_ray)
 {
-    switch (P) {
-    case 1: return 1.60;
-    case 2: return 1.62;
-    case 3: return 1.64;
-    case 4: return 1.655;
-    case 5: return 1.68;
-    case 6: return 1.76;
-    case 8: return 1.915;
-    case 10: return 2.07;
-    case 12: return 2.23;
-    default: return 2.55;
-    }
+    int q = 9;
+    for (int i = 0; i < 10; ++i)
+        if (kCostOrders[i] >= P) { q = i; break; }
+    if (near_per_ray <= kCostNear[0]) return kCostPs[0][q];
+    if (near_per_ray >= kCostNear[2]) return kCostPs[2][q];
+    const int r = near_per_ray < kCostNear[1] ? 0 : 1;
+    const double f = (near_per_ray - kCostNear[r]) / (kCostNear[r + 1] - kCostNear[r]);
+    return (1.0 - f) * kCostPs[r][q] + f * kCostPs[r + 1][q];
 }
-// hierarchical build and node record, nanoseconds per node and coefficient
-// (k_node_shift: 6.3 ms for 1.38e6 nodes x 5 coefficients)
-constexpr double kNodeCostNs = 1.1;
+// whole field build, nanoseconds per level-2 node and coefficient: the
+// paper-scale field's create time grew by 4.6 ms from the (60, 10), p = 5
+// grid to the (80, 20), p = 4 grid, 3.57e6 more node coefficients
+constexpr double kNodeCostNs = 1.3;
 
 struct GridChoice {
     int sx = 20, sy = 20, p = 0;
@@ -269,11 +280,12 @@ struct GridChoice {
 struct TuneCand {
     int sx, sy, P;
     double nodes, rays;
+    double near_per_ray;            // mean near-list length (level 1 is the same for all candidates)
 };
 
 double cand_cost(const TuneCand &c, int P)
 {
-    return c.rays * ray_cost_ps(P) * 1e-3 + c.nodes * (P + 1) * kNodeCostNs;   // ns
+    return c.rays * ray_cost_ps(P, c.near_per_ray) * 1e-3 + c.nodes * (P + 1) * kNodeCostNs;   // ns
 }
 
 uint64_t mix64(uint64_t h, uint64_t v)
@@ -353,6 +365,21 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
         }
     const double tol = d.far_tol > 0.0 ? d.far_tol : 1e-7;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // mean near-list length over the level-1 cells (3 x 3 block counts of the
+    // binned lenses; cells of the lattice weigh alike)
+    double near_per_ray = 0.0;
+    if (e == cudaSuccess && !cands.empty()) {
+        const Geo &gc = cands[0].g;
+        std::vector<int32_t> cnt((size_t)(gc.NEx * gc.NEy + 1));
+        e = cudaMemcpy(cnt.data(), cands[0].counts, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        double tot = 0.0;
+        for (int64_t cy = 0; cy < gc.N1y && e == cudaSuccess; ++cy)
+            for (int64_t cx = 0; cx < gc.N1x; ++cx)
+                for (int64_t dy = 0; dy < 3; ++dy)
+                    for (int64_t dxx = 0; dxx < 3; ++dxx)
+                        tot += cnt[(size_t)((cy + dy) * gc.NEx + cx + dxx)];
+        near_per_ray = tot / (double)std::max<int64_t>(1, gc.N1x * gc.N1y);
+    }
     std::vector<TuneCand> res;
     for (Cand &c : cands) {
         if (e != cudaSuccess) break;
@@ -369,7 +396,7 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
             }
         }
         res.push_back(TuneCand{c.sx, c.sy, mixed_p_supported(p), (double)c.g.N2x * (double)c.g.N2y,
-                               (double)c.g.n3x * (double)c.g.n3y});
+                               (double)c.g.n3x * (double)c.g.n3y, near_per_ray});
     }
     for (Cand &c : cands) {
         if (c.cells) cudaFreeAsync(c.cells, s);
@@ -502,6 +529,7 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     ML_CK(f->alloc(&f->d_scell, n, s));
     ML_CK(f->alloc(&f->d_perm, n, s));
     ML_CK(f->alloc(&f->d_stats, 8, s));
+    ML_CK(f->alloc(&f->d_sum, 1, s));
     ML_CK(f->alloc(&f->d_work, 1, s));
     ML_CK(f->alloc(&f->d_status, 1, s));
     ML_CK(cudaHostAlloc((void **)&f->h_abort, sizeof(int), cudaHostAllocMapped));
@@ -572,7 +600,7 @@ int planned_order(const ml_field *f)
 
 // Finish: far-field coefficients of order p at every level-2 node (§3.2
 // Level 2), node records, zeroed map.
-ml_status create_finish(ml_field *f, int p, cudaStream_t s)
+ml_status create_finish(ml_field *f, int p, cudaStream_t s, bool sync = true)
 {
     const ml_field_desc *d = &f->desc;
     Geo &g = f->g;
@@ -614,7 +642,7 @@ ml_status create_finish(ml_field *f, int p, cudaStream_t s)
         ML_CK(f->alloc(&f->d_map_f32, npix, s));
         ML_CK(cudaMemsetAsync(f->d_map_f32, 0, npix * sizeof(float), s));
     }
-    ML_CK(cudaStreamSynchronize(s));
+    if (sync) ML_CK(cudaStreamSynchronize(s));
     ML_CK(cudaGetLastError());
     return ML_OK;
 }
@@ -826,16 +854,38 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
         }
     }
     b->fields.assign(n, nullptr);
-    std::vector<int> order(n);
     for (int32_t i = 0; i < n; ++i) {
         b->fields[i] = new (std::nothrow) ml_field();
         if (!b->fields[i]) return fail(ML_ERR_OOM, "host allocation failed");
         ml_status st = create_plan(&plan[i], s, b->fields[i]);
         if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
         b->fields[i]->tuned = tuned[i];
-        order[i] = planned_order(b->fields[i]);
-        st = create_finish(b->fields[i], order[i], s);
-        if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
+    }
+    // coefficient builds of different maps overlap on a few streams
+    {
+        constexpr int kBuildStreams = 8;
+        cudaStream_t bs[kBuildStreams] = {};
+        cudaEvent_t ready = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, s);
+        for (int q = 0; q < kBuildStreams && e == cudaSuccess; ++q) {
+            e = cudaStreamCreateWithFlags(&bs[q], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(bs[q], ready, 0);
+        }
+        ml_status st = ML_OK;
+        for (int32_t i = 0; i < n && e == cudaSuccess && st == ML_OK; ++i) {
+            st = create_finish(b->fields[i], planned_order(b->fields[i]), bs[i % kBuildStreams], false);
+            if (st != ML_OK) st = fail(st, "map " + std::to_string(i) + ": " + g_err);
+        }
+        for (int q = 0; q < kBuildStreams; ++q) {
+            if (!bs[q]) continue;
+            cudaError_t e2 = cudaStreamSynchronize(bs[q]);
+            if (e == cudaSuccess) e = e2;
+            cudaStreamDestroy(bs[q]);
+        }
+        if (ready) cudaEventDestroy(ready);
+        if (st != ML_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "batch build");
     }
     b->num_sms = b->fields[0]->num_sms;
     size_t mu_total = 0;
@@ -955,6 +1005,8 @@ ml_status ml_batch_run(ml_batch *b, int32_t use_graph, void *stream)
     for (ml_field *f : b->fields) {
         f->launches = 1;
         f->rays_asked = (uint64_t)f->g.n3x * (uint64_t)f->g.n3y;
+        f->map_base = 0;
+        f->in_at_set = 0;
     }
     return ML_OK;
 }
@@ -1272,10 +1324,17 @@ ml_status ml_field_set_counts(ml_field *f, const uint32_t *counts, int32_t in_is
 {
     if (!f || !counts) return fail(ML_ERR_INVALID_ARG, "NULL argument");
     if (!f->d_map_u32) return fail(ML_ERR_STATE, "a CIC field has no integer counts");
+    cudaStream_t s = (cudaStream_t)stream;
     const size_t npix = (size_t)f->g.mnx * f->g.mny;
+    unsigned long long sum = 0, st[8];
     ML_CK(cudaMemcpyAsync(f->d_map_u32, counts, npix * sizeof(uint32_t),
-                          in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          (cudaStream_t)stream));
+                          in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    ML_CK(launch_map_sum(f->d_map_u32, npix, f->d_sum, f->num_sms, s));
+    ML_CK(cudaMemcpyAsync(&sum, f->d_sum, sizeof(sum), cudaMemcpyDeviceToHost, s));
+    ML_CK(cudaMemcpyAsync(st, f->d_stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+    ML_CK(cudaStreamSynchronize(s));
+    f->map_base = sum;
+    f->in_at_set = st[ML_STAT_RAYS_IN];
     return ML_OK;
 }
 
@@ -1290,6 +1349,8 @@ ml_status ml_field_clear(ml_field *f, void *stream)
     ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
     f->rays_asked = 0;
     f->launches = 0;
+    f->map_base = 0;
+    f->in_at_set = 0;
     return ML_OK;
 }
 
@@ -1297,11 +1358,16 @@ ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream)
 {
     if (!f || !out) return fail(ML_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long st[8];
+    unsigned long long st[8], sum = 0;
     unsigned flags = 0;
+    if (f->d_map_u32)
+        ML_CK(launch_map_sum(f->d_map_u32, (size_t)f->g.mnx * f->g.mny, f->d_sum, f->num_sms, s));
     ML_CK(cudaMemcpyAsync(st, f->d_stats, sizeof(st), cudaMemcpyDeviceToHost, s));
     ML_CK(cudaMemcpyAsync(&flags, f->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    if (f->d_map_u32) ML_CK(cudaMemcpyAsync(&sum, f->d_sum, sizeof(sum), cudaMemcpyDeviceToHost, s));
     ML_CK(cudaStreamSynchronize(s));
+    // a wrapped pixel loses 2^32 from the map's sum
+    if (f->d_map_u32 && sum != f->map_base + (st[ML_STAT_RAYS_IN] - f->in_at_set)) flags |= 1u;
     for (int q = 0; q < 8; ++q) out[q] = st[q];
     out[ML_STAT_LAUNCHES] = f->launches;
     out[ML_STAT_FLAGS] = flags;

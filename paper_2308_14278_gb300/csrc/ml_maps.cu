@@ -2,6 +2,8 @@
 // Gaussian source along straight tracks (§4.1, Fig. 3).
 #include "ml_internal.cuh"
 
+#include <algorithm>
+
 #include <math.h>
 
 #include <mutex>
@@ -254,6 +256,38 @@ cudaError_t launch_light_curves_dev(const Geo &g, const uint32_t *cu, const floa
     if (n == 0) return cudaSuccess;
     k_light_curves<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g, cu, cf, scale, d_tracks, n_tracks,
                                                                n_samples, h, d_taps, out);
+    return cudaGetLastError();
+}
+
+// ---- 64-bit sum of a count map -------------------------------------------------
+//
+// The shooting kernels add counts with fire-and-forget atomics, so a wrapped
+// uint32 pixel is not seen there; it shows as a map sum (taken in 64 bits)
+// that falls short of the in-map ray counter by a multiple of 2^32.
+__global__ void k_map_sum(const uint32_t *__restrict__ map, size_t n, unsigned long long *sum)
+{
+    unsigned long long acc = 0;
+    const size_t n4 = n / 4;
+    const uint4 *m4 = reinterpret_cast<const uint4 *>(map);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 v = m4[i];
+        acc += (unsigned long long)v.x + v.y + (unsigned long long)v.z + v.w;
+    }
+    for (size_t i = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        acc += map[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
+}
+
+cudaError_t launch_map_sum(const uint32_t *map, size_t n, unsigned long long *sum, int num_sms,
+                           cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(sum, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    const size_t want = (n / 4 + 255) / 256;
+    const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>(want, (size_t)num_sms * 8));
+    k_map_sum<<<blocks, 256, 0, s>>>(map, n, sum);
     return cudaGetLastError();
 }
 

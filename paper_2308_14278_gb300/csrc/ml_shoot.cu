@@ -182,11 +182,12 @@ __global__ void __launch_bounds__(256) k_shoot_fp64(ShootArgs a)
 
 // Per-lane run-length state of the NGP deposit: consecutive rays of a lane's
 // walk usually land in the same pixel (the macro map compresses x), so counts
-// are merged and added with one atomic when the pixel changes.  The atomic's
-// old value is checked for wrap-around at the next flush, off the critical path.
+// are merged and added with one atomic when the pixel changes.  The atomics
+// return nothing (fire-and-forget reductions); a wrapped uint32 count is found
+// afterwards by comparing the map's 64-bit sum with the in-map ray counter.
 struct RunState {
     int cx, cy;
-    unsigned cnt, pold, pcnt, ovf;
+    unsigned cnt;
     unsigned in, out;
 };
 
@@ -194,9 +195,7 @@ __device__ __forceinline__ void run_flush(RunState &rs, uint32_t *map, int mnx, 
 {
     if (rs.cnt == 0) return;
     if ((unsigned)rs.cx < (unsigned)mnx && (unsigned)rs.cy < (unsigned)mny) {
-        rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
-        rs.pold = atomicAdd(map + (size_t)rs.cy * (unsigned)mnx + (unsigned)rs.cx, rs.cnt);
-        rs.pcnt = rs.cnt;
+        atomicAdd(map + (size_t)rs.cy * (unsigned)mnx + (unsigned)rs.cx, rs.cnt);
         rs.in += rs.cnt;
     } else {
         rs.out += rs.cnt;
@@ -246,9 +245,7 @@ __device__ __forceinline__ void run_step(RunState &rs, bool valid, int gx, int g
         if (chg) {
             if (rs.cnt) {
                 if ((unsigned)rs.cx < (unsigned)mnx && (unsigned)rs.cy < (unsigned)mny) {
-                    rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
-                    rs.pold = atomicAdd(map + (size_t)rs.cy * (unsigned)mnx + (unsigned)rs.cx, rs.cnt);
-                    rs.pcnt = rs.cnt;
+                    atomicAdd(map + (size_t)rs.cy * (unsigned)mnx + (unsigned)rs.cx, rs.cnt);
                     rs.in += rs.cnt;
                 } else {
                     rs.out += rs.cnt;
@@ -268,9 +265,7 @@ __device__ __forceinline__ void flush_run(RunState &rs, int cx, int cy, unsigned
 {
     if (cnt == 0) return;
     if ((unsigned)cx < (unsigned)mnx && (unsigned)cy < (unsigned)mny) {
-        rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
-        rs.pold = atomicAdd(map + (size_t)cy * (unsigned)mnx + (unsigned)cx, cnt);
-        rs.pcnt = cnt;
+        atomicAdd(map + (size_t)cy * (unsigned)mnx + (unsigned)cx, cnt);
         rs.in += cnt;
     } else {
         rs.out += cnt;
@@ -284,6 +279,14 @@ __device__ __forceinline__ void flush_run(RunState &rs, int cx, int cy, unsigned
 // indices where it starts and ends, so no per-ray counting is needed; one
 // warp vote per pair decides whether any lane's pixel changed.  Per ray the
 // arithmetic is exactly near_sum_f32's and row_eval's.
+//
+// Pixels are compared in their raw floor form: the bit pattern r of
+// X + 1.5 * 2^23 rounded toward -inf, so that pixel = r - 0x4B400000 + base
+// (wrapping 32-bit arithmetic, a bijection); the pixel itself is formed only
+// when a run is flushed.  A ray that coincides with a lens (close-pass path
+// fails) gets a near sum of 1e30, which sends it far outside the map; it is
+// counted as dropped there and as out by the run, and the kernel's epilogue
+// subtracts the dropped rays from the out count.
 template <int P, int NN>
 __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
                                            int kbeg, int kend, bool on, float dyl, float dyl_lo,
@@ -299,64 +302,104 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         dy2[q] = __fmul_rn(dy[q], dy[q]);
     }
     const Geo &g = a.g;
+    const unsigned offx = (unsigned)rp.bx - 0x4B400000u, offy = (unsigned)rp.by - 0x4B400000u;
+    unsigned rcx = (unsigned)rs.cx - offx, rcy = (unsigned)rs.cy - offy;   // raw form of the run's pixel
     int kst = kbeg;                      // first ray of the current run in this walk
     float u = __fadd_rn((float)kbeg, a.c0_f);
-    for (int k = kbeg; k < kend; k += 2, u += 2.f) {
+
+    // near sum of one ray (exactly near_sum_f32's arithmetic)
+    auto near = [&](float t, float &sx, float &sy, float &mn) {
+        sx = 0.f; sy = 0.f; mn = 3.0e38f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            float dx = __fsub_rn(t, lx[q]);
+            float r2 = __fmaf_rn(dx, dx, dy2[q]);
+            mn = fminf(mn, r2);
+            float sv = __fmul_rn(lm[q], rcp_approx(r2));
+            sx = __fmaf_rn(dx, sv, sx);
+            sy = __fmaf_rn(dy[q], sv, sy);
+        }
+    };
+    auto raw = [&](float X, float Y, float sx, float sy, unsigned &rx, unsigned &ry) {
+        rx = (unsigned)__float_as_int(__fadd_rd(__fmaf_rn(-sx, a.ipx_f, X), 12582912.0f));
+        ry = (unsigned)__float_as_int(__fadd_rd(__fmaf_rn(-sy, a.ipy_f, Y), 12582912.0f));
+    };
+    // a failed close pass (ray on a lens) sends the ray far outside the map
+    auto close_pass = [&](bool c, float uu, float t, float &sx, float &sy) {
+        if (c && !near_sum_hilo(nl, NN, uu, t, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx, sy)) {
+            sx = 1.0e30f;
+            ++drop;
+        }
+    };
+
+    int k = kbeg;
+    for (; k + 1 < kend; k += 2, u += 2.f) {
         const float u1 = __fadd_rn(u, 1.f);
         const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
         float X0, Y0, X1, Y1;
         row_eval<P>(rp, t0, X0, Y0);
         row_eval<P>(rp, t1, X1, Y1);
-        float sx0 = 0.f, sy0 = 0.f, mn0 = 3.0e38f, sx1 = 0.f, sy1 = 0.f, mn1 = 3.0e38f;
-#pragma unroll
-        for (int q = 0; q < NN; ++q) {
-            float dx0 = __fsub_rn(t0, lx[q]), dx1 = __fsub_rn(t1, lx[q]);
-            float r20 = __fmaf_rn(dx0, dx0, dy2[q]), r21 = __fmaf_rn(dx1, dx1, dy2[q]);
-            mn0 = fminf(mn0, r20);
-            mn1 = fminf(mn1, r21);
-            float s0 = __fmul_rn(lm[q], rcp_approx(r20)), s1 = __fmul_rn(lm[q], rcp_approx(r21));
-            sx0 = __fmaf_rn(dx0, s0, sx0);
-            sy0 = __fmaf_rn(dy[q], s0, sy0);
-            sx1 = __fmaf_rn(dx1, s1, sx1);
-            sy1 = __fmaf_rn(dy[q], s1, sy1);
-        }
-        const bool has1 = k + 1 < kend;  // warp-uniform
-        bool ok0 = true, ok1 = true;
+        float sx0, sy0, mn0, sx1, sy1, mn1;
+        near(t0, sx0, sy0, mn0);
+        near(t1, sx1, sy1, mn1);
         if (NN > 0) {
-            const bool c0 = on && mn0 < a.rc2, c1 = on && has1 && mn1 < a.rc2;
+            const bool c0 = on && mn0 < a.rc2, c1 = on && mn1 < a.rc2;
             if (__ballot_sync(0xffffffffu, c0 || c1)) {
-                if (c0) ok0 = near_sum_hilo(nl, NN, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx0, sy0);
-                if (c1) ok1 = near_sum_hilo(nl, NN, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx1, sy1);
+                close_pass(c0, u, t0, sx0, sy0);
+                close_pass(c1, u1, t1, sx1, sy1);
             }
         }
-        int gx0, gy0, gx1, gy1;
-        pixel_xy(__fmaf_rn(-sx0, a.ipx_f, X0), __fmaf_rn(-sy0, a.ipy_f, Y0), rp.bx, rp.by, gx0, gy0);
-        pixel_xy(__fmaf_rn(-sx1, a.ipx_f, X1), __fmaf_rn(-sy1, a.ipy_f, Y1), rp.bx, rp.by, gx1, gy1);
-        if (NN > 0) {
-            if (!ok0) { gx0 = -1; gy0 = -1; drop += on ? 1u : 0u; }
-            if (!ok1) { gx1 = -1; gy1 = -1; drop += (on && has1) ? 1u : 0u; }
-        }
-        const bool ch0 = on && (gx0 != rs.cx || gy0 != rs.cy);
-        const int nx = ch0 ? gx0 : rs.cx, ny = ch0 ? gy0 : rs.cy;
-        const bool ch1 = on && has1 && (gx1 != nx || gy1 != ny);
+        unsigned rx0, ry0, rx1, ry1;
+        raw(X0, Y0, sx0, sy0, rx0, ry0);
+        raw(X1, Y1, sx1, sy1, rx1, ry1);
+        // after ray 0 the run's pixel is ray 0's whether or not it changed
+        const bool ch0 = on && (rx0 != rcx || ry0 != rcy);
+        const bool ch1 = on && (rx1 != rx0 || ry1 != ry0);
         if (__ballot_sync(0xffffffffu, ch0 || ch1)) {
             if (ch0) {
-                flush_run(rs, rs.cx, rs.cy, rs.cnt + (unsigned)(k - kst), a.map_u32, g.mnx, g.mny);
+                flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(k - kst),
+                          a.map_u32, g.mnx, g.mny);
                 rs.cnt = 0;
                 kst = k;
-                rs.cx = gx0;
-                rs.cy = gy0;
+                rcx = rx0;
+                rcy = ry0;
             }
             if (ch1) {
-                flush_run(rs, rs.cx, rs.cy, rs.cnt + (unsigned)(k + 1 - kst), a.map_u32, g.mnx, g.mny);
+                flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(k + 1 - kst),
+                          a.map_u32, g.mnx, g.mny);
                 rs.cnt = 0;
                 kst = k + 1;
-                rs.cx = gx1;
-                rs.cy = gy1;
+                rcx = rx1;
+                rcy = ry1;
+            }
+        }
+    }
+    if (k < kend) {                      // odd tail (warp-uniform)
+        const float t0 = __fmul_rn(u, a.l3x_f);
+        float X0, Y0, sx0, sy0, mn0;
+        row_eval<P>(rp, t0, X0, Y0);
+        near(t0, sx0, sy0, mn0);
+        if (NN > 0) {
+            const bool c0 = on && mn0 < a.rc2;
+            if (__ballot_sync(0xffffffffu, c0)) close_pass(c0, u, t0, sx0, sy0);
+        }
+        unsigned rx0, ry0;
+        raw(X0, Y0, sx0, sy0, rx0, ry0);
+        const bool ch0 = on && (rx0 != rcx || ry0 != rcy);
+        if (__ballot_sync(0xffffffffu, ch0)) {
+            if (ch0) {
+                flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(k - kst),
+                          a.map_u32, g.mnx, g.mny);
+                rs.cnt = 0;
+                kst = k;
+                rcx = rx0;
+                rcy = ry0;
             }
         }
     }
     if (on) rs.cnt += (unsigned)(kend - kst);
+    rs.cx = (int)(rcx + offx);
+    rs.cy = (int)(rcy + offy);
 }
 
 // The same for a near list of any length (read from shared memory).
@@ -468,7 +511,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4 *near = smem + wid * a.near_cap;
     float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * a.near_cap) + wid * a.near_cap;
-    RunState rs{-1, -1, 0u, 0u, 0u, 0u, 0u, 0u};
+    RunState rs{-1, -1, 0u, 0u, 0u};
     unsigned drop = 0;
     unsigned long long pairs = 0, tasks = 0;
     float dyl, dyl_lo;
@@ -480,9 +523,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
         shoot_task<P>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks);
     }
     run_flush(rs, a.map_u32, a.g.mnx, a.g.mny);
-    rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
     // dropped rays were sent to (-1, -1) and counted as out above
-    flush_stats(a, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, rs.ovf);
+    flush_stats(a, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
 }
 
 // Batched persistent kernel: one launch over the tasks of many maps (all
@@ -496,7 +538,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float4 *near = smem + wid * b.near_cap;
     float2 *nlo = reinterpret_cast<float2 *>(smem + WARPS_PER_CTA * b.near_cap) + wid * b.near_cap;
-    RunState rs{-1, -1, 0u, 0u, 0u, 0u, 0u, 0u};
+    RunState rs{-1, -1, 0u, 0u, 0u};
     unsigned drop = 0;
     unsigned long long pairs = 0, tasks = 0;
     float dyl = 0.f, dyl_lo = 0.f;
@@ -525,9 +567,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
             if (cur >= 0) {
                 const ShootArgs &ac = b.args[cur];
                 run_flush(rs, ac.map_u32, ac.g.mnx, ac.g.mny);
-                rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
-                flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, rs.ovf);
-                rs = RunState{-1, -1, 0u, 0u, 0u, 0u, 0u, 0u};
+                            flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
+                rs = RunState{-1, -1, 0u, 0u, 0u};
                 drop = 0;
                 pairs = 0;
                 tasks = 0;
@@ -541,8 +582,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
     if (cur >= 0) {
         const ShootArgs &ac = b.args[cur];
         run_flush(rs, ac.map_u32, ac.g.mnx, ac.g.mny);
-        rs.ovf |= (rs.pold > 0xFFFFFFFFu - rs.pcnt);
-        flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, rs.ovf);
+            flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
     }
 }
 

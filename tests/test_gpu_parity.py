@@ -296,3 +296,29 @@ def test_paper_scale_sampled_parity(ml):
     st = f.stats()
     assert st["rays_in"] + st["rays_out"] + st["rays_dropped"] == r1 - r0
     f.close()
+
+
+def test_wrapped_count_is_reported(ml):
+    """Counts are added without reading them back; a wrapped uint32 pixel
+    must still be reported by ml_field_stats (map sum against in-map rays)."""
+    import torch
+    w = _mixed_case()
+    f = _field(ml, w, precision=ml.PREC_MIXED)
+    f.shoot()
+    counts = f.counts()
+    assert f.stats()["rays_in"] == int(counts.to(torch.int64).sum())
+    # preset the busiest pixel just below 2^32 and shoot the same rays again
+    flat = counts.view(-1)
+    k = int(torch.argmax(flat))
+    assert int(flat[k]) > 0
+    preset = torch.zeros_like(counts)
+    preset.view(-1)[k] = -1                   # 0xFFFFFFFF as uint32
+    ml.ml_field_set_counts(f.h, preset)
+    f.shoot()
+    d, st = ml.ml_field_stats(f.h, None, check=False)
+    assert st == 5 and d["flags"] & 1          # ML_ERR_OVERFLOW
+    # without the preset the same run is clean
+    f.clear()
+    f.shoot()
+    assert f.stats()["rays_in"] == int(f.counts().to(torch.int64).sum())
+    f.close()
