@@ -239,13 +239,6 @@ constexpr int ADJ_BUF = 128;          // buffered rays per warp for the near pas
 constexpr int FAR_THREADS = 256;      // lenses per block of k_adj_far
 constexpr int FAR_NODES = 32;         // nodes per shared-memory tile of k_adj_far
 
-__device__ __forceinline__ int pow2_at_least(int n)
-{
-    int p = 1;
-    while (p < n) p <<= 1;
-    return p;
-}
-
 // dLoss/dbeta of one ray from its cloud-in-cell weights: with the ray at
 // pixel coordinates (bx + X, by + Y), weights (1-wx)(1-wy), wx(1-wy),
 // (1-wx)wy, wx wy to the four nearest pixel centres, and
@@ -274,40 +267,59 @@ __device__ __forceinline__ void cic_dbeta(const Geo &g, const float *__restrict_
 
 // Near pass: the buffered rays (x offset from the node, y offset from the
 // task's first row, dL/dbeta) against the task's near lenses.  Lane = (lens
-// slot, ray group): with nn lenses padded to a power of two `pad`, the 32/pad
-// groups take every (32/pad)-th ray and are summed at the end, so short lists
-// keep all lanes busy.  Per pair, t = (g . d) / r^2 and
+// slot, ray group): with a chunk of c <= 32 lenses, floor(32 / c) groups of c
+// lanes take every group-th ray, two rays per step with separate sums, and
+// the groups are summed at the end, so short lists keep the lanes busy.  Per
+// pair, t = (g . d) / r^2 and
 //   ax += (g_x - 2 d_x t) / r^2,  ay += (g_y - 2 d_y t) / r^2,  am += t,
 // later scaled to dL/dx_k = m_k ax, dL/dy_k = m_k ay, dL/dm_k = -am.
+__device__ __forceinline__ void near_pair(const float4 &R, const float4 &L, const float2 &lo, float &ax,
+                                          float &ay, float &am)
+{
+    const float dx = __fsub_rn(__fsub_rn(R.x, L.x), lo.x);
+    const float dy = __fsub_rn(__fsub_rn(R.y, L.y), lo.y);
+    const float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+    const float inv = rcp_approx(r2);
+    const float tq = __fmul_rn(__fmaf_rn(R.z, dx, __fmul_rn(R.w, dy)), inv);
+    const float v = -2.f * tq;
+    am += tq;
+    ax = __fmaf_rn(inv, __fmaf_rn(dx, v, R.z), ax);
+    ay = __fmaf_rn(inv, __fmaf_rn(dy, v, R.w), ay);
+}
+
 __device__ __forceinline__ void near_pass(const float4 *near, const float2 *nlo, double *acc,
                                           const float4 *buf, int nn, int nb, int lane)
 {
     __syncwarp();
-    const int pad = nn >= 32 ? 32 : pow2_at_least(nn);
-    const int ngrp = 32 / pad;
-    const int sl = lane & (pad - 1), grp = lane / pad;
     for (int c0 = 0; c0 < nn; c0 += 32) {
+        const int cn = min(32, nn - c0);            // lenses in this chunk
+        const int ngrp = 32 / cn, used = ngrp * cn;
+        const int sl = lane % cn, grp = lane / cn;
+        const bool have = lane < used;
         const int slot = c0 + sl;
-        const bool have = slot < nn;
         const float4 L = have ? near[slot] : make_float4(1.0e18f, 1.0e18f, 0.f, 0.f);
         const float2 lo = have ? nlo[slot] : make_float2(0.f, 0.f);
-        float ax = 0.f, ay = 0.f, am = 0.f;
-        for (int r = grp; r < nb; r += ngrp) {
-            const float4 R = buf[r];
-            const float dx = __fsub_rn(__fsub_rn(R.x, L.x), lo.x);
-            const float dy = __fsub_rn(__fsub_rn(R.y, L.y), lo.y);
-            const float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-            const float inv = rcp_approx(r2);
-            const float tq = __fmul_rn(__fmaf_rn(R.z, dx, __fmul_rn(R.w, dy)), inv);
-            const float v = -2.f * tq;
-            am += tq;
-            ax = __fmaf_rn(inv, __fmaf_rn(dx, v, R.z), ax);
-            ay = __fmaf_rn(inv, __fmaf_rn(dy, v, R.w), ay);
+        float ax = 0.f, ay = 0.f, am = 0.f, bx = 0.f, by = 0.f, bm = 0.f;
+        int r = have ? grp : nb;
+        for (; r + ngrp < nb; r += 2 * ngrp) {
+            const float4 R0 = buf[r], R1 = buf[r + ngrp];
+            near_pair(R0, L, lo, ax, ay, am);
+            near_pair(R1, L, lo, bx, by, bm);
         }
-        for (int off = pad; off < 32; off <<= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, off);
-            ay += __shfl_xor_sync(0xffffffffu, ay, off);
-            am += __shfl_xor_sync(0xffffffffu, am, off);
+        if (r < nb) near_pair(buf[r], L, lo, ax, ay, am);
+        ax += bx;
+        ay += by;
+        am += bm;
+        // sum the groups of each slot into group 0
+        for (int off = cn; off < used; off <<= 1) {
+            const float ox = __shfl_down_sync(0xffffffffu, ax, off);
+            const float oy = __shfl_down_sync(0xffffffffu, ay, off);
+            const float om = __shfl_down_sync(0xffffffffu, am, off);
+            if (lane + off < used) {
+                ax += ox;
+                ay += oy;
+                am += om;
+            }
         }
         if (grp == 0 && have) {
             acc[3 * slot] += (double)ax;

@@ -586,7 +586,10 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
     }
 }
 
-// Cloud-in-cell variant: a float map, four weighted atomics per ray.
+// Cloud-in-cell variant: a float map.  A ray's bilinear weights go to the
+// four pixel centres around it; consecutive rays of a lane that share those
+// four pixels (the macro map compresses x) have their weights summed in
+// registers, and the run is added with four atomics when the quad changes.
 template <int P>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mixed_cic(ShootArgs a)
 {
@@ -600,6 +603,23 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
     const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
     unsigned in = 0, out = 0, drop = 0;
     unsigned long long pairs = 0, tasks = 0;
+    // the lane's run: lower-left pixel of the quad, summed weights, rays
+    unsigned qx = 0xFFFFFFFFu, qy = 0xFFFFFFFFu, rc = 0;
+    float W0 = 0.f, W1 = 0.f, W2 = 0.f, W3 = 0.f;
+    const unsigned mnx = (unsigned)g.mnx, mny = (unsigned)g.mny;
+    auto flush = [&]() {
+        if (rc == 0) return;
+        bool any = false;
+        // the quad's second column and row, in wrapping 32-bit arithmetic
+        // (qx = 0xFFFFFFFF is the column left of the map, whose neighbour is 0)
+        const unsigned px1 = qx + 1u, py1 = qy + 1u;
+        const bool x0 = qx < mnx, x1 = px1 < mnx, y0 = qy < mny, y1 = py1 < mny;
+        if (x0 && y0) { atomicAdd(a.map_f32 + ((size_t)qy * mnx + qx), W0); any = true; }
+        if (x1 && y0) { atomicAdd(a.map_f32 + ((size_t)qy * mnx + px1), W1); any = true; }
+        if (x0 && y1) { atomicAdd(a.map_f32 + ((size_t)py1 * mnx + qx), W2); any = true; }
+        if (x1 && y1) { atomicAdd(a.map_f32 + ((size_t)py1 * mnx + px1), W3); any = true; }
+        if (any) in += rc; else out += rc;
+    };
     for (;;) {
         bool stop;
         const int64_t t = fetch_task(a, lane, stop);
@@ -643,21 +663,25 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
                 float flx, fly;
                 int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
                 float wx = __fsub_rn(fx, flx), wy = __fsub_rn(fy, fly);
-                unsigned ix = (unsigned)rp.bx + (unsigned)kx;
-                unsigned iy = (unsigned)rp.by + (unsigned)ky;
-                bool any = false;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    unsigned px = ix + (unsigned)(qq & 1), py = iy + (unsigned)(qq >> 1);
-                    if (px >= (unsigned)g.mnx || py >= (unsigned)g.mny) continue;
-                    float w = __fmul_rn((qq & 1) ? wx : 1.f - wx, (qq >> 1) ? wy : 1.f - wy);
-                    atomicAdd(a.map_f32 + (size_t)py * (unsigned)g.mnx + px, w);
-                    any = true;
+                const unsigned ix = (unsigned)rp.bx + (unsigned)kx;
+                const unsigned iy = (unsigned)rp.by + (unsigned)ky;
+                if (ix != qx || iy != qy) {
+                    flush();
+                    qx = ix;
+                    qy = iy;
+                    W0 = W1 = W2 = W3 = 0.f;
+                    rc = 0;
                 }
-                if (any) ++in; else ++out;
+                const float ox = 1.f - wx, oy = 1.f - wy;
+                W0 = __fmaf_rn(ox, oy, W0);
+                W1 = __fmaf_rn(wx, oy, W1);
+                W2 = __fmaf_rn(ox, wy, W2);
+                W3 = __fmaf_rn(wx, wy, W3);
+                ++rc;
             }
         }
     }
+    flush();
     flush_stats(a, in, out, drop, pairs, lane == 0 ? tasks : 0, 0u);
 }
 
