@@ -48,7 +48,9 @@ class _Geom(C.Structure):
                 ("rx0", C.c_double), ("ry0", C.c_double), ("l3x", C.c_double), ("l3y", C.c_double),
                 ("n3x", C.c_int64), ("n3y", C.c_int64),
                 ("mx0", C.c_double), ("my0", C.c_double), ("dpx", C.c_double), ("dpy", C.c_double),
-                ("mnx", C.c_int64), ("mny", C.c_int64)]
+                ("mnx", C.c_int64), ("mny", C.c_int64),
+                ("macro_mode", C.c_int64), ("kappa0", C.c_double), ("d_x", C.c_double),
+                ("d_y", C.c_double)]
 
 
 class _Grid(C.Structure):
@@ -127,6 +129,10 @@ class Geometry:
     N1x: int = 0             # level-1 cells across the lattice
     N1y: int = 0
     p: int = 3
+    macro_mode: int = 0      # 0: constant (kappa, gamma), Eq. 1; 1: fold, Eq. 5
+    kappa0: float = 0.0      # fold: convergence on the critical curve
+    d_x: float = 0.0         # fold: d = -(grad kappa)_0 - (grad gamma)_0, in 1/theta_E
+    d_y: float = 0.0
 
     @property
     def n_rays(self) -> int:
@@ -135,7 +141,8 @@ class Geometry:
     def c_geom(self) -> _Geom:
         return _Geom(self.kappa, self.gamma, self.kappa_star, self.sheet_cx, self.sheet_cy,
                      self.sheet_r, self.rx0, self.ry0, self.l3x, self.l3y, self.n3x, self.n3y,
-                     self.mx0, self.my0, self.dpx, self.dpy, self.mnx, self.mny)
+                     self.mx0, self.my0, self.dpx, self.dpy, self.mnx, self.mny,
+                     self.macro_mode, self.kappa0, self.d_x, self.d_y)
 
     def c_grid(self) -> _Grid:
         return _Grid(self.n1x, self.n1y, self.n2x, self.n2y, self.N1x, self.N1y, self.p)
@@ -164,9 +171,38 @@ def _round_half_up(v: float) -> int:
     return int(math.floor(v + 0.5))
 
 
+def fold_ray_box(kappa0, d_x, d_y, src_box):
+    """Bounding box of the pre-image of the source box src_box = (x0, y0, x1,
+    y1) under the fold map of Eq. 5, beta_x = d_x theta_x^2 / 2 + d_y theta_x
+    theta_y, beta_y = 2 (1 - kappa_0) theta_y (reading: the image plane is the
+    smallest rectangle holding every image of s').
+
+    theta_y = beta_y / (2 (1 - kappa_0)).  For fixed theta_y (and d_x > 0; the
+    map is mirrored in beta_x otherwise) the images of beta_x <= x1 are
+    |theta_x - t*| <= s1 with t* = -d_y theta_y / d_x and
+    s1 = sqrt(2 x1 / d_x + (d_y theta_y / d_x)^2); t* + s1 is convex and
+    t* - s1 concave in theta_y, so the extremes lie at the ends of the
+    theta_y range.  Requires images (x1 > 0 after mirroring)."""
+    x0, y0, x1, y1 = src_box
+    a = 2.0 * (1.0 - kappa0)
+    if a == 0.0 or d_x == 0.0:
+        raise ValueError("fold map is singular")
+    ty = sorted((y0 / a, y1 / a))
+    if d_x < 0.0:
+        x0, x1, d_x, d_y = -x1, -x0, -d_x, -d_y
+    if x1 <= 0.0:
+        raise ValueError("the source box has no images under the fold map")
+    lo, hi = math.inf, -math.inf
+    for t in ty:
+        c = -d_y * t / d_x
+        s1 = math.sqrt(2.0 * x1 / d_x + (d_y * t / d_x) ** 2)
+        lo, hi = min(lo, c - s1), max(hi, c + s1)
+    return lo, ty[0], hi, ty[1]
+
+
 def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, map_n,
                     ray_box=None, ray_n=None, n_av=0.0, l1=None, l2_sub=20, p=3,
-                    l2_sub_y=None) -> Geometry:
+                    l2_sub_y=None, macro=None) -> Geometry:
     """The parameters of §3.1-§3.2 for one map.
 
     Readings: the ray rectangle is the pre-image of the widened source region
@@ -181,7 +217,11 @@ def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, ma
     mnx, mny = map_n
     dpx = (mx1 - mx0) / mnx
     dpy = (my1 - my0) / mny
-    if ray_box is None:
+    if ray_box is None and macro is not None:
+        w = 0.5 * protection_width(kappa_star)
+        rx0, ry0, rx1, ry1 = fold_ray_box(macro[1], macro[2], macro[3],
+                                          (mx0 - w, my0 - w, mx1 + w, my1 + w))
+    elif ray_box is None:
         w = 0.5 * protection_width(kappa_star)
         a = 1.0 - kappa - gamma
         b = 1.0 - kappa + gamma
@@ -222,6 +262,8 @@ def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, ma
     g = Geometry(kappa, gamma, kappa_star, sheet[0], sheet[1], sheet[2],
                  rx0, ry0, rx1, ry1, l3x, l3y, n3x, n3y, mx0, my0, dpx, dpy, mnx, mny,
                  n_in, l0, n1x, n1y, n2x, n2y, -(-n3x // n1x), -(-n3y // n1y), p)
+    if macro is not None:
+        g.macro_mode, g.kappa0, g.d_x, g.d_y = 1, float(macro[1]), float(macro[2]), float(macro[3])
     return g
 
 
@@ -229,6 +271,8 @@ def geometry_of(w, **kw) -> Geometry:
     """derive_geometry for a paper_2308_14278_gb300.inputs.Workload."""
     if getattr(w, "l1", None) is not None and "l1" not in kw:
         kw["l1"] = w.l1
+    if getattr(w, "macro", None) is not None and "macro" not in kw:
+        kw["macro"] = w.macro
     return derive_geometry(w.kappa, w.gamma, w.kappa_star, w.lenses.x, w.lenses.y, w.sheet,
                            w.map_box, w.map_n, ray_box=w.ray_box, ray_n=w.ray_n,
                            n_av=w.n_av, **kw)
@@ -448,10 +492,12 @@ def cic_grad_dM(g: Geometry, x, y, m, dL_dM, ray_begin=0, ray_end=None, threads=
     gl = np.zeros((len(x), 3))
     gp = np.zeros(3)
     gg = g.c_geom()
-    lib().orc_cic_grad(C.byref(gg), _ptr(x, C.c_double), _ptr(y, C.c_double),
-                       _ptr(m, C.c_double), len(x), int(ray_begin), int(ray_end),
-                       _ptr(G, C.c_double), cic_mu_scale(g), _ptr(gl, C.c_double),
-                       _ptr(gp, C.c_double), threads or default_threads())
+    rc = lib().orc_cic_grad(C.byref(gg), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                            _ptr(m, C.c_double), len(x), int(ray_begin), int(ray_end),
+                            _ptr(G, C.c_double), cic_mu_scale(g), _ptr(gl, C.c_double),
+                            _ptr(gp, C.c_double), threads or default_threads())
+    if rc != 0:
+        raise ValueError("the oracle's CIC gradient covers the constant-(kappa, gamma) macro only")
     return gl, gp
 
 
@@ -466,8 +512,10 @@ def cic_grad(g: Geometry, x, y, m, target, ray_begin=0, ray_end=None, threads=No
     gl = np.zeros((len(x), 3))
     gp = np.zeros(3)
     gg = g.c_geom()
-    lib().orc_cic_grad(C.byref(gg), _ptr(x, C.c_double), _ptr(y, C.c_double),
-                       _ptr(m, C.c_double), len(x), int(ray_begin), int(ray_end),
-                       _ptr(G, C.c_double), cic_mu_scale(g), _ptr(gl, C.c_double),
-                       _ptr(gp, C.c_double), threads or default_threads())
+    rc = lib().orc_cic_grad(C.byref(gg), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                            _ptr(m, C.c_double), len(x), int(ray_begin), int(ray_end),
+                            _ptr(G, C.c_double), cic_mu_scale(g), _ptr(gl, C.c_double),
+                            _ptr(gp, C.c_double), threads or default_threads())
+    if rc != 0:
+        raise ValueError("the oracle's CIC gradient covers the constant-(kappa, gamma) macro only")
     return gl, gp

@@ -12,11 +12,16 @@
  * All arithmetic is IEEE binary64; build with -ffp-contract=off so that x86
  * and Arm hosts give the same bits.
  *
- * Lens equation in the constant-(kappa, gamma) form of Eq. 1 plus the
- * microlens and negative-sheet terms of Eq. 6:
- *   beta = diag(1-kappa-gamma, 1-kappa+gamma) theta
+ * Lens equation: a macro term plus the microlens and negative-sheet terms of
+ * Eq. 6:
+ *   beta = macro(theta)
  *          - sum_k m_k (theta - theta_k) / |theta - theta_k|^2
  *          - alpha_{-kappa*}(theta)
+ * with macro(theta) either the constant-(kappa, gamma) form of Eq. 1,
+ * diag(1-kappa-gamma, 1-kappa+gamma) theta, or the fold form of Eq. 5 as
+ * printed in Eq. 6, (d_x theta_x^2 / 2 + d_y theta_x theta_y,
+ * 2 (1 - kappa_0) theta_y), whose Jacobian determinant is the
+ * 2 (1 - kappa_0) (theta . d) of Eq. 4
  * with alpha_{-kappa*} the field of a uniform disc of surface density
  * -kappa_* (centre c, radius R): -kappa_* (theta - c) inside, and
  * -kappa_* R^2 (theta - c)/|theta - c|^2 outside.
@@ -43,6 +48,8 @@ typedef struct {
     int64_t n3x, n3y;
     double mx0, my0, dpx, dpy;
     int64_t mnx, mny;
+    int64_t macro_mode;        /* 0: constant (kappa, gamma), Eq. 1; 1: fold, Eq. 5 */
+    double kappa0, d_x, d_y;   /* fold parameters (d in 1/theta_E) */
 } orc_geom;
 
 /* Three-level grid of §3.2 as laid on the ray lattice: a level-2 cell holds
@@ -98,6 +105,18 @@ static void sheet_deflection(const orc_geom *g, double tx, double ty,
     }
 }
 
+/* The smooth (macro) part of beta. */
+static void macro_term(const orc_geom *g, double tx, double ty, double *mx, double *my)
+{
+    if (g->macro_mode == 1) {
+        *mx = 0.5 * g->d_x * tx * tx + g->d_y * tx * ty;
+        *my = 2.0 * (1.0 - g->kappa0) * ty;
+    } else {
+        *mx = (1.0 - g->kappa - g->gamma) * tx;
+        *my = (1.0 - g->kappa + g->gamma) * ty;
+    }
+}
+
 static void ray_position(const orc_geom *g, int64_t r, double *tx, double *ty)
 {
     int64_t i = r % g->n3x, j = r / g->n3x;
@@ -105,15 +124,16 @@ static void ray_position(const orc_geom *g, int64_t r, double *tx, double *ty)
     *ty = g->ry0 + ((double)j + 0.5) * g->l3y;
 }
 
-/* Full lens equation (Eq. 6 with the macro term of Eq. 1), direct sum. */
+/* Full lens equation (Eq. 6), direct sum. */
 static int beta_direct(const orc_geom *g, const orc_lenses *L, double tx, double ty,
                        double *bx, double *by)
 {
-    double ax, ay, sx, sy;
+    double ax, ay, sx, sy, mx, my;
     if (deflect_direct(L, NULL, 0, tx, ty, &ax, &ay)) return 1;
     sheet_deflection(g, tx, ty, &sx, &sy);
-    *bx = (1.0 - g->kappa - g->gamma) * tx - ax - sx;
-    *by = (1.0 - g->kappa + g->gamma) * ty - ay - sy;
+    macro_term(g, tx, ty, &mx, &my);
+    *bx = mx - ax - sx;
+    *by = my - ay - sy;
     return 0;
 }
 
@@ -318,10 +338,11 @@ static int beta_interp(const orc_geom *g, const orc_grid *grid, const orc_lenses
     double complex F = 0.0;
     for (int n = grid->p; n >= 0; --n) F = F * d + c[n];
     /* alpha_far = conj(F) */
-    double sx, sy;
+    double sx, sy, mx, my;
     sheet_deflection(g, tx, ty, &sx, &sy);
-    *bx = (1.0 - g->kappa - g->gamma) * tx - ax - creal(F) - sx;
-    *by = (1.0 - g->kappa + g->gamma) * ty - ay + cimag(F) - sy;
+    macro_term(g, tx, ty, &mx, &my);
+    *bx = mx - ax - creal(F) - sx;
+    *by = my - ay + cimag(F) - sy;
     return 0;
 }
 
@@ -514,6 +535,7 @@ int orc_cic_grad(const orc_geom *g, const double *x, const double *y, const doub
                  int64_t n, int64_t ray_begin, int64_t ray_end, const double *G,
                  double scale, double *glens, double *gpar, int nthreads)
 {
+    if (g->macro_mode != 0) return -2;     /* kappa, gamma terms are those of Eq. 1 */
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     double **gl = (double **)calloc((size_t)nthreads, sizeof(double *));

@@ -125,6 +125,7 @@ class Workload:
     ray_n: tuple | None = None      # explicit (n3x, n3y), or None to use n_av
     n_av: float = 0.0
     l1: tuple | None = None         # explicit level-1 cell size, or None for Eq. 10's rule
+    macro: tuple | None = None      # ("fold", kappa0, d_x, d_y) for the fold model, else None
     n_tracks: int = 0
     track_samples: int = 4096
     sigma_px: float = 0.5

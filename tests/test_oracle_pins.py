@@ -328,3 +328,79 @@ def test_light_curves_pins():
     u = 6.3 + t * (21.7 - 6.3) - 0.5
     v = 7.1 + t * (19.9 - 7.1) - 0.5
     assert np.allclose(lc[0], 0.25 * u - 0.5 * v + 3.0, rtol=0, atol=1e-12)
+
+
+# -- Fold macro model (Eq. 4-6) --------------------------------------------------
+
+FOLD = ("fold", 0.83, 0.05, -0.047)   # kappa_0 of Table 1, d scaled up so that the image plane is small
+
+
+def _fold_geom(map_box, map_n, ray_box=None, ray_n=None, n_av=0.0, kappa_star=0.0, sheet=(0, 0, 1e6)):
+    return oracle.derive_geometry(0.0, 0.0, kappa_star, [], [], sheet, map_box, map_n,
+                                  ray_box=ray_box, ray_n=ray_n, n_av=n_av, macro=FOLD)
+
+
+def test_fold_jacobian_is_eq4():
+    """Central differences of the oracle's beta (no lenses) at lattice
+    neighbours: for the quadratic map they are exact up to rounding.  Eq. 4
+    fixes A_11 = theta . d, A_21 = 0, A_22 = 2 (1 - kappa_0) and so the
+    determinant; A_12 = d_y theta_x is what integrating Eq. 5 as printed gives."""
+    _, k0, dx, dy = FOLD
+    h = 1e-2
+    for tx, ty in [(3.0, 1.0), (-7.5, 2.0), (12.0, -4.0), (0.3, 0.2)]:
+        g = _fold_geom((0, 0, 1, 1), (4, 4), ray_box=(tx - 1.5 * h, ty - 1.5 * h, tx + 1.5 * h, ty + 1.5 * h),
+                       ray_n=(3, 3))
+        b, _ = oracle.beta_direct(g, NO, NO, NO, np.arange(9))
+        b = b.reshape(3, 3, 2)                      # [j][i]
+        A11 = (b[1, 2, 0] - b[1, 0, 0]) / (2 * h)
+        A12 = (b[2, 1, 0] - b[0, 1, 0]) / (2 * h)
+        A21 = (b[1, 2, 1] - b[1, 0, 1]) / (2 * h)
+        A22 = (b[2, 1, 1] - b[0, 1, 1]) / (2 * h)
+        assert abs(A11 - (dx * tx + dy * ty)) <= 1e-9
+        assert abs(A21) <= 1e-9 and abs(A22 - 2 * (1 - k0)) <= 1e-9
+        assert abs(A12 - dy * tx) <= 1e-9
+        assert abs((A11 * A22 - A12 * A21) - 2 * (1 - k0) * (dx * tx + dy * ty)) <= 1e-8
+
+
+def test_fold_ray_box_holds_every_image_and_is_tight():
+    box = (0.2, -1.0, 3.0, 1.5)
+    x0, y0, x1, y1 = oracle.fold_ray_box(*FOLD[1:], box)
+    # map a lattice over a larger rectangle with the oracle (no lenses)
+    wide = (x0 - 3, y0 - 1, x1 + 3, y1 + 1)
+    g = _fold_geom((0, 0, 1, 1), (4, 4), ray_box=wide, ray_n=(1200, 300))
+    b, _ = oracle.beta_direct(g, NO, NO, NO, np.arange(g.n_rays))
+    tx, ty = oracle.ray_position(g, np.arange(g.n_rays))
+    inside = (b[:, 0] >= box[0]) & (b[:, 0] <= box[2]) & (b[:, 1] >= box[1]) & (b[:, 1] <= box[3])
+    assert inside.sum() > 1000
+    assert np.all((tx[inside] >= x0) & (tx[inside] <= x1) & (ty[inside] >= y0) & (ty[inside] <= y1))
+    # tight: images come within two lattice spacings of every side
+    assert tx[inside].min() - x0 < 2 * g.l3x and x1 - tx[inside].max() < 2 * g.l3x
+    assert ty[inside].min() - y0 < 2 * g.l3y and y1 - ty[inside].max() < 2 * g.l3y
+
+
+def test_fold_map_without_lenses_is_the_two_image_magnification():
+    """No lenses, no sheet: every source point above the caustic has two images
+    with |det A| = 2 (1 - kappa_0) d_x s each, s = |theta_x - theta_*| (Eq. 4),
+    so mu(beta) = 1 / ((1 - kappa_0) d_x s(beta)),
+    s = sqrt(2 beta_x / d_x + (d_y theta_y / d_x)^2), theta_y = beta_y / (2 (1 - kappa_0)).
+    Pixel means of that closed form by Gauss-Legendre quadrature against the
+    oracle's ray counts."""
+    _, k0, dx, dy = FOLD
+    box, n = (0.5, -1.0, 3.5, 1.0), (24, 16)
+    g = _fold_geom(box, n, n_av=30000.0)
+    counts, st = oracle.shoot_direct(g, NO, NO, NO)
+    mu = counts * oracle.cic_mu_scale(g)
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    ref = np.zeros(n[::-1])
+    for j in range(n[1]):
+        for i in range(n[0]):
+            bx = g.mx0 + (i + 0.5 + 0.5 * xg) * g.dpx
+            by = g.my0 + (j + 0.5 + 0.5 * xg) * g.dpy
+            BX, BY = np.meshgrid(bx, by)
+            ty = BY / (2 * (1 - k0))
+            s = np.sqrt(2 * BX / dx + (dy * ty / dx) ** 2)
+            ref[j, i] = (np.outer(wg, wg) * (1.0 / ((1 - k0) * dx * s))).sum() / 4.0
+    rel = np.abs(mu - ref) / ref
+    assert abs(mu.sum() / ref.sum() - 1) < 1e-4          # the map's total
+    assert rel.mean() < 0.006, rel.mean()                 # lattice sampling: 0.3 % here
+    assert rel.max() < 0.02, rel.max()
