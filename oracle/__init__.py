@@ -50,7 +50,7 @@ class _Geom(C.Structure):
                 ("mx0", C.c_double), ("my0", C.c_double), ("dpx", C.c_double), ("dpy", C.c_double),
                 ("mnx", C.c_int64), ("mny", C.c_int64),
                 ("macro_mode", C.c_int64), ("kappa0", C.c_double), ("d_x", C.c_double),
-                ("d_y", C.c_double)]
+                ("d_y", C.c_double), ("sheet_shape", C.c_int64)]
 
 
 class _Grid(C.Structure):
@@ -133,6 +133,7 @@ class Geometry:
     kappa0: float = 0.0      # fold: convergence on the critical curve
     d_x: float = 0.0         # fold: d = -(grad kappa)_0 - (grad gamma)_0, in 1/theta_E
     d_y: float = 0.0
+    sheet_shape: int = 0     # 0: disc (centre, radius); 1: strip along x (centre line y, half-width)
 
     @property
     def n_rays(self) -> int:
@@ -142,7 +143,7 @@ class Geometry:
         return _Geom(self.kappa, self.gamma, self.kappa_star, self.sheet_cx, self.sheet_cy,
                      self.sheet_r, self.rx0, self.ry0, self.l3x, self.l3y, self.n3x, self.n3y,
                      self.mx0, self.my0, self.dpx, self.dpy, self.mnx, self.mny,
-                     self.macro_mode, self.kappa0, self.d_x, self.d_y)
+                     self.macro_mode, self.kappa0, self.d_x, self.d_y, self.sheet_shape)
 
     def c_grid(self) -> _Grid:
         return _Grid(self.n1x, self.n1y, self.n2x, self.n2y, self.N1x, self.N1y, self.p)
@@ -264,6 +265,8 @@ def derive_geometry(kappa, gamma, kappa_star, lens_x, lens_y, sheet, map_box, ma
                  n_in, l0, n1x, n1y, n2x, n2y, -(-n3x // n1x), -(-n3y // n1y), p)
     if macro is not None:
         g.macro_mode, g.kappa0, g.d_x, g.d_y = 1, float(macro[1]), float(macro[2]), float(macro[3])
+    if len(sheet) > 3 and sheet[3] == "strip":
+        g.sheet_shape = 1
     return g
 
 

@@ -22,9 +22,12 @@
  * printed in Eq. 6, (d_x theta_x^2 / 2 + d_y theta_x theta_y,
  * 2 (1 - kappa_0) theta_y), whose Jacobian determinant is the
  * 2 (1 - kappa_0) (theta . d) of Eq. 4
- * with alpha_{-kappa*} the field of a uniform disc of surface density
- * -kappa_* (centre c, radius R): -kappa_* (theta - c) inside, and
- * -kappa_* R^2 (theta - c)/|theta - c|^2 outside.
+ * with alpha_{-kappa*} the field of a uniform sheet of surface density
+ * -kappa_* laid where the lenses are: a disc (centre c, radius R),
+ * -kappa_* (theta - c) inside and -kappa_* R^2 (theta - c)/|theta - c|^2
+ * outside; or a strip unbounded in x and bounded in y (centre line c_y,
+ * half-width R), -2 kappa_* (theta_y - c_y) y-hat inside and
+ * -2 kappa_* R sign(theta_y - c_y) y-hat outside.
  *
  * Ray lattice (§3.2, Level 3, Eq. 11): ray (i, j) sits at the centre of
  * level-3 pixel (i, j): theta = (rx0 + (i + 1/2) l3x, ry0 + (j + 1/2) l3y);
@@ -50,6 +53,7 @@ typedef struct {
     int64_t mnx, mny;
     int64_t macro_mode;        /* 0: constant (kappa, gamma), Eq. 1; 1: fold, Eq. 5 */
     double kappa0, d_x, d_y;   /* fold parameters (d in 1/theta_E) */
+    int64_t sheet_shape;       /* 0: disc, 1: strip along x */
 } orc_geom;
 
 /* Three-level grid of §3.2 as laid on the ray lattice: a level-2 cell holds
@@ -89,11 +93,21 @@ static int deflect_direct(const orc_lenses *L, const int64_t *sel, int64_t nsel,
     return 0;
 }
 
-/* Deflection of the compensating negative sheet, alpha_{-kappa*} of Eq. 6. */
+/* Deflection of the compensating negative sheet, alpha_{-kappa*} of Eq. 6:
+ * minus the field of a uniform sheet of density kappa_*, whose divergence is
+ * 2 kappa_* inside. */
 static void sheet_deflection(const orc_geom *g, double tx, double ty,
                              double *ax, double *ay)
 {
     double ux = tx - g->sheet_cx, uy = ty - g->sheet_cy;
+    if (g->sheet_shape == 1) {
+        /* an unbounded slab: by symmetry the field is along y, 2 kappa_* uy inside */
+        double h = g->sheet_r;
+        double v = uy > h ? h : (uy < -h ? -h : uy);
+        *ax = 0.0;
+        *ay = -2.0 * g->kappa_star * v;
+        return;
+    }
     double s2 = ux * ux + uy * uy;
     double R2 = g->sheet_r * g->sheet_r;
     if (s2 <= R2) {

@@ -404,3 +404,29 @@ def test_fold_map_without_lenses_is_the_two_image_magnification():
     assert abs(mu.sum() / ref.sum() - 1) < 1e-4          # the map's total
     assert rel.mean() < 0.006, rel.mean()                 # lattice sampling: 0.3 % here
     assert rel.max() < 0.02, rel.max()
+
+
+def test_strip_sheet_cancels_the_mean_field_of_a_long_lens_strip():
+    """A long strip of lenses of density kappa_* (a regular grid, unit
+    spacing cells of mass kappa_* a^2 / pi) and the strip sheet of the same
+    density: far from the strip's ends the two fields cancel, so with a macro
+    term theta (kappa = gamma = 0) beta = theta.  Pins the strip sheet's
+    factor 2 (Gauss: a slab's field is 2 kappa_* (theta_y - c_y)) and sign."""
+    a, h, L, ks = 0.1, 1.0, 100.0, 0.1
+    xs = np.arange(-L + a / 2, L, a)
+    ys = np.arange(-h + a / 2, h, a)
+    X, Y = np.meshgrid(xs, ys)
+    m = np.full(X.size, ks * a * a / math.pi)
+    for tx, ty in [(0.0, 0.5), (3.0, -0.3), (-10.0, 0.9)]:
+        g = _geom(0.0, 0.0, ks, X.ravel(), Y.ravel(), (0.0, 0.0, h, "strip"), (-1, -1, 1, 1), (8, 8),
+                  ray_box=(tx - 0.5 * a, ty - 0.5 * a, tx + 0.5 * a, ty + 0.5 * a), ray_n=(1, 1))
+        b, _ = oracle.beta_direct(g, X.ravel(), Y.ravel(), m, np.array([0]))
+        # the strip's finite ends leave an x field of (kappa_* / pi) 2h ln((L + x)/(L - x))
+        ends = ks / math.pi * 2 * h * abs(math.log((L + tx) / (L - tx)))
+        assert abs(b[0, 0] - tx) <= 1.1 * ends + 1e-5, (b[0], tx, ends)
+        assert abs(b[0, 1] - ty) <= 0.02 * 2 * ks * abs(ty) + 1e-4, (b[0], tx, ty)
+        # without the sheet the lens strip alone deflects by about 2 kappa_* theta_y
+        g0 = _geom(0.0, 0.0, 0.0, X.ravel(), Y.ravel(), (0.0, 0.0, h, "strip"), (-1, -1, 1, 1), (8, 8),
+                   ray_box=(tx - 0.5 * a, ty - 0.5 * a, tx + 0.5 * a, ty + 0.5 * a), ray_n=(1, 1))
+        b0, _ = oracle.beta_direct(g0, X.ravel(), Y.ravel(), m, np.array([0]))
+        assert abs((ty - b0[0, 1]) - 2 * ks * ty) <= 0.02 * 2 * ks * abs(ty)
