@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-#define ML_ABI_VERSION 2
+#define ML_ABI_VERSION 3
 
 typedef enum {
     ML_OK = 0,
@@ -128,7 +128,31 @@ typedef struct {
     int32_t tune;               /* 1: pick l2_sub_x, l2_sub_y (and with them p) by the
                                    built-in cost model when both are zero */
     int32_t reserved0;
+
+    /* Macro model.  ML_MACRO_LINEAR (0): the constant-(kappa, gamma) form of
+     * Eq. 1 above.  ML_MACRO_FOLD (1): the fold near the critical curve, Eq. 5
+     * as printed in Eq. 6:
+     *   macro(theta) = (d_x theta_x^2 / 2 + d_y theta_x theta_y, 2 (1 - kappa0) theta_y),
+     * with d = -(grad kappa)_0 - (grad gamma)_0 in units of 1/theta_E
+     * (kappa and gamma are then unused).  The default ray rectangle is the
+     * bounding box of the pre-image of the protected map, which must reach
+     * beyond the caustic (images exist).  The gradients of ml_cic_backward are
+     * defined for ML_MACRO_LINEAR only. */
+    int32_t macro_mode;
+    /* Shape of the negative sheet of Eq. 6 (a uniform sheet laid where the
+     * lenses are).  ML_SHEET_DISC (0): the disc (sheet_cx, sheet_cy,
+     * sheet_radius) above.  ML_SHEET_STRIP (1): a strip unbounded in x with
+     * centre line sheet_cy and half-width sheet_radius in y, for lenses in a
+     * long rectangle; its field is -2 kappa_* (theta_y - sheet_cy) y-hat
+     * inside.  The near/far modes need every ray inside the sheet. */
+    int32_t sheet_shape;
+    double kappa0, d_x, d_y;
 } ml_field_desc;
+
+/* Macro models of ml_field_desc.macro_mode. */
+enum { ML_MACRO_LINEAR = 0, ML_MACRO_FOLD = 1 };
+/* Sheet shapes of ml_field_desc.sheet_shape. */
+enum { ML_SHEET_DISC = 0, ML_SHEET_STRIP = 1 };
 
 /* Derived parameters of a field (what §3.1-§3.2 compute from the desc). */
 typedef struct {

@@ -23,9 +23,11 @@ from . import inputs  # noqa: F401  (seeded synthetic inputs, no method arithmet
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libml.so")
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 PREC_DIRECT64, PREC_NEARFAR64, PREC_MIXED = 0, 1, 2
 DEPOSIT_NGP, DEPOSIT_CIC = 0, 1
+MACRO_LINEAR, MACRO_FOLD = 0, 1
+SHEET_DISC, SHEET_STRIP = 0, 1
 BUILD_AUTO, BUILD_DIRECT, BUILD_HIERARCHICAL = 0, 1, 2
 MAP_COUNTS_U32, MAP_MU_F32, MAP_MU_F64 = 0, 1, 2
 STAT_NAMES = ("rays_in", "rays_out", "rays_dropped", "near_pairs", "tasks", "launches",
@@ -67,6 +69,8 @@ class FieldDesc(C.Structure):
         ("l1_x", C.c_double), ("l1_y", C.c_double), ("l2_sub_x", C.c_int32),
         ("l2_sub_y", C.c_int32), ("far_tol", C.c_double), ("max_launch_rays", C.c_uint64),
         ("tune", C.c_int32), ("reserved0", C.c_int32),
+        ("macro_mode", C.c_int32), ("sheet_shape", C.c_int32),
+        ("kappa0", C.c_double), ("d_x", C.c_double), ("d_y", C.c_double),
     ]
 
 
@@ -295,7 +299,9 @@ def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_A
     d.n_lens = len(lx)
     d.lens_mem_is_device = 0
     d.taylor_p = taylor_p
-    d.sheet_cx, d.sheet_cy, d.sheet_radius = w.sheet
+    d.sheet_cx, d.sheet_cy, d.sheet_radius = w.sheet[:3]
+    if len(w.sheet) > 3 and w.sheet[3] == "strip":
+        d.sheet_shape = SHEET_STRIP
     if w.ray_box is not None:
         d.ray_x0, d.ray_y0, d.ray_x1, d.ray_y1 = w.ray_box
     if w.ray_n is not None:
@@ -309,6 +315,10 @@ def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_A
         d.l1_x, d.l1_y = l1
     d.l2_sub_x, d.l2_sub_y = l2_sub
     d.tune = 1 if tune else 0
+    macro = getattr(w, "macro", None)
+    if macro is not None:
+        d.macro_mode = MACRO_FOLD
+        d.kappa0, d.d_x, d.d_y = macro[1], macro[2], macro[3]
     d.far_tol = far_tol
     d.max_launch_rays = max_launch_rays
     d._keep = (lx, ly, lm)       # keep the arrays alive until create returns

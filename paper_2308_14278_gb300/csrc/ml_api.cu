@@ -107,9 +107,14 @@ ml_status derive_geometry(const ml_field_desc &d, const std::vector<double> &hx,
     g.kappa = d.kappa;
     g.gamma = d.gamma;
     g.kappa_star = d.kappa_star;
+    g.macro = d.macro_mode;
+    g.kappa0 = d.kappa0;
+    g.dx = d.d_x;
+    g.dy = d.d_y;
     g.sheet_cx = d.sheet_cx;
     g.sheet_cy = d.sheet_cy;
     g.sheet_r = d.sheet_radius;
+    g.sheet_shape = d.sheet_shape;
     g.precision = d.precision;
     g.deposit = d.deposit;
     g.mnx = d.map_nx;
@@ -119,7 +124,39 @@ ml_status derive_geometry(const ml_field_desc &d, const std::vector<double> &hx,
     g.dpx = (d.map_x1 - d.map_x0) / d.map_nx;
     g.dpy = (d.map_y1 - d.map_y0) / d.map_ny;
     double rx0, rx1, ry0, ry1;
-    if (d.ray_x0 == 0.0 && d.ray_y0 == 0.0 && d.ray_x1 == 0.0 && d.ray_y1 == 0.0) {
+    if (d.ray_x0 == 0.0 && d.ray_y0 == 0.0 && d.ray_x1 == 0.0 && d.ray_y1 == 0.0 &&
+        d.macro_mode == ML_MACRO_FOLD) {
+        // bounding box of the pre-image of s' under the fold map (Eq. 5):
+        // theta_y = beta_y / (2 (1 - kappa0)); for fixed theta_y and d_x > 0 the
+        // images of beta_x <= b1 lie within t* +- s1, t* = -d_y theta_y / d_x,
+        // s1 = sqrt(2 b1 / d_x + (d_y theta_y / d_x)^2); t* + s1 is convex and
+        // t* - s1 concave in theta_y, so the extremes sit at the ends of its range
+        const double w = 0.5 * (20.0 * sqrt(d.kappa_star));
+        const double a = 2.0 * (1.0 - d.kappa0);
+        double b0 = d.map_x0 - w, b1 = d.map_x1 + w, dx = d.d_x, dy = d.d_y;
+        if (dx < 0.0) {              // mirror beta_x
+            const double t = b0;
+            b0 = -b1;
+            b1 = -t;
+            dx = -dx;
+            dy = -dy;
+        }
+        (void)b0;
+        if (!(b1 > 0.0))
+            return fail(ML_ERR_INVALID_ARG, "the protected map has no images under the fold map "
+                                            "(it lies beyond the caustic)");
+        const double ty[2] = {(d.map_y0 - w) / a, (d.map_y1 + w) / a};
+        rx0 = INFINITY;
+        rx1 = -INFINITY;
+        for (double t : ty) {
+            const double c = -dy * t / dx;
+            const double s1 = sqrt(2.0 * b1 / dx + (dy * t / dx) * (dy * t / dx));
+            rx0 = std::min(rx0, c - s1);
+            rx1 = std::max(rx1, c + s1);
+        }
+        ry0 = std::min(ty[0], ty[1]);
+        ry1 = std::max(ty[0], ty[1]);
+    } else if (d.ray_x0 == 0.0 && d.ray_y0 == 0.0 && d.ray_x1 == 0.0 && d.ray_y1 == 0.0) {
         // pre-image of s' = s widened by 10 sqrt(kappa_*) per side (§3.1)
         double w = 0.5 * (20.0 * sqrt(d.kappa_star));
         double a = 1.0 - d.kappa - d.gamma, b = 1.0 - d.kappa + d.gamma;
@@ -215,11 +252,20 @@ ml_status validate(const ml_field_desc *d)
         return fail(ML_ERR_INVALID_ARG, "bad l2_sub_x / l2_sub_y");
     if (d->l1_x < 0.0 || d->l1_y < 0.0) return fail(ML_ERR_INVALID_ARG, "negative l1 size");
     if (d->far_tol < 0.0) return fail(ML_ERR_INVALID_ARG, "negative far_tol");
+    if (d->macro_mode != ML_MACRO_LINEAR && d->macro_mode != ML_MACRO_FOLD)
+        return fail(ML_ERR_INVALID_ARG, "unknown macro_mode");
+    if (d->sheet_shape != ML_SHEET_DISC && d->sheet_shape != ML_SHEET_STRIP)
+        return fail(ML_ERR_INVALID_ARG, "unknown sheet_shape");
+    if (d->macro_mode == ML_MACRO_FOLD &&
+        (!is_fin(d->kappa0) || !is_fin(d->d_x) || !is_fin(d->d_y) || d->kappa0 == 1.0 || d->d_x == 0.0))
+        return fail(ML_ERR_INVALID_ARG, "fold macro needs finite kappa0 != 1 and d_x != 0");
     return ML_OK;
 }
 
 bool rays_inside_sheet(const Geo &g)
 {
+    if (g.sheet_shape == ML_SHEET_STRIP)
+        return g.ry0 - g.sheet_cy >= -g.sheet_r && g.ry1 - g.sheet_cy <= g.sheet_r;
     double R2 = g.sheet_r * g.sheet_r;
     double xs[2] = {g.rx0 - g.sheet_cx, g.rx1 - g.sheet_cx};
     double ys[2] = {g.ry0 - g.sheet_cy, g.ry1 - g.sheet_cy};
@@ -395,6 +441,7 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
                 if (w <= tol) { p = q; break; }
             }
         }
+        if (d.macro_mode == ML_MACRO_FOLD) p = std::max(p, 2);
         res.push_back(TuneCand{c.sx, c.sy, mixed_p_supported(p), (double)c.g.N2x * (double)c.g.N2y,
                                (double)c.g.n3x * (double)c.g.n3y, near_per_ray});
     }
@@ -594,6 +641,8 @@ int planned_order(const ml_field *f)
         for (int q = 1; q <= PMAX; ++q)
             if (f->worst[q - 1] <= tol) { p = q; break; }
     }
+    // the fold's macro term is quadratic in theta_x: the row polynomials need degree 2
+    if (d->macro_mode == ML_MACRO_FOLD && d->precision != ML_PREC_DIRECT64) p = std::max(p, 2);
     if (d->precision == ML_PREC_MIXED) p = mixed_p_supported(p);
     return p;
 }
@@ -682,8 +731,10 @@ ShootArgs make_args(const ml_field *f)
     }
     a.ipx_f = (float)(1.0 / g.dpx);
     a.ipy_f = (float)(1.0 / g.dpy);
-    a.Ax_f = (float)((1.0 - g.kappa - g.gamma + g.kappa_star) / g.dpx);
-    a.rho_y = (1.0 - g.kappa + g.gamma + g.kappa_star) * g.l3y / g.dpy;
+    const bool fold = g.macro == ML_MACRO_FOLD;
+    a.cxy_f = fold ? (float)(g.dy * g.l3y / g.dpx) : 0.f;
+    a.q2_f = fold ? (float)(0.5 * g.dx / g.dpx) : 0.f;
+    a.rho_y = ((fold ? 2.0 * (1.0 - g.kappa0) : 1.0 - g.kappa + g.gamma) + sheet_ky(g)) * g.l3y / g.dpy;
     return a;
 }
 
@@ -1282,6 +1333,9 @@ ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens,
         return fail(ML_ERR_INVALID_ARG, "unknown adjoint method");
     if (f->g.deposit != ML_DEPOSIT_CIC || f->g.precision != ML_PREC_MIXED)
         return fail(ML_ERR_STATE, "the adjoint needs a field with ML_DEPOSIT_CIC and ML_PREC_MIXED");
+    if (f->g.macro != ML_MACRO_LINEAR || f->g.sheet_shape != ML_SHEET_DISC)
+        return fail(ML_ERR_UNSUPPORTED, "the adjoint's parameter terms are those of the "
+                                        "constant-(kappa, gamma) macro model with a disc sheet");
     cudaStream_t s = (cudaStream_t)stream;
     const Geo &g = f->g;
     const int64_t n = std::max<int64_t>(f->n_lens, 0);

@@ -284,18 +284,26 @@ __global__ void k_node_finalize(Geo g, const double *__restrict__ coef, unsigned
     double zx = g.rx0 + ((double)c2x + 0.5) * g.l2x;
     double zy = g.ry0 + ((double)c2y + 0.5) * g.l2y;
     const double *c = coef + node * (int64_t)(g.p + 1) * 2;
-    // beta = M theta + kappa_* (theta - c_sheet) - conj(F), F(z_node) = c_0
-    double bx = (1.0 - g.kappa - g.gamma) * zx + g.kappa_star * (zx - g.sheet_cx) - c[0];
-    double by = (1.0 - g.kappa + g.gamma) * zy + g.kappa_star * (zy - g.sheet_cy) + c[1];
+    // beta = macro(theta) + kappa_* (theta - c_sheet) - conj(F), F(z_node) = c_0
+    double mx, my;
+    macro64(g, zx, zy, mx, my);
+    double bx = mx + sheet_kx(g) * (zx - g.sheet_cx) - c[0];
+    double by = my + sheet_ky(g) * (zy - g.sheet_cy) + c[1];
     double Sx = (bx - g.mx0) / g.dpx;
     double Sy = (by - g.my0) / g.dpy;
     double fbx = floor(Sx);
     fbx = fmin(fmax(fbx, -16777216.0), 16777216.0);
+    // slope of the macro and sheet terms in theta_x at the node, and the
+    // per-row shift of beta_x (fold: d_x z_x + d_y z_y and d_y z_x l3y)
+    const double ax = g.macro == ML_MACRO_FOLD ? g.dx * zx + g.dy * zy : 1.0 - g.kappa - g.gamma;
+    const double bq = g.macro == ML_MACRO_FOLD ? g.dy * zx * g.l3y : 0.0;
     unsigned char *rec = out + node * node_stride(g.p);
     *reinterpret_cast<double *>(rec) = Sy;
     *reinterpret_cast<int *>(rec + 8) = (int)fbx;
     *reinterpret_cast<float *>(rec + 12) = (float)(Sx - fbx);
-    float2 *cf = reinterpret_cast<float2 *>(rec + 16);
+    *reinterpret_cast<float *>(rec + 16) = (float)((ax + sheet_kx(g)) / g.dpx);
+    *reinterpret_cast<float *>(rec + 20) = (float)(bq / g.dpx);
+    float2 *cf = reinterpret_cast<float2 *>(rec + 24);
     for (int q = 1; q <= g.p; ++q) cf[q - 1] = make_float2((float)c[2 * q], (float)c[2 * q + 1]);
 }
 

@@ -18,7 +18,10 @@ constexpr int WARPS_PER_CTA = 8;
 // Parameters derived from an ml_field_desc (§3.1 and §3.2).
 struct Geo {
     double kappa, gamma, kappa_star;
+    int32_t macro;                  // ML_MACRO_LINEAR or ML_MACRO_FOLD
+    double kappa0, dx, dy;          // fold parameters (Eq. 5)
     double sheet_cx, sheet_cy, sheet_r;
+    int32_t sheet_shape;            // ML_SHEET_DISC or ML_SHEET_STRIP
     double rx0, ry0, rx1, ry1;      // ray rectangle
     double l3x, l3y;                // level-3 pixel (ray spacing)
     int64_t n3x, n3y;               // lattice size
@@ -43,12 +46,14 @@ struct LensTable {
     int64_t n;
 };
 
-// Per-node record of the mixed-precision path, stride 16 + 8p bytes:
-//   double Sy;  int32 bx;  float fx;  float2 c[p]
+// Per-node record of the mixed-precision path, stride 24 + 8p bytes:
+//   double Sy;  int32 bx;  float fx;  float ax;  float bq;  float2 c[p]
 // (Sy, bx + fx) is the smooth part of beta at the node in map pixel units
-// (macro model, sheet and far-field c_0); c[n-1] is the FP32 far-field
-// Taylor coefficient c_n, n = 1..p, in theta_E units.
-__host__ __device__ inline size_t node_stride(int p) { return 16 + 8 * (size_t)p; }
+// (macro model, sheet and far-field c_0); ax is d(beta_x)/d(theta_x) of the
+// macro and sheet terms at the node in pixels per theta_E; bq is the change
+// of beta_x per ray row (pixels; the fold's d_y theta_x term, else 0); c[n-1]
+// is the FP32 far-field Taylor coefficient c_n, n = 1..p, in theta_E units.
+__host__ __device__ inline size_t node_stride(int p) { return 24 + 8 * (size_t)p; }
 
 // Everything a shooting or tracing kernel needs.
 struct ShootArgs {
@@ -69,9 +74,11 @@ struct ShootArgs {
     int64_t n_tasks;
     int near_cap;                   // float4 slots of shared memory per warp
     // float constants of the mixed kernel
-    float l3x_f, l3x_lo, c0_f, ipx_f, ipy_f, Ax_f;  // Ax_f = (1-kappa-gamma+kappa_*)/dpx
+    float l3x_f, l3x_lo, c0_f, ipx_f, ipy_f;
+    float cxy_f;                    // d(beta_x)/d(theta_x) change per ray row (fold: d_y l3y / dpx)
+    float q2_f;                     // beta_x curvature in theta_x (fold: d_x / (2 dpx)), else 0
     float rc2;                      // close-pass radius^2 of near_sum_f32
-    double rho_y;                   // (1-kappa+gamma+kappa_*) * l3y / dpy
+    double rho_y;                   // (d(macro_y)/d(theta_y) + kappa_*) * l3y / dpy
 };
 
 // Many maps in one persistent launch: per-map arguments (device array) and
@@ -135,6 +142,24 @@ int mixed_p_supported(int p);     // the Taylor order the mixed kernel will use 
 // ---- shared device arithmetic ---------------------------------------------
 
 #if defined(__CUDACC__)
+
+// Inside the sheet, beta gains kappa_* (theta - c) (disc) or
+// 2 kappa_* (theta_y - c_y) y-hat (strip): the linear coefficients.
+__host__ __device__ inline double sheet_kx(const Geo &g) { return g.sheet_shape == ML_SHEET_STRIP ? 0.0 : g.kappa_star; }
+__host__ __device__ inline double sheet_ky(const Geo &g) { return g.sheet_shape == ML_SHEET_STRIP ? 2.0 * g.kappa_star : g.kappa_star; }
+
+// The smooth (macro) part of beta in FP64: the constant-(kappa, gamma) form
+// of Eq. 1, or the fold of Eq. 5 as printed in Eq. 6.
+__host__ __device__ inline void macro64(const Geo &g, double tx, double ty, double &mx, double &my)
+{
+    if (g.macro == ML_MACRO_FOLD) {
+        mx = 0.5 * g.dx * tx * tx + g.dy * tx * ty;
+        my = 2.0 * (1.0 - g.kappa0) * ty;
+    } else {
+        mx = (1.0 - g.kappa - g.gamma) * tx;
+        my = (1.0 - g.kappa + g.gamma) * ty;
+    }
+}
 
 // Near-lens records: rec(k) = (x_k - x_node, y_k - y_ref, m_k, -) rounded to
 // FP32, lo(k) = the rounding remainders of the two offsets.  Deflection of the near lenses (the directly summed part of
@@ -260,7 +285,9 @@ __device__ __forceinline__ void row_setup(const unsigned char *rec, float q, con
     const double Sy = *reinterpret_cast<const double *>(rec);
     const int bx0 = *reinterpret_cast<const int *>(rec + 8);
     const float fx = *reinterpret_cast<const float *>(rec + 12);
-    const float2 *c = reinterpret_cast<const float2 *>(rec + 16);
+    const float axn = *reinterpret_cast<const float *>(rec + 16);
+    const float bqn = *reinterpret_cast<const float *>(rec + 20);
+    const float2 *c = reinterpret_cast<const float2 *>(rec + 24);
     const float s = __fmul_rn(q, (float)a.g.l3y);
     float br[P + 1], bi[P + 1];
     br[0] = 0.f;
@@ -287,9 +314,12 @@ __device__ __forceinline__ void row_setup(const unsigned char *rec, float q, con
         rp.X[m] = __fmul_rn(-br[m], a.ipx_f);
         rp.Y[m] = __fmul_rn(bi[m], a.ipy_f);
     }
-    rp.X[1] = __fadd_rn(rp.X[1], a.Ax_f);
+    // macro and sheet terms: slope at the node plus its change per row, the
+    // fold's curvature, and the fold's per-row shift of beta_x
+    rp.X[1] = __fadd_rn(rp.X[1], __fmaf_rn(a.cxy_f, q, axn));
+    if constexpr (P >= 2) rp.X[2] = __fadd_rn(rp.X[2], a.q2_f);
     // x base: fx in [0, 1) plus the far-field offset of this row
-    float x0 = __fadd_rn(fx, rp.X[0]);
+    float x0 = __fadd_rn(__fmaf_rn(bqn, q, fx), rp.X[0]);
     float kx = floorf(x0);
     rp.X[0] = __fsub_rn(x0, kx);
     rp.bx = bx0 + (int)kx;

@@ -30,6 +30,13 @@ namespace ml {
 
 __device__ __forceinline__ void sheet64(const Geo &g, double tx, double ty, double &sx, double &sy)
 {
+    if (g.sheet_shape == ML_SHEET_STRIP) {
+        // unbounded slab of half-width R: -2 kappa_* (theta_y - c_y) inside, constant outside
+        const double v = fmin(fmax(ty - g.sheet_cy, -g.sheet_r), g.sheet_r);
+        sx = 0.0;
+        sy = -2.0 * g.kappa_star * v;
+        return;
+    }
     // deflection of the negative sheet (Eq. 6): -kappa_* u inside the disc,
     // -kappa_* R^2 u / |u|^2 outside
     double ux = tx - g.sheet_cx, uy = ty - g.sheet_cy;
@@ -58,8 +65,10 @@ __device__ bool beta_direct64(const ShootArgs &a, int64_t i, int64_t j, double &
     }
     double sx, sy;
     sheet64(g, tx, ty, sx, sy);
-    bx = (1.0 - g.kappa - g.gamma) * tx - ax - sx;
-    by = (1.0 - g.kappa + g.gamma) * ty - ay - sy;
+    double mx, my;
+    macro64(g, tx, ty, mx, my);
+    bx = mx - ax - sx;
+    by = my - ay - sy;
     return !hit;
 }
 
@@ -98,8 +107,10 @@ __device__ bool beta_nearfar64(const ShootArgs &a, int64_t i, int64_t j, double 
     }
     double sx, sy;
     sheet64(g, tx, ty, sx, sy);
-    bx = (1.0 - g.kappa - g.gamma) * tx - ax - Fr - sx;   // alpha_far = conj(F)
-    by = (1.0 - g.kappa + g.gamma) * ty - ay + Fi - sy;
+    double mx, my;
+    macro64(g, tx, ty, mx, my);
+    bx = mx - ax - Fr - sx;   // alpha_far = conj(F)
+    by = my - ay + Fi - sy;
     return !hit;
 }
 

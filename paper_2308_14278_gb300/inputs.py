@@ -195,6 +195,42 @@ def differentiable_field(seed: int = 0, n_lens: int = 1000, n_rays: float = 4e8,
                     (map_px, map_px), n_av=n_rays / (map_px * map_px), l1=(12.0, 12.0))
 
 
+# Table 1 (§4.1): the fold field of MACS J1149.5+2223, theta_E = 1e-6 arcsec.
+TABLE1_KAPPA0 = 0.83
+TABLE1_D_PER_ARCMIN = (3.62, -3.41)
+TABLE1_THETA_E_ARCSEC = 1e-6
+TABLE1_KAPPA_STAR = 0.001
+TABLE1_N_STAR = 13745
+# Image-plane rectangle of the 40 x 200 theta_E^2 source region of §4.1 widened
+# by the protection band, under the fold map (rounded outward): holds 13,839
+# lenses at kappa_* = 0.001 by N_* = L_ix L_iy kappa_* / pi (Table 1: 13,745).
+TABLE1_LENS_RECT = (-36560.0, -1.0, 37120.0, 589.2)
+
+
+def fold_field(seed: int = 0, n_rays: float = 1e11, map_px=(2048, 10240),
+               n_tracks: int = 10) -> Workload:
+    """The Table-1 fold field at reduced resolution: kappa_0 = 0.83,
+    d = (3.62, -3.41) arcmin^-1 in units of 1/theta_E, kappa_* = 0.001,
+    13,745 unit-mass lenses uniform in the image-plane rectangle, the sheet a
+    strip over the same y range (the rectangle is 125 times longer than it is
+    wide, so its field is a slab's); the source region
+    beta_x in [0, 40], beta_y in [0, 200] (the 200 x 40 theta_E^2 of §4.1) on
+    map_px pixels, n_rays rays."""
+    arcmin_in_theta_e = 60.0 / TABLE1_THETA_E_ARCSEC
+    dx = TABLE1_D_PER_ARCMIN[0] / arcmin_in_theta_e
+    dy = TABLE1_D_PER_ARCMIN[1] / arcmin_in_theta_e
+    x0, y0, x1, y1 = TABLE1_LENS_RECT
+    u = uniform01(seed, 31, TABLE1_N_STAR)
+    v = uniform01(seed, 32, TABLE1_N_STAR)
+    lf = LensField(x0 + (x1 - x0) * u, y0 + (y1 - y0) * v, np.ones(TABLE1_N_STAR),
+                   0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.0)
+    nx, ny = map_px
+    return Workload(f"fold field (Table 1): {TABLE1_N_STAR} lenses, {n_rays:.0e} rays, {nx}x{ny} map",
+                    lf, 0.0, 0.0, TABLE1_KAPPA_STAR, (0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * (y1 - y0), "strip"),
+                    (0.0, 0.0, 40.0, 200.0), (nx, ny), n_av=n_rays / (nx * ny),
+                    n_tracks=n_tracks, macro=("fold", TABLE1_KAPPA0, dx, dy))
+
+
 def batched_maps(n_maps: int = 80, seed: int = 0, map_px: int = 4096,
                  ray_range=(1e9, 1e10), tracks_per_map: int = 10):
     """Heterogeneous maps: N ~ U{2000..20000}, kappa_* in {0.002, 0.005, 0.01},
