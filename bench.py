@@ -277,6 +277,7 @@ def run_ours(args, rank, world, local):
                    "macro": "fold (Eq. 5)" if getattr(w, "macro", None) else "constant kappa, gamma (Eq. 1)",
                    "taylor_p": p, "far_bound_theta_e": info["far_bound"],
                    "l2_sub": [info["l2_sub_x"], info["l2_sub_y"]], "tuned_grid": bool(info["tuned"]),
+                   "l1_theta_e": [info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]],
                    "coefficient_build": {1: "direct", 2: "hierarchical"}.get(info["build"]),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": (f"one map sharded over {world} GPUs (level-1 bands, integer "
@@ -351,8 +352,9 @@ def parity_stripe(ml, w, stream, tune=False):
     alone, with the benchmark's level-2 grid."""
     import oracle
     f = ml.Field(w, precision=ml.PREC_MIXED, tune=tune)
-    g = oracle.geometry_of(w, p=f.info["taylor_p"], l2_sub=f.info["l2_sub_x"],
-                           l2_sub_y=f.info["l2_sub_y"])
+    info = f.info
+    g = oracle.geometry_of(w, p=info["taylor_p"], l2_sub=info["l2_sub_x"], l2_sub_y=info["l2_sub_y"],
+                           l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]))
     r0 = (g.n3y // 2) * g.n3x + 777
     r1 = r0 + 1_000_000
     f.shoot(r0, r1)

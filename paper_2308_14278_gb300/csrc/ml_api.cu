@@ -275,14 +275,17 @@ bool rays_inside_sheet(const Geo &g)
     return true;
 }
 
-// ---- level-2 grid autotuner --------------------------------------------------
+// ---- level-1/level-2 grid autotuner ---------------------------------------------
 //
-// The paper fixes L2 = L1 / 20.  A finer level-2 grid along the long side of
-// the level-1 cells shrinks the expansion radius, so a lower Taylor order meets
-// the same truncation bound, at the price of more nodes to build.  The tuner
-// evaluates a few (l2_sub_x, l2_sub_y) candidates with their rigorous bound
-// (one p_bound launch each) and a cost model of GB300 measurements:
-//   time = rays * ray_cost(P) + nodes * (P + 1) * node_cost,
+// The paper fixes L1 by Eq. 10 and L2 = L1 / 20.  A finer level-2 grid along
+// the long side of the level-1 cells shrinks the expansion radius, so a lower
+// Taylor order meets the same truncation bound, at the price of more nodes to
+// build; smaller level-1 cells shorten the near lists, at the price of more
+// cells and nodes.  The tuner evaluates level-1 scales (1, 1/sqrt 2, 1/2 of
+// Eq. 10's size, unless the caller fixed L1) times (l2_sub_x, l2_sub_y)
+// candidates with their rigorous bound (one p_bound launch each) and their
+// mean near-list length, and ranks them by a cost model of GB300 measurements:
+//   time = rays * ray_cost(P, near) + nodes * (P + 1) * node_cost,
 // the field's build plus one shot of all its rays.
 
 // Shooting time per ray of the mixed kernel on the whole GB300, in
@@ -300,13 +303,18 @@ constexpr double kCostPs[3][10] = {
     {2.11, 2.18, 2.26, 2.39, 2.50, 2.62, 3.25, 3.72, 4.02, 4.79},
 };
 
+// Beyond the measured near counts each further near lens adds about this
+// much per ray (the Table-1 fold field: 9 near lenses, 3.8 ps per ray at P = 4).
+constexpr double kCostPairPs = 0.25;
+
 double ray_cost_ps(int P, double near_per_ray)
 {
     int q = 9;
     for (int i = 0; i < 10; ++i)
         if (kCostOrders[i] >= P) { q = i; break; }
     if (near_per_ray <= kCostNear[0]) return kCostPs[0][q];
-    if (near_per_ray >= kCostNear[2]) return kCostPs[2][q];
+    if (near_per_ray >= kCostNear[2])
+        return kCostPs[2][q] + (near_per_ray - kCostNear[2]) * kCostPairPs;
     const int r = near_per_ray < kCostNear[1] ? 0 : 1;
     const double f = (near_per_ray - kCostNear[r]) / (kCostNear[r + 1] - kCostNear[r]);
     return (1.0 - f) * kCostPs[r][q] + f * kCostPs[r + 1][q];
@@ -318,6 +326,7 @@ constexpr double kNodeCostNs = 1.3;
 
 struct GridChoice {
     int sx = 20, sy = 20, p = 0;
+    double l1x = 0.0, l1y = 0.0;    // level-1 size; 0 = Eq. 10's
     double cost = 0.0;
 };
 
@@ -326,7 +335,8 @@ struct GridChoice {
 struct TuneCand {
     int sx, sy, P;
     double nodes, rays;
-    double near_per_ray;            // mean near-list length (level 1 is the same for all candidates)
+    double near_per_ray;            // mean near-list length over the level-1 cells
+    double l1x, l1y;                // level-1 size; 0 = Eq. 10's
 };
 
 double cand_cost(const TuneCand &c, int P)
@@ -379,17 +389,25 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
     const bool xlong = g0.l1x >= g0.l1y;
     static const int fine[] = {20, 40, 60, 80};
     static const int coarse[] = {10, 20};
-    struct Cand { int sx, sy; Geo g; int32_t *cells; int32_t *counts; double *bound; };
+    // level-1 scales: Eq. 10's size unless the caller fixed it
+    std::vector<double> scales{1.0};
+    if (d.l1_x == 0.0 && d.l1_y == 0.0) { scales.push_back(0.70710678118654752); scales.push_back(0.5); }
+    struct Cand { int sx, sy; double l1x, l1y; Geo g; int32_t *cells; int32_t *counts; double *bound; };
     std::vector<Cand> cands;
     cudaError_t e = cudaSuccess;
+    for (double sc : scales)
     for (int a : fine)
         for (int b : coarse) {
             Cand c{};
             c.sx = xlong ? a : b;
             c.sy = xlong ? b : a;
+            c.l1x = sc == 1.0 ? d.l1_x : sc * g0.l1x;
+            c.l1y = sc == 1.0 ? d.l1_y : sc * g0.l1y;
             ml_field_desc dc = d;
             dc.l2_sub_x = c.sx;
             dc.l2_sub_y = c.sy;
+            dc.l1_x = c.l1x;
+            dc.l1_y = c.l1y;
             if (derive_geometry(dc, hx, hy, c.g) != ML_OK) continue;
             if (c.g.n2x < 2 || c.g.n2y < 1 || c.g.N2x * c.g.N2y > ((int64_t)1 << 26)) continue;
             if (c.g.NEx * c.g.NEy >= ((int64_t)1 << 30)) continue;
@@ -411,27 +429,24 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
         }
     const double tol = d.far_tol > 0.0 ? d.far_tol : 1e-7;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    // mean near-list length over the level-1 cells (3 x 3 block counts of the
-    // binned lenses; cells of the lattice weigh alike)
-    double near_per_ray = 0.0;
-    if (e == cudaSuccess && !cands.empty()) {
-        const Geo &gc = cands[0].g;
-        std::vector<int32_t> cnt((size_t)(gc.NEx * gc.NEy + 1));
-        e = cudaMemcpy(cnt.data(), cands[0].counts, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
-        double tot = 0.0;
-        for (int64_t cy = 0; cy < gc.N1y && e == cudaSuccess; ++cy)
-            for (int64_t cx = 0; cx < gc.N1x; ++cx)
-                for (int64_t dy = 0; dy < 3; ++dy)
-                    for (int64_t dxx = 0; dxx < 3; ++dxx)
-                        tot += cnt[(size_t)((cy + dy) * gc.NEx + cx + dxx)];
-        near_per_ray = tot / (double)std::max<int64_t>(1, gc.N1x * gc.N1y);
-    }
     std::vector<TuneCand> res;
     for (Cand &c : cands) {
         if (e != cudaSuccess) break;
         std::vector<double> bound((size_t)(c.g.N1x * c.g.N1y * PMAX));
         e = cudaMemcpy(bound.data(), c.bound, bound.size() * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) break;
+        // mean near-list length over the level-1 cells (3 x 3 block counts of
+        // the binned lenses; cells of the lattice weigh alike)
+        std::vector<int32_t> cnt((size_t)(c.g.NEx * c.g.NEy + 1));
+        e = cudaMemcpy(cnt.data(), c.counts, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) break;
+        double tot = 0.0;
+        for (int64_t cy = 0; cy < c.g.N1y; ++cy)
+            for (int64_t cx = 0; cx < c.g.N1x; ++cx)
+                for (int64_t dy = 0; dy < 3; ++dy)
+                    for (int64_t dxx = 0; dxx < 3; ++dxx)
+                        tot += cnt[(size_t)((cy + dy) * c.g.NEx + cx + dxx)];
+        const double near_per_ray = tot / (double)std::max<int64_t>(1, c.g.N1x * c.g.N1y);
         int p = d.taylor_p;
         if (p == 0) {
             p = PMAX;
@@ -443,7 +458,7 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
         }
         if (d.macro_mode == ML_MACRO_FOLD) p = std::max(p, 2);
         res.push_back(TuneCand{c.sx, c.sy, mixed_p_supported(p), (double)c.g.N2x * (double)c.g.N2y,
-                               (double)c.g.n3x * (double)c.g.n3y, near_per_ray});
+                               (double)c.g.n3x * (double)c.g.n3y, near_per_ray, c.l1x, c.l1y});
     }
     for (Cand &c : cands) {
         if (c.cells) cudaFreeAsync(c.cells, s);
@@ -466,6 +481,7 @@ GridChoice best_single(const std::vector<TuneCand> &cands)
         double cost = cand_cost(c, c.P);
         if (!found || cost < best.cost) {
             best.sx = c.sx; best.sy = c.sy; best.p = c.P; best.cost = cost;
+            best.l1x = c.l1x; best.l1y = c.l1y;
             found = true;
         }
     }
@@ -548,6 +564,8 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
         if (st != ML_OK) return st;
         d->l2_sub_x = gc.sx;
         d->l2_sub_y = gc.sy;
+        d->l1_x = gc.l1x;
+        d->l1_y = gc.l1y;
         f->tuned = 1;
     }
     ml_status st = derive_geometry(*d, hx, hy, f->g);
@@ -901,6 +919,8 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
         if (best.p > 0) {
             plan[i].l2_sub_x = best.sx;
             plan[i].l2_sub_y = best.sy;
+            plan[i].l1_x = best.l1x;
+            plan[i].l1_y = best.l1y;
             tuned[i] = 1;
         }
     }

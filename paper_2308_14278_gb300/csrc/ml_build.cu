@@ -334,6 +334,20 @@ cudaError_t launch_node_finalize(const Geo &g, const double *coef64, unsigned ch
 constexpr int HP = 32;               // order of the box and sub-block series
 constexpr int HPARTS = 16;           // lens partitions per box (partial sums)
 
+// Binomial coefficients C(n, k), n, k <= HP (exact in FP64), built once at
+// compile time by Pascal's rule.
+struct BinomTable {
+    double v[(HP + 1) * (HP + 1)];
+    constexpr BinomTable() : v()
+    {
+        for (int n = 0; n <= HP; ++n)
+            for (int k = 0; k <= HP; ++k)
+                v[n * (HP + 1) + k] = k > n ? 0.0 : (k == 0 || k == n ? 1.0
+                                                    : v[(n - 1) * (HP + 1) + k - 1] + v[(n - 1) * (HP + 1) + k]);
+    }
+};
+__constant__ BinomTable c_binom = BinomTable();
+
 struct Hier {
     int64_t bxn, byn;                // level-1 cells per box side
     int64_t NBx, NBy;                // boxes across the level-1 grid
@@ -487,13 +501,7 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
         A[2 * j] = vr;
         A[2 * j + 1] = vi;
     }
-    for (int t = threadIdx.x; t < (HP + 1) * (HP + 1); t += blockDim.x) {
-        int n = t / (HP + 1), kk = t % (HP + 1);
-        double c = 1.0;                        // C(n, kk), exact in FP64 for n <= 32
-        if (kk > n) c = 0.0;
-        else for (int q = 1; q <= kk; ++q) c = c * (double)(n - kk + q) / (double)q;
-        binom[t] = c;
-    }
+    for (int t = threadIdx.x; t < (HP + 1) * (HP + 1); t += blockDim.x) binom[t] = c_binom.v[t];
     __syncthreads();
     block_sum_store(ar, ai, sub + s * (HP + 1) * 2, red);
     __syncthreads();
@@ -521,15 +529,8 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
 __global__ void __launch_bounds__(128) k_node_shift(Geo g, Hier h, const double *__restrict__ sub,
                                                    double *__restrict__ coef)
 {
-    __shared__ double binom[(HP + 1) * (HP + 1)];
-    for (int t = threadIdx.x; t < (HP + 1) * (HP + 1); t += blockDim.x) {
-        int n = t / (HP + 1), kk = t % (HP + 1);
-        double c = 1.0;
-        if (kk > n) c = 0.0;
-        else for (int q = 1; q <= kk; ++q) c = c * (double)(n - kk + q) / (double)q;
-        binom[t] = c;
-    }
-    __syncthreads();
+    // node-uniform loop indices: the binomials come from the constant cache
+    const double *binom = c_binom.v;
     int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (node >= g.N2x * g.N2y) return;
     int64_t c2x = node % g.N2x, c2y = node / g.N2x;
@@ -546,18 +547,37 @@ __global__ void __launch_bounds__(128) k_node_shift(Geo g, Hier h, const double 
     const int64_t s = (cy * g.N1x + cx) * h.nsx * h.nsy + sbb * h.nsx + sa;
     const double *a = sub + s * (HP + 1) * 2;
     double *out = coef + node * (int64_t)(g.p + 1) * 2;
+    // The mixed mode keeps c_1..c_p in FP32 (node records), so they are summed
+    // in FP32 there: the shifted series decays (ratio < 0.6), no term cancels
+    // far below the sum.  c_0, the node's far deflection, stays FP64; the FP64
+    // near/far mode takes every order in FP64.
+    const bool fp32_tail = g.precision == ML_PREC_MIXED;
     double hn = 1.0;
     for (int n = 0; n <= g.p; ++n) {
-        double vr = 0.0, vi = 0.0;
-        for (int j = HP; j >= n; --j) {
-            double c = binom[j * (HP + 1) + n];
-            double nr = vr * er - vi * ei + c * a[2 * j];
-            double ni = vr * ei + vi * er + c * a[2 * j + 1];
-            vr = nr;
-            vi = ni;
+        if (n > 0 && fp32_tail) {
+            const float erf = (float)er, eif = (float)ei;
+            float vr = 0.f, vi = 0.f;
+            for (int j = HP; j >= n; --j) {
+                const float c = (float)binom[j * (HP + 1) + n];
+                const float nr = __fmaf_rn(vr, erf, __fmaf_rn(-vi, eif, c * (float)a[2 * j]));
+                const float ni = __fmaf_rn(vr, eif, __fmaf_rn(vi, erf, c * (float)a[2 * j + 1]));
+                vr = nr;
+                vi = ni;
+            }
+            out[2 * n] = (double)vr / hn;
+            out[2 * n + 1] = (double)vi / hn;
+        } else {
+            double vr = 0.0, vi = 0.0;
+            for (int j = HP; j >= n; --j) {
+                double c = binom[j * (HP + 1) + n];
+                double nr = vr * er - vi * ei + c * a[2 * j];
+                double ni = vr * ei + vi * er + c * a[2 * j + 1];
+                vr = nr;
+                vi = ni;
+            }
+            out[2 * n] = vr / hn;
+            out[2 * n + 1] = vi / hn;
         }
-        out[2 * n] = vr / hn;
-        out[2 * n + 1] = vi / hn;
         hn *= hs;
     }
 }

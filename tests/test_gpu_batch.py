@@ -59,7 +59,8 @@ def test_tuned_batch_groups_orders_and_matches_single_maps(ml):
         info = b.info(i)
         assert info["tuned"] == 1 and info["far_bound"] <= 1e-7
         f = ml.Field(w, precision=ml.PREC_MIXED, taylor_p=info["taylor_p"],
-                     l2_sub=(info["l2_sub_x"], info["l2_sub_y"]))
+                     l2_sub=(info["l2_sub_x"], info["l2_sub_y"]),
+                     l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]))
         f.shoot()
         assert np.array_equal(b.counts(i).cpu().numpy(), f.counts().cpu().numpy()), i
         f.close()
@@ -109,7 +110,8 @@ def test_tuned_field_meets_bound_and_matches_oracle(ml):
     assert info["tuned"] == 1
     assert info["far_bound"] <= 1e-7
     g = oracle.geometry_of(w, p=info["taylor_p"], l2_sub=info["l2_sub_x"],
-                           l2_sub_y=info["l2_sub_y"])
+                           l2_sub_y=info["l2_sub_y"],
+                           l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]))
     assert (info["n1x"], info["n2x"], info["n1y"], info["n2y"]) == (g.n1x, g.n2x, g.n1y, g.n2y)
     idx = np.unique(np.random.default_rng(5).integers(0, g.n_rays, 10000))
     beta, _ = f.trace(idx)
@@ -121,6 +123,7 @@ def test_tuned_field_meets_bound_and_matches_oracle(ml):
     assert rel.max() <= 1e-5
     # a second identical field reuses the tuner's decision
     f2 = ml.Field(w, precision=ml.PREC_MIXED, tune=True)
-    assert (f2.info["l2_sub_x"], f2.info["l2_sub_y"]) == (info["l2_sub_x"], info["l2_sub_y"])
+    assert (f2.info["l2_sub_x"], f2.info["l2_sub_y"], f2.info["n1x"], f2.info["n1y"]) == \
+        (info["l2_sub_x"], info["l2_sub_y"], info["n1x"], info["n1y"])
     f.close()
     f2.close()

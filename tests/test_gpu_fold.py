@@ -31,7 +31,8 @@ def _fold_case(seed=3, ks=0.1, box=(0.5, -2.0, 6.5, 2.0), n=(64, 48), n_av=120.0
 def _geom(w, f):
     info = f.info
     return oracle.geometry_of(w, p=max(1, info["taylor_p"]), l2_sub=info["l2_sub_x"],
-                              l2_sub_y=info["l2_sub_y"])
+                              l2_sub_y=info["l2_sub_y"],
+                              l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]))
 
 
 def test_fold_geometry_matches_oracle(ml):
