@@ -522,3 +522,40 @@ def cic_grad(g: Geometry, x, y, m, target, ray_begin=0, ray_end=None, threads=No
     if rc != 0:
         raise ValueError("the oracle's CIC gradient covers the constant-(kappa, gamma) macro only")
     return gl, gp
+
+
+# ---------------------------------------------------------------------------
+# Peak identification on light curves (§4.2)
+# ---------------------------------------------------------------------------
+
+def peaks(counts, along: str = "x", nsigma: float = 5.0):
+    """The two-step peak identification of §4.2 on a count map (ny x nx).
+
+    Light curves run along `along` ("x": each map row is a curve and the
+    neighbouring curves are the rows above and below; "y": each column).
+    Step 1, candidate at position j of curve i: N_ij > max(N_i,j-1, N_i,j+1)
+    and h_ij = N_ij - <N> > nsigma sigma_ij, <N> = (N_i,j-1 + N_ij + N_i,j+1)/3,
+    sigma_ij = sqrt(<N>).  Squared (both sides positive), with a, b the two
+    neighbours: (2 N - a - b)^2 > 3 nsigma^2 (a + N + b), compared in FP64.
+    Positions at the ends of a curve have no candidate.
+    Step 2, a candidate is a true peak when one of positions j-1, j, j+1 of
+    curve i-1 and one of curve i+1 are candidates; the first and last curves
+    have no true peaks.
+    Returns the uint8 mask: bit 0 candidate, bit 1 true peak."""
+    N = np.asarray(counts)
+    if along == "y":
+        return peaks(N.T, "x", nsigma).T.copy()
+    ny, nx = N.shape
+    mask = np.zeros((ny, nx), np.uint8)
+    k2x3 = 3.0 * nsigma * nsigma
+    for i in range(ny):
+        for j in range(1, nx - 1):
+            a, c, b = int(N[i, j - 1]), int(N[i, j]), int(N[i, j + 1])
+            if c > a and c > b and float((2 * c - a - b) ** 2) > k2x3 * float(a + c + b):
+                mask[i, j] |= 1
+    cand = (mask & 1).astype(bool)
+    for i in range(1, ny - 1):
+        for j in range(1, nx - 1):
+            if cand[i, j] and cand[i - 1, j - 1:j + 2].any() and cand[i + 1, j - 1:j + 2].any():
+                mask[i, j] |= 2
+    return mask

@@ -430,3 +430,51 @@ def test_strip_sheet_cancels_the_mean_field_of_a_long_lens_strip():
                    ray_box=(tx - 0.5 * a, ty - 0.5 * a, tx + 0.5 * a, ty + 0.5 * a), ray_n=(1, 1))
         b0, _ = oracle.beta_direct(g0, X.ravel(), Y.ravel(), m, np.array([0]))
         assert abs((ty - b0[0, 1]) - 2 * ks * ty) <= 0.02 * 2 * ks * abs(ty)
+
+
+# -- Peak identification (§4.2) ---------------------------------------------------
+
+def test_peaks_ridge_spike_and_threshold():
+    """A ridge crossing five curves at one position: candidates on all five,
+    true peaks on the inner three (each has candidate neighbours on both
+    sides); an isolated spike is a candidate only; a bump below 5 sigma is
+    nothing.  Along y the transposed map gives the transposed mask."""
+    N = np.full((9, 12), 1000, np.int64)
+    N[2:7, 5] = 1300            # h = 200 > 5 sqrt(1100) = 165.8
+    N[1, 9] = 1400              # isolated
+    N[7, 2] = 1200              # h = 133 < 5 sqrt(1067) = 163.3
+    m = oracle.peaks(N)
+    assert np.array_equal(np.nonzero(m & 1)[0], [1, 2, 3, 4, 5, 6])
+    assert set(zip(*np.nonzero(m & 1))) == {(1, 9), (2, 5), (3, 5), (4, 5), (5, 5), (6, 5)}
+    assert set(zip(*np.nonzero(m & 2))) == {(3, 5), (4, 5), (5, 5)}
+    assert np.array_equal(oracle.peaks(N.T, along="y"), m.T)
+
+
+def test_peaks_threshold_is_strict_and_exact():
+    """The oracle's squared integer form of h > 5 sigma against the criterion
+    as the paper states it (h = N - <N> against 5 sqrt(<N>)), by brute force
+    over N for two neighbours of 1000: both switch at the same N, and the
+    comparison is strict."""
+    a = b = 1000
+    first = None
+    for c in range(1001, 1400):
+        mean = (a + b + c) / 3.0
+        if (c - mean) > 5.0 * math.sqrt(mean) + 1e-9:
+            first = c
+            break
+    N = np.full((3, 3), a, np.int64)
+    N[1, 1] = first - 1
+    assert not (oracle.peaks(N)[1, 1] & 1)
+    N[1, 1] = first
+    assert oracle.peaks(N)[1, 1] & 1
+    # ties are not peaks: N must exceed both neighbours
+    N = np.array([[5, 5, 5], [1000, 5000, 5000], [5, 5, 5]])
+    assert not (oracle.peaks(N)[1, 1] & 1)
+
+
+def test_peaks_of_poisson_noise_are_rare():
+    """A flat Poisson map (mean 1000): 5 sigma candidates occur with
+    probability about 3e-7 per pixel, true peaks (three aligned) never."""
+    N = np.random.default_rng(3).poisson(1000.0, (200, 300))
+    m = oracle.peaks(N)
+    assert (m & 1).sum() <= 2 and (m & 2).sum() == 0
