@@ -356,6 +356,31 @@ ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens,
  */
 ml_status ml_field_set_counts(ml_field *f, const uint32_t *counts, int32_t in_is_device, void *stream);
 
+/* Light-curve directions of ml_find_peaks. */
+enum { ML_ALONG_X = 0, ML_ALONG_Y = 1 };
+
+/*
+ * ml_find_peaks - peak identification of §4.2 on the field's count map.
+ * Light curves run along x (each map row is a curve; the neighbouring curves
+ * are the rows above and below) or along y.  Step 1: position j of curve i
+ * is a candidate when N_ij > N_i,j-1 and N_ij > N_i,j+1 and
+ * h = N_ij - <N> > nsigma sqrt(<N>), <N> the mean of the three, tested as
+ * (2N - a - b)^2 > 3 nsigma^2 (a + N + b) in FP64 (exact for counts below
+ * 2^26); curve ends are never candidates.  Step 2: a candidate is a true peak
+ * when a candidate lies among positions j-1, j, j+1 of both neighbouring
+ * curves; the first and last curves have none.  The paper uses nsigma = 5.
+ *  mask:     device, 4-byte aligned, map_ny x map_nx bytes + 4 bytes of
+ *            padding; bit 0 candidate, bit 1 true peak; NULL to use internal
+ *            scratch.
+ *  peaks:    device, capacity x (ix, iy) int32 pairs of true peaks, in no
+ *            particular order; may be NULL when capacity is 0.
+ *  n_found:  host; the number of true peaks (may exceed capacity).
+ * Synchronises `stream`.  Errors: ML_ERR_STATE for a CIC field;
+ * ML_ERR_INVALID_ARG; ML_ERR_CUDA.
+ */
+ml_status ml_find_peaks(ml_field *f, int32_t along, double nsigma, uint8_t *mask, int32_t *peaks,
+                        int64_t capacity, int64_t *n_found, void *stream);
+
 /*
  * ml_field_clear - zero the map and the counters (stream-ordered).
  */

@@ -42,7 +42,7 @@ EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays"
            "ml_light_curves_noalloc", "ml_batch_create", "ml_batch_run", "ml_batch_field",
            "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy",
            "ml_cic_forward", "ml_cic_backward", "ml_cic_backward_ex", "ml_map_light_curves",
-           "ml_map_light_curves_backward", "ml_field_set_counts")
+           "ml_map_light_curves_backward", "ml_field_set_counts", "ml_find_peaks")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -131,6 +131,7 @@ def load(path: str | None = None):
         "ml_cic_backward": ([V, V, V, V, V], st),
         "ml_cic_backward_ex": ([V, V, V, V, C.c_int32, V], st),
         "ml_field_set_counts": ([V, V, C.c_int32, V], st),
+        "ml_find_peaks": ([V, C.c_int32, C.c_double, V, V, C.c_int64, P(C.c_int64), V], st),
         "ml_map_light_curves": ([V, C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V], st),
         "ml_map_light_curves_backward": ([C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V, V], st),
         "ml_field_clear": ([V, V], st),
@@ -219,6 +220,21 @@ ADJOINT_NEARFAR, ADJOINT_DIRECT = 0, 1
 def _tracks_host(tracks):
     tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
     return tr, tr.ctypes.data
+
+
+ALONG_X, ALONG_Y = 0, 1
+
+
+def ml_find_peaks(field, along=ALONG_X, nsigma=5.0, mask=None, capacity=0, stream=None):
+    """Peak identification of §4.2 (see ml.h).  Returns (n_found, peaks) with
+    peaks a device int32 tensor (min(n_found, capacity), 2) of (ix, iy)."""
+    import torch
+    peaks = torch.empty((max(capacity, 1), 2), dtype=torch.int32, device="cuda")
+    n = C.c_int64()
+    _check(load().ml_find_peaks(field, along, float(nsigma), _dptr(mask) if mask is not None else None,
+                                _dptr(peaks) if capacity > 0 else None, capacity, C.byref(n),
+                                _stream(stream)))
+    return n.value, peaks[:min(n.value, capacity)]
 
 
 def ml_field_set_counts(field, counts, stream=None):

@@ -1412,6 +1412,33 @@ ml_status ml_field_set_counts(ml_field *f, const uint32_t *counts, int32_t in_is
     return ML_OK;
 }
 
+ml_status ml_find_peaks(ml_field *f, int32_t along, double nsigma, uint8_t *mask, int32_t *peaks,
+                        int64_t capacity, int64_t *n_found, void *stream)
+{
+    if (!f || !n_found) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (!f->d_map_u32) return fail(ML_ERR_STATE, "peak identification needs an NGP count map");
+    if (along != ML_ALONG_X && along != ML_ALONG_Y) return fail(ML_ERR_INVALID_ARG, "unknown curve direction");
+    if (!(nsigma > 0.0) || !is_fin(nsigma)) return fail(ML_ERR_INVALID_ARG, "nsigma must be positive");
+    if (capacity < 0 || (capacity > 0 && !peaks)) return fail(ML_ERR_INVALID_ARG, "bad peak list");
+    if (mask && (uintptr_t)mask % 4 != 0) return fail(ML_ERR_INVALID_ARG, "mask must be 4-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t npix = (size_t)f->g.mnx * f->g.mny;
+    uint8_t *m = mask;
+    unsigned long long *found = nullptr, h_found = 0;
+    cudaError_t e = cudaSuccess;
+    if (!m) e = cudaMallocAsync((void **)&m, npix + 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&found, sizeof(unsigned long long), s);
+    if (e == cudaSuccess)
+        e = launch_peaks(f->d_map_u32, f->g.mnx, f->g.mny, along, nsigma, m, peaks, capacity, found, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_found, found, sizeof(h_found), cudaMemcpyDeviceToHost, s);
+    if (found) cudaFreeAsync(found, s);
+    if (!mask && m) cudaFreeAsync(m, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "peak identification");
+    *n_found = (int64_t)h_found;
+    return ML_OK;
+}
+
 ml_status ml_field_clear(ml_field *f, void *stream)
 {
     if (!f) return fail(ML_ERR_INVALID_ARG, "field is NULL");

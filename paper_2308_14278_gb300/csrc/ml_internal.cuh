@@ -129,6 +129,8 @@ cudaError_t launch_light_curves_noalloc(const Geo &g, const uint32_t *cu, const 
                                         double scale, const double *tracks_host, int n_tracks,
                                         int n_samples, double sigma_px, float *out, cudaStream_t s);
 int light_curve_taps(double sigma_px, float taps[129]);
+cudaError_t launch_peaks(const uint32_t *N, int nx, int ny, int along, double nsigma, uint8_t *mask,
+                         int32_t *peaks, int64_t capacity, unsigned long long *found, cudaStream_t s);
 cudaError_t launch_map_sum(const uint32_t *map, size_t n, unsigned long long *sum, int num_sms,
                            cudaStream_t s);
 cudaError_t launch_light_curves_adj(int mnx, int mny, const double *d_tracks, int n_tracks,

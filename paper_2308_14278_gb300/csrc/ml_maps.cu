@@ -291,6 +291,81 @@ cudaError_t launch_map_sum(const uint32_t *map, size_t n, unsigned long long *su
     return cudaGetLastError();
 }
 
+// ---- peak identification on light curves (§4.2) ---------------------------------
+//
+// Curves run along x (a map row is a curve; its neighbours are the rows above
+// and below) or along y.  Candidate at position j of curve i: N > both
+// neighbours along the curve and (2N - a - b)^2 > 3 k^2 (a + N + b), the
+// squared form of N - <N> > k sqrt(<N>), compared in FP64 (exact for counts
+// below 2^26).  True peak: a candidate with a candidate among positions
+// j-1..j+1 of both neighbouring curves.
+__device__ __forceinline__ uint32_t peak_count(const uint32_t *N, int nx, int c, int j, int along)
+{
+    return along == 0 ? N[(size_t)c * nx + j] : N[(size_t)j * nx + c];
+}
+
+__global__ void k_peak_candidates(const uint32_t *__restrict__ N, int nx, int ny, int along,
+                                  double k2x3, uint8_t *__restrict__ mask)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)nx * ny) return;
+    const int ix = (int)(q % nx), iy = (int)(q / nx);
+    const int len = along == 0 ? nx : ny;          // positions along a curve
+    const int j = along == 0 ? ix : iy, c = along == 0 ? iy : ix;
+    uint8_t m = 0;
+    if (j > 0 && j < len - 1) {
+        const uint32_t a = peak_count(N, nx, c, j - 1, along), v = peak_count(N, nx, c, j, along),
+                       b = peak_count(N, nx, c, j + 1, along);
+        if (v > a && v > b) {
+            const double d = 2.0 * (double)v - (double)a - (double)b;
+            if (d * d > k2x3 * ((double)a + (double)v + (double)b)) m = 1;
+        }
+    }
+    mask[q] = m;
+}
+
+__global__ void k_peak_validate(int nx, int ny, int along, uint8_t *__restrict__ mask,
+                                int32_t *__restrict__ peaks, int64_t capacity,
+                                unsigned long long *__restrict__ found)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)nx * ny) return;
+    if (!(mask[q] & 1)) return;
+    const int ix = (int)(q % nx), iy = (int)(q / nx);
+    const int ncurves = along == 0 ? ny : nx, len = along == 0 ? nx : ny;
+    const int j = along == 0 ? ix : iy, c = along == 0 ? iy : ix;
+    if (c == 0 || c == ncurves - 1) return;
+    bool lo = false, hi = false;
+    for (int dj = -1; dj <= 1; ++dj) {
+        const int jj = j + dj;
+        if (jj < 0 || jj >= len) continue;
+        const size_t ql = along == 0 ? (size_t)(c - 1) * nx + jj : (size_t)jj * nx + (c - 1);
+        const size_t qh = along == 0 ? (size_t)(c + 1) * nx + jj : (size_t)jj * nx + (c + 1);
+        lo |= (mask[ql] & 1) != 0;
+        hi |= (mask[qh] & 1) != 0;
+    }
+    if (!(lo && hi)) return;
+    // bit 1 only: other threads read bit 0 of this byte concurrently
+    atomicOr(reinterpret_cast<unsigned int *>(mask + (q & ~(int64_t)3)), 2u << (8 * (q & 3)));
+    const unsigned long long slot = atomicAdd(found, 1ull);
+    if ((int64_t)slot < capacity) {
+        peaks[2 * slot] = ix;
+        peaks[2 * slot + 1] = iy;
+    }
+}
+
+cudaError_t launch_peaks(const uint32_t *N, int nx, int ny, int along, double nsigma, uint8_t *mask,
+                         int32_t *peaks, int64_t capacity, unsigned long long *found, cudaStream_t s)
+{
+    const int64_t n = (int64_t)nx * ny;
+    cudaError_t e = cudaMemsetAsync(found, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    k_peak_candidates<<<blocks, 256, 0, s>>>(N, nx, ny, along, 3.0 * nsigma * nsigma, mask);
+    k_peak_validate<<<blocks, 256, 0, s>>>(nx, ny, along, mask, peaks, capacity, found);
+    return cudaGetLastError();
+}
+
 // ---- adjoint of the light curves ---------------------------------------------
 //
 // A light-curve sample is L = sum_c w_c sum_{dx,dy} taps[dx] taps[dy] M[p_c + (dx, dy)]
