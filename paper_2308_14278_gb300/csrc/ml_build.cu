@@ -481,14 +481,35 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
     double ar[HP + 1], ai[HP + 1];
 #pragma unroll
     for (int j = 0; j <= HP; ++j) { ar[j] = 0.0; ai[j] = 0.0; }
-    for (int64_t k = threadIdx.x; k < L.n; k += blockDim.x) {
-        int2 c = lc[k];
-        int64_t lbx = floor_div(c.x, h.bxn), lby = floor_div(c.y, h.byn);
-        bool in_box_block = lbx - Bx <= 1 && Bx - lbx <= 1 && lby - By <= 1 && By - lby <= 1;
-        bool near = (int64_t)c.x - cx <= 1 && cx - (int64_t)c.x <= 1 &&
-                    (int64_t)c.y - cy <= 1 && cy - (int64_t)c.y <= 1;
-        if (!in_box_block || near) continue;
-        p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ar, ai);
+    // lenses of the box block (3 x 3 boxes) outside the cell's 3 x 3 block.
+    // Cells of the binning grid (the lattice and its ring) are contiguous
+    // runs of the sorted table, one per row; lenses beyond the ring (the last
+    // bucket) are scanned only when the box block reaches past the ring.
+    const int64_t xlo = (Bx - 1) * h.bxn, xhi = (Bx + 2) * h.bxn - 1;
+    const int64_t ylo = (By - 1) * h.byn, yhi = (By + 2) * h.byn - 1;
+    const int64_t NE = g.NEx * g.NEy;
+    const int64_t rx0 = max(xlo, (int64_t)-1), rx1 = min(xhi, g.N1x);
+    const int64_t ry0 = max(ylo, (int64_t)-1), ry1 = min(yhi, g.N1y);
+    for (int64_t ry = ry0; ry <= ry1 && rx0 <= rx1; ++ry) {
+        const int64_t b0 = (ry + 1) * g.NEx + (rx0 + 1), b1 = (ry + 1) * g.NEx + (rx1 + 1);
+        const int64_t k0 = L.start[b0], k1 = L.start[b1 + 1];
+        const bool near_row = ry - cy <= 1 && cy - ry <= 1;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            if (near_row) {
+                const int64_t lx = lc[k].x;
+                if (lx - cx <= 1 && cx - lx <= 1) continue;
+            }
+            p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ar, ai);
+        }
+    }
+    if (xlo < -1 || xhi > g.N1x || ylo < -1 || yhi > g.N1y) {
+        for (int64_t k = L.start[NE] + threadIdx.x; k < L.start[NE + 1]; k += blockDim.x) {
+            const int2 c = lc[k];
+            const int64_t lbx = floor_div(c.x, h.bxn), lby = floor_div(c.y, h.byn);
+            const bool in_box_block = lbx - Bx <= 1 && Bx - lbx <= 1 && lby - By <= 1 && By - lby <= 1;
+            if (!in_box_block) continue;
+            p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ar, ai);
+        }
     }
     // box series of this cell's box: sum of the partitions (fixed order)
     const int64_t b = By * h.NBx + Bx;
