@@ -298,7 +298,12 @@ __device__ __forceinline__ void flush_run(RunState &rs, int cx, int cy, unsigned
 // fails) gets a near sum of 1e30, which sends it far outside the map; it is
 // counted as dropped there and as out by the run, and the kernel's epilogue
 // subtracts the dropped rays from the out count.
-template <int P, int NN>
+//
+// CLOSE = false when no ray of the warp's walk can come within the close-pass
+// radius of a near lens (checked per row against the lens's distance to the
+// row's ray segment, with a margin): the per-ray minimum distance and its
+// vote are then skipped; the close-pass branch could not be taken anyway.
+template <int P, int NN, bool CLOSE>
 __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
                                            int kbeg, int kend, bool on, float dyl, float dyl_lo,
                                            RunState &rs, unsigned &drop)
@@ -325,7 +330,7 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         for (int q = 0; q < NN; ++q) {
             float dx = __fsub_rn(t, lx[q]);
             float r2 = __fmaf_rn(dx, dx, dy2[q]);
-            mn = fminf(mn, r2);
+            if (CLOSE) mn = fminf(mn, r2);
             float sv = __fmul_rn(lm[q], rcp_approx(r2));
             sx = __fmaf_rn(dx, sv, sx);
             sy = __fmaf_rn(dy[q], sv, sy);
@@ -353,7 +358,7 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         float sx0, sy0, mn0, sx1, sy1, mn1;
         near(t0, sx0, sy0, mn0);
         near(t1, sx1, sy1, mn1);
-        if (NN > 0) {
+        if (NN > 0 && CLOSE) {
             const bool c0 = on && mn0 < a.rc2, c1 = on && mn1 < a.rc2;
             if (__ballot_sync(0xffffffffu, c0 || c1)) {
                 close_pass(c0, u, t0, sx0, sy0);
@@ -390,7 +395,7 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         float X0, Y0, sx0, sy0, mn0;
         row_eval<P>(rp, t0, X0, Y0);
         near(t0, sx0, sy0, mn0);
-        if (NN > 0) {
+        if (NN > 0 && CLOSE) {
             const bool c0 = on && mn0 < a.rc2;
             if (__ballot_sync(0xffffffffu, c0)) close_pass(c0, u, t0, sx0, sy0);
         }
@@ -494,12 +499,36 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
         const bool on = k1 > k0;
         const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
         if (uniform && nn <= 4) {
-            switch (nn) {
-            case 0: walk_fixed<P, 0>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-            case 1: walk_fixed<P, 1>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-            case 2: walk_fixed<P, 2>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-            case 3: walk_fixed<P, 3>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
-            default: walk_fixed<P, 4>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+            // can a ray of this walk pass within the close-pass radius of a lens?
+            // (distance from each lens to the row's ray segment, 1 % margin
+            // against the FP32 rounding of the per-ray r^2)
+            bool close = false;
+            if (on) {
+                const float tlo = __fmul_rn(__fadd_rn((float)kbeg, a.c0_f), a.l3x_f);
+                const float thi = __fmul_rn(__fadd_rn((float)(kend - 1), a.c0_f), a.l3x_f);
+                for (int q = 0; q < nn; ++q) {
+                    const float4 L = near[q];
+                    const float dy = __fsub_rn(dyl, L.y);
+                    const float dx = fmaxf(0.f, fmaxf(tlo - L.x, L.x - thi));
+                    close |= __fmaf_rn(dx, dx, dy * dy) <= 1.01f * a.rc2 + 1e-30f;
+                }
+            }
+            if (__any_sync(0xffffffffu, close)) {
+                switch (nn) {
+                case 0: walk_fixed<P, 0, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 1: walk_fixed<P, 1, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 2: walk_fixed<P, 2, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 3: walk_fixed<P, 3, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                default: walk_fixed<P, 4, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                }
+            } else {
+                switch (nn) {
+                case 0: walk_fixed<P, 0, false>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 1: walk_fixed<P, 1, false>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 2: walk_fixed<P, 2, false>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 3: walk_fixed<P, 3, false>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                default: walk_fixed<P, 4, false>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                }
             }
         } else {
             walk_any<P>(rp, a, nl, nn, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop);
