@@ -37,10 +37,10 @@ N_TRACKS, TRACK_SAMPLES, SIGMA_PX = 10, 4096, 0.5
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per ray of the shooting kernel, from the ncu capture summarised in
 # profiles/k_shoot_mixed_paper-map-2e10-ray-slice.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 447.5 MB for 2.0e10 rays, tuned grid (80, 20),
+# dram__bytes_write.sum = 444.1 MB for 2.0e10 rays, tuned grid (80, 20),
 # p = 4), valid for the kernel sources with these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = 447.481088e6 / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "7b402787", "ml_internal.cuh": "574b71d3", "ml_task.cuh": "99f52f61"}
+TRAFFIC_BYTES_PER_RAY = 444.141824e6 / 2.0e10
+TRAFFIC_SOURCES = {"ml_shoot.cu": "6d8f64ad", "ml_internal.cuh": "967cb42c", "ml_task.cuh": "99f52f61"}
 
 
 def traffic_per_launch(rays_per_launch: float):
