@@ -67,9 +67,9 @@ __device__ __forceinline__ bool forward_ray(const ShootArgs &a, int64_t r, float
     float u = __fadd_rn((float)(i - c2x * g.n2x), a.c0_f);
     float tt = __fmul_rn(u, a.l3x_f);
     float ax, ay, mn;
-    row_eval<P>(rp, tt, X, Y);
+    row_eval<P>(rp, u, X, Y);
     const NearRuns nr = near_runs(a, c1x, c1y);
-    const GlobalNear nl{&a.L, nr, xnode, yref};
+    const GlobalNear nl{&a.L, nr, xnode, yref, 1.0, 1.0};
     const int nn = nr.total();
     near_sum_f32(nl, nn, tt, dyl, ax, ay, mn);
     bool ok = true;
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
         if (!decode_task(a, t, ts)) continue;
         const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
         const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
-        const int nn = stage_near_y(a, nr, yref, near, nlo, lane);
+        const int nn = stage_near_y<false>(a, nr, yref, near, nlo, lane);
         for (int k = lane; k < 3 * nn; k += 32) acc[k] = 0.0;
         const int64_t j = ts.row0 + lane;
         const bool active = j < ts.rows_end;
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
         const bool head = active && (lane == 0 || j == c2y * g.n2y);
         for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
             const double xnode = g.rx0 + ((double)c2x + 0.5) * g.l2x;
-            stage_near_x(a, nn, xnode, near, nlo, lane);
+            stage_near_x<false>(a, nn, xnode, near, nlo, lane);
             const int64_t i0 = c2x * g.n2x;
             const int kend = (int)(min(i0 + g.n2x, g.n3x) - i0);
             RowPoly<P> rp;
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
                 float gbx = 0.f, gby = 0.f;
                 if (active) {
                     float X, Y, ax, ay, mn;
-                    row_eval<P>(rp, t0, X, Y);
+                    row_eval<P>(rp, u, X, Y);
                     near_sum_f32(nl, nn, t0, dyl, ax, ay, mn);
                     bool ok = true;
                     if (mn < a.rc2)

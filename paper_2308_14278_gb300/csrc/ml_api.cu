@@ -743,15 +743,23 @@ ShootArgs make_args(const ml_field *f)
     // close-pass radius: FP32 offsets of size up to |t| + |dyl| give a relative
     // near-term error of 2 * 2^-24 (|t| + |dyl|) / r; below r_c it could pass
     // 5e-7, so those rays take the hi/lo path
+    // (the same radius in lattice units for the counting kernels' sums)
     {
         double rc = 4.0 * 5.9604644775390625e-8 * (0.5 * g.l2x + 32.0 * g.l3y) / 5e-7;
         a.rc2 = (float)(rc * rc);
+        a.rc2u = (float)((rc / g.l3x) * (rc / g.l3x));
     }
     a.ipx_f = (float)(1.0 / g.dpx);
     a.ipy_f = (float)(1.0 / g.dpy);
+    a.l3yx = g.l3y / g.l3x;
+    a.l3yx_f = (float)a.l3yx;
+    a.il3x = 1.0 / g.l3x;
+    a.mpx = 1.0 / (g.l3x * g.dpx);
+    a.yx_f = (float)(g.dpx / g.dpy);
     const bool fold = g.macro == ML_MACRO_FOLD;
-    a.cxy_f = fold ? (float)(g.dy * g.l3y / g.dpx) : 0.f;
-    a.q2_f = fold ? (float)(0.5 * g.dx / g.dpx) : 0.f;
+    // macro terms of the row polynomial per power of u (theta_x offset u l3x)
+    a.cxy_f = fold ? (float)(g.dy * g.l3y * g.l3x / g.dpx) : 0.f;
+    a.q2_f = fold ? (float)(0.5 * g.dx * g.l3x * g.l3x / g.dpx) : 0.f;
     a.rho_y = ((fold ? 2.0 * (1.0 - g.kappa0) : 1.0 - g.kappa + g.gamma) + sheet_ky(g)) * g.l3y / g.dpy;
     return a;
 }

@@ -272,7 +272,8 @@ cudaError_t launch_coeffs_direct(const Geo &g, const LensTable &L, double *coef6
 // ---------------------------------------------------------------------------
 // Node records for the mixed path: the smooth part of beta at each node
 // (macro term of Eq. 1, sheet term and far-field c_0, Eq. 9) in map pixel
-// units, split into an integer base and an FP32 fraction, plus c_1..c_p in FP32.
+// units, split into an integer base and an FP32 fraction, plus c_n l3x^n,
+// n = 1..p, in FP32 (the far series per power of the lattice offset).
 // ---------------------------------------------------------------------------
 
 __global__ void k_node_finalize(Geo g, const double *__restrict__ coef, unsigned char *__restrict__ out)
@@ -301,10 +302,15 @@ __global__ void k_node_finalize(Geo g, const double *__restrict__ coef, unsigned
     *reinterpret_cast<double *>(rec) = Sy;
     *reinterpret_cast<int *>(rec + 8) = (int)fbx;
     *reinterpret_cast<float *>(rec + 12) = (float)(Sx - fbx);
-    *reinterpret_cast<float *>(rec + 16) = (float)((ax + sheet_kx(g)) / g.dpx);
+    *reinterpret_cast<float *>(rec + 16) = (float)((ax + sheet_kx(g)) * g.l3x / g.dpx);
     *reinterpret_cast<float *>(rec + 20) = (float)(bq / g.dpx);
+    // c_n per power of the lattice offset u: c_n l3x^n
     float2 *cf = reinterpret_cast<float2 *>(rec + 24);
-    for (int q = 1; q <= g.p; ++q) cf[q - 1] = make_float2((float)c[2 * q], (float)c[2 * q + 1]);
+    double ln = 1.0;
+    for (int q = 1; q <= g.p; ++q) {
+        ln *= g.l3x;
+        cf[q - 1] = make_float2((float)(c[2 * q] * ln), (float)(c[2 * q + 1] * ln));
+    }
 }
 
 cudaError_t launch_node_finalize(const Geo &g, const double *coef64, unsigned char *nodes,

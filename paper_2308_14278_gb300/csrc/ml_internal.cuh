@@ -50,9 +50,10 @@ struct LensTable {
 //   double Sy;  int32 bx;  float fx;  float ax;  float bq;  float2 c[p]
 // (Sy, bx + fx) is the smooth part of beta at the node in map pixel units
 // (macro model, sheet and far-field c_0); ax is d(beta_x)/d(theta_x) of the
-// macro and sheet terms at the node in pixels per theta_E; bq is the change
-// of beta_x per ray row (pixels; the fold's d_y theta_x term, else 0); c[n-1]
-// is the FP32 far-field Taylor coefficient c_n, n = 1..p, in theta_E units.
+// macro and sheet terms at the node in pixels per ray column (l3x); bq is the
+// change of beta_x per ray row (pixels; the fold's d_y theta_x term, else 0);
+// c[n-1] = c_n l3x^n in FP32, n = 1..p: the far-field Taylor coefficient of
+// Eq. 9 per power of the lattice offset u (theta_x - x_node = u l3x).
 __host__ __device__ inline size_t node_stride(int p) { return 24 + 8 * (size_t)p; }
 
 // Everything a shooting or tracing kernel needs.
@@ -75,10 +76,16 @@ struct ShootArgs {
     int near_cap;                   // float4 slots of shared memory per warp
     // float constants of the mixed kernel
     float l3x_f, l3x_lo, c0_f, ipx_f, ipy_f;
-    float cxy_f;                    // d(beta_x)/d(theta_x) change per ray row (fold: d_y l3y / dpx)
-    float q2_f;                     // beta_x curvature in theta_x (fold: d_x / (2 dpx)), else 0
-    float rc2;                      // close-pass radius^2 of near_sum_f32
+    float cxy_f;                    // change of the u slope of beta_x per ray row (fold: d_y l3y l3x / dpx)
+    float q2_f;                     // beta_x curvature in u (fold: d_x l3x^2 / (2 dpx)), else 0
+    float rc2;                      // close-pass radius^2 of near_sum_f32 (theta_E^2)
+    float rc2u;                     // the same in lattice units (near_sum_lat)
+    float l3yx_f;                   // l3y / l3x: a ray row in lattice units
+    float yx_f;                     // dpx / dpy: y deflection per x deflection unit (pixels)
     double rho_y;                   // (d(macro_y)/d(theta_y) + kappa_*) * l3y / dpy
+    double l3yx;                    // l3y / l3x (FP64)
+    double il3x;                    // 1 / l3x
+    double mpx;                     // 1 / (l3x dpx): lens mass to lattice-unit pixel deflection
 };
 
 // Many maps in one persistent launch: per-map arguments (device array) and
@@ -163,14 +170,22 @@ __host__ __device__ inline void macro64(const Geo &g, double tx, double ty, doub
     }
 }
 
-// Near-lens records: rec(k) = (x_k - x_node, y_k - y_ref, m_k, -) rounded to
-// FP32, lo(k) = the rounding remainders of the two offsets.  Deflection of the near lenses (the directly summed part of
-// Eq. 9) in FP32 on these node-relative coordinates:
+// Near-lens records in theta units (CIC forward and adjoint): rec(k) =
+// (x_k - x_node, y_k - y_ref, m_k, -) rounded to FP32, lo(k) = the rounding
+// remainders of the two offsets.  Deflection of the near lenses (the directly
+// summed part of Eq. 9) in FP32 on these node-relative coordinates:
 //   dx = t - lx,  dy = dyl - ly,  t = u * l3x (u a half-integer lattice offset).
 // The FP32 rounding of the offsets costs a relative error of about
 // 2^-23 (|t| + |dyl|) / r for a ray at distance r from a lens.  Rays that pass
 // closer than r_c (sqrt(rc2), where that error could exceed 5e-7) redo the
 // sum with the offsets carried as hi + lo float pairs (near_sum_hilo).
+//
+// The counting kernels (NGP) and the tracer take the same sum in lattice
+// units: offsets divided by l3x, so that the ray's x offset is u itself
+// (exact in FP32), and masses scaled to pixel units, m' = m / (l3x dpx).  The
+// near deflection then adds to the row polynomial's pixel value directly:
+//   X += (lx - u) m' / r^2,  Y += (ly - dyl) (dpx/dpy) m' / r^2.
+// The same error argument holds with r_c / l3x (rc2u).
 // Approximate reciprocal (the PTX rcp.approx.ftz.f32 instruction, relative
 // error below 2^-23).  The near sums use m * rcp(r^2); r^2 never comes near
 // the float range limits for lenses and rays inside a field.
@@ -202,33 +217,79 @@ __device__ __forceinline__ void near_sum_f32(const Near &nl, int nn, float t, fl
     rmin = mn;
 }
 
-// The same for two rays of one row (t0, t1), sharing each lens record and
-// dy; per ray the operations are exactly those of near_sum_f32.
+// Lattice-unit near sum of one ray at offset u, added to the ray's pixel
+// position (X, Y); rmin = the smallest r^2 (lattice units).
 template <class Near>
-__device__ __forceinline__ void near_sum2_f32(const Near &nl, int nn, float t0, float t1, float dyl,
-                                              float &ax0, float &ay0, float &rmin0,
-                                              float &ax1, float &ay1, float &rmin1)
+__device__ __forceinline__ void near_sum_lat(const Near &nl, int nn, float u, float dyl, float yx,
+                                             float &X, float &Y, float &rmin)
 {
-    float sx0 = 0.f, sy0 = 0.f, mn0 = 3.0e38f, sx1 = 0.f, sy1 = 0.f, mn1 = 3.0e38f;
+    float mn = 3.0e38f;
     for (int k = 0; k < nn; ++k) {
         float4 L = nl.rec(k);
-        float dy = __fsub_rn(dyl, L.y);
+        float dy = __fsub_rn(L.y, dyl);
         float dy2 = __fmul_rn(dy, dy);
-        float dx0 = __fsub_rn(t0, L.x);
-        float dx1 = __fsub_rn(t1, L.x);
+        float dyy = __fmul_rn(dy, yx);
+        float dx = __fsub_rn(L.x, u);
+        float r2 = __fmaf_rn(dx, dx, dy2);
+        mn = fminf(mn, r2);
+        float s = __fmul_rn(L.z, rcp_approx(r2));
+        X = __fmaf_rn(dx, s, X);
+        Y = __fmaf_rn(dyy, s, Y);
+    }
+    rmin = mn;
+}
+
+// The same for two rays of one row (u0, u1), sharing each lens record and
+// dy; per ray the operations are exactly those of near_sum_lat.
+template <class Near>
+__device__ __forceinline__ void near_sum2_lat(const Near &nl, int nn, float u0, float u1, float dyl,
+                                              float yx, float &X0, float &Y0, float &rmin0,
+                                              float &X1, float &Y1, float &rmin1)
+{
+    float mn0 = 3.0e38f, mn1 = 3.0e38f;
+    for (int k = 0; k < nn; ++k) {
+        float4 L = nl.rec(k);
+        float dy = __fsub_rn(L.y, dyl);
+        float dy2 = __fmul_rn(dy, dy);
+        float dyy = __fmul_rn(dy, yx);
+        float dx0 = __fsub_rn(L.x, u0);
+        float dx1 = __fsub_rn(L.x, u1);
         float r20 = __fmaf_rn(dx0, dx0, dy2);
         float r21 = __fmaf_rn(dx1, dx1, dy2);
         mn0 = fminf(mn0, r20);
         mn1 = fminf(mn1, r21);
         float s0 = __fmul_rn(L.z, rcp_approx(r20));
         float s1 = __fmul_rn(L.z, rcp_approx(r21));
-        sx0 = __fmaf_rn(dx0, s0, sx0);
-        sy0 = __fmaf_rn(dy, s0, sy0);
-        sx1 = __fmaf_rn(dx1, s1, sx1);
-        sy1 = __fmaf_rn(dy, s1, sy1);
+        X0 = __fmaf_rn(dx0, s0, X0);
+        Y0 = __fmaf_rn(dyy, s0, Y0);
+        X1 = __fmaf_rn(dx1, s1, X1);
+        Y1 = __fmaf_rn(dyy, s1, Y1);
     }
-    ax0 = sx0; ay0 = sy0; rmin0 = mn0;
-    ax1 = sx1; ay1 = sy1; rmin1 = mn1;
+    rmin0 = mn0;
+    rmin1 = mn1;
+}
+
+// Close-pass path in lattice units: u is exact, so only the records' and the
+// row's rounding remainders are carried.  Adds to (X, Y), which the caller
+// resets to the row polynomial's value.  Returns false when the ray
+// coincides with a lens even at this precision.
+template <class Near>
+__device__ __forceinline__ bool near_sum_hilo_lat(const Near &nl, int nn, float u, float dyl,
+                                                  float dyl_lo, float yx, float &X, float &Y)
+{
+    bool hit = false;
+    for (int k = 0; k < nn; ++k) {
+        float4 L = nl.rec(k);
+        float2 R = nl.lo(k);
+        float dx = __fadd_rn(__fsub_rn(L.x, u), R.x);
+        float dy = __fadd_rn(__fsub_rn(L.y, dyl), __fsub_rn(R.y, dyl_lo));
+        float r2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        hit |= (r2 == 0.f);
+        float s = __fmul_rn(L.z, rcp_approx(r2));
+        X = __fmaf_rn(dx, s, X);
+        Y = __fmaf_rn(__fmul_rn(dy, yx), s, Y);
+    }
+    return !hit;
 }
 
 // Close-pass path: the near sum with the offsets carried as hi + lo float
@@ -267,8 +328,9 @@ struct SmemNear {
 };
 
 // Per-ray-row polynomial of the smooth part of beta (map pixel units) in the
-// node-relative x offset t:  X(t) = sum X[m] t^m,  Y(t) = sum Y[m] t^m, with
-// integer bases bx, by (pixel = base + floor(value)).
+// node-relative lattice offset u (theta_x - x_node = u l3x):
+// X(u) = sum X[m] u^m,  Y(u) = sum Y[m] u^m, with integer bases bx, by
+// (pixel = base + floor(value)).
 template <int P>
 struct RowPoly {
     float X[P + 1], Y[P + 1];
@@ -276,10 +338,10 @@ struct RowPoly {
 };
 
 // Build the row polynomial of one node for the ray row at node-relative y
-// offset s = q * l3y (q a half-integer):  the far series
-// F(t + i s) = sum_{n=1..P} c_n (t + i s)^n is re-expanded in t by a Taylor
-// shift (repeated synthetic division), then beta_x = Sx + Ax t - Re F / dpx
-// and beta_y = Sy + Ay s + Im F / dpy.
+// offset q * l3y (q a half-integer), in lattice units s = q l3y / l3x: the
+// far series F = sum_{n=1..P} c_n l3x^n (u + i s)^n is re-expanded in u by a
+// Taylor shift (repeated synthetic division), then beta_x = Sx + Ax u -
+// Re F / dpx and beta_y = Sy + Ay q + Im F / dpy.
 template <int P>
 __device__ __forceinline__ void row_setup(const unsigned char *rec, float q, const ShootArgs &a,
                                           RowPoly<P> &rp)
@@ -290,7 +352,7 @@ __device__ __forceinline__ void row_setup(const unsigned char *rec, float q, con
     const float axn = *reinterpret_cast<const float *>(rec + 16);
     const float bqn = *reinterpret_cast<const float *>(rec + 20);
     const float2 *c = reinterpret_cast<const float2 *>(rec + 24);
-    const float s = __fmul_rn(q, (float)a.g.l3y);
+    const float s = __fmul_rn(q, a.l3yx_f);
     float br[P + 1], bi[P + 1];
     br[0] = 0.f;
     bi[0] = 0.f;
@@ -336,13 +398,13 @@ __device__ __forceinline__ void row_setup(const unsigned char *rec, float q, con
 }
 
 template <int P>
-__device__ __forceinline__ void row_eval(const RowPoly<P> &rp, float t, float &X, float &Y)
+__device__ __forceinline__ void row_eval(const RowPoly<P> &rp, float u, float &X, float &Y)
 {
     float x = rp.X[P], y = rp.Y[P];
 #pragma unroll
     for (int m = P - 1; m >= 0; --m) {
-        x = __fmaf_rn(x, t, rp.X[m]);
-        y = __fmaf_rn(y, t, rp.Y[m]);
+        x = __fmaf_rn(x, u, rp.X[m]);
+        y = __fmaf_rn(y, u, rp.Y[m]);
     }
     X = x;
     Y = y;

@@ -224,24 +224,6 @@ __device__ __forceinline__ void run_add(RunState &rs, int gx, int gy, uint32_t *
     ++rs.cnt;
 }
 
-// Everything of one ray after its near sum: subtract it (pixel units), take
-// the close-pass path if needed, return the pixel coordinates.  A ray that
-// hits a lens exactly is sent to (-1, -1) and counted in `drop`.
-template <int P, class Near>
-__device__ __forceinline__ void finish_ray(const RowPoly<P> &rp, const ShootArgs &a, const Near &nl,
-                                           int nn, float u, float t, float dyl, float dyl_lo,
-                                           float X, float Y, float ax, float ay, float rmin,
-                                           int &gx, int &gy, unsigned &drop)
-{
-    bool ok = true;
-    if (rmin < a.rc2)
-        ok = near_sum_hilo(nl, nn, u, t, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
-    X = __fmaf_rn(-ax, a.ipx_f, X);
-    Y = __fmaf_rn(-ay, a.ipy_f, Y);
-    pixel_xy(X, Y, rp.bx, rp.by, gx, gy);
-    if (!ok) { gx = -1; gy = -1; ++drop; }
-}
-
 // Lane-valid ray of a warp-uniform walk position.
 __device__ __forceinline__ bool in_range(int k, int k0, int k1) { return k >= k0 && k < k1; }
 
@@ -289,13 +271,13 @@ __device__ __forceinline__ void flush_run(RunState &rs, int cx, int cy, unsigned
 // registers).  Rays go in pairs; a run's length is the distance between the
 // indices where it starts and ends, so no per-ray counting is needed; one
 // warp vote per pair decides whether any lane's pixel changed.  Per ray the
-// arithmetic is exactly near_sum_f32's and row_eval's.
+// arithmetic is exactly near_sum_lat's and row_eval's.
 //
 // Pixels are compared in their raw floor form: the bit pattern r of
 // X + 1.5 * 2^23 rounded toward -inf, so that pixel = r - 0x4B400000 + base
 // (wrapping 32-bit arithmetic, a bijection); the pixel itself is formed only
 // when a run is flushed.  A ray that coincides with a lens (close-pass path
-// fails) gets a near sum of 1e30, which sends it far outside the map; it is
+// fails) gets X = -1e30, which sends it far outside the map; it is
 // counted as dropped there and as out by the run, and the kernel's epilogue
 // subtracts the dropped rays from the out count.
 //
@@ -308,14 +290,15 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
                                            int kbeg, int kend, bool on, float dyl, float dyl_lo,
                                            RunState &rs, unsigned &drop)
 {
-    float lx[NN > 0 ? NN : 1], lm[NN > 0 ? NN : 1], dy[NN > 0 ? NN : 1], dy2[NN > 0 ? NN : 1];
+    float lx[NN > 0 ? NN : 1], lm[NN > 0 ? NN : 1], dy2[NN > 0 ? NN : 1], dyy[NN > 0 ? NN : 1];
 #pragma unroll
     for (int q = 0; q < NN; ++q) {
         float4 L = nl.near[q];
         lx[q] = L.x;
         lm[q] = L.z;
-        dy[q] = __fsub_rn(dyl, L.y);
-        dy2[q] = __fmul_rn(dy[q], dy[q]);
+        const float dy = __fsub_rn(L.y, dyl);
+        dy2[q] = __fmul_rn(dy, dy);
+        dyy[q] = __fmul_rn(dy, a.yx_f);
     }
     const Geo &g = a.g;
     const unsigned offx = (unsigned)rp.bx - 0x4B400000u, offy = (unsigned)rp.by - 0x4B400000u;
@@ -323,51 +306,54 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
     int kst = kbeg;                      // first ray of the current run in this walk
     float u = __fadd_rn((float)kbeg, a.c0_f);
 
-    // near sum of one ray (exactly near_sum_f32's arithmetic)
-    auto near = [&](float t, float &sx, float &sy, float &mn) {
-        sx = 0.f; sy = 0.f; mn = 3.0e38f;
+    // near sum of one ray added to its pixel position (exactly near_sum_lat's
+    // arithmetic)
+    auto near = [&](float uu, float &X, float &Y, float &mn) {
+        mn = 3.0e38f;
 #pragma unroll
         for (int q = 0; q < NN; ++q) {
-            float dx = __fsub_rn(t, lx[q]);
+            float dx = __fsub_rn(lx[q], uu);
             float r2 = __fmaf_rn(dx, dx, dy2[q]);
             if (CLOSE) mn = fminf(mn, r2);
             float sv = __fmul_rn(lm[q], rcp_approx(r2));
-            sx = __fmaf_rn(dx, sv, sx);
-            sy = __fmaf_rn(dy[q], sv, sy);
+            X = __fmaf_rn(dx, sv, X);
+            Y = __fmaf_rn(dyy[q], sv, Y);
         }
     };
-    auto raw = [&](float X, float Y, float sx, float sy, unsigned &rx, unsigned &ry) {
-        rx = (unsigned)__float_as_int(__fadd_rd(__fmaf_rn(-sx, a.ipx_f, X), 12582912.0f));
-        ry = (unsigned)__float_as_int(__fadd_rd(__fmaf_rn(-sy, a.ipy_f, Y), 12582912.0f));
+    auto raw = [&](float X, float Y, unsigned &rx, unsigned &ry) {
+        rx = (unsigned)__float_as_int(__fadd_rd(X, 12582912.0f));
+        ry = (unsigned)__float_as_int(__fadd_rd(Y, 12582912.0f));
     };
-    // a failed close pass (ray on a lens) sends the ray far outside the map
-    auto close_pass = [&](bool c, float uu, float t, float &sx, float &sy) {
-        if (c && !near_sum_hilo(nl, NN, uu, t, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx, sy)) {
-            sx = 1.0e30f;
-            ++drop;
+    // a close pass redoes the ray from its row polynomial; a failed one (ray
+    // on a lens) sends the ray far outside the map
+    auto close_pass = [&](bool c, float uu, float &X, float &Y) {
+        if (c) {
+            row_eval<P>(rp, uu, X, Y);
+            if (!near_sum_hilo_lat(nl, NN, uu, dyl, dyl_lo, a.yx_f, X, Y)) {
+                X = -1.0e30f;
+                ++drop;
+            }
         }
     };
 
     int k = kbeg;
     for (; k + 1 < kend; k += 2, u += 2.f) {
         const float u1 = __fadd_rn(u, 1.f);
-        const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
-        float X0, Y0, X1, Y1;
-        row_eval<P>(rp, t0, X0, Y0);
-        row_eval<P>(rp, t1, X1, Y1);
-        float sx0, sy0, mn0, sx1, sy1, mn1;
-        near(t0, sx0, sy0, mn0);
-        near(t1, sx1, sy1, mn1);
+        float X0, Y0, X1, Y1, mn0, mn1;
+        row_eval<P>(rp, u, X0, Y0);
+        row_eval<P>(rp, u1, X1, Y1);
+        near(u, X0, Y0, mn0);
+        near(u1, X1, Y1, mn1);
         if (NN > 0 && CLOSE) {
-            const bool c0 = on && mn0 < a.rc2, c1 = on && mn1 < a.rc2;
+            const bool c0 = on && mn0 < a.rc2u, c1 = on && mn1 < a.rc2u;
             if (__ballot_sync(0xffffffffu, c0 || c1)) {
-                close_pass(c0, u, t0, sx0, sy0);
-                close_pass(c1, u1, t1, sx1, sy1);
+                close_pass(c0, u, X0, Y0);
+                close_pass(c1, u1, X1, Y1);
             }
         }
         unsigned rx0, ry0, rx1, ry1;
-        raw(X0, Y0, sx0, sy0, rx0, ry0);
-        raw(X1, Y1, sx1, sy1, rx1, ry1);
+        raw(X0, Y0, rx0, ry0);
+        raw(X1, Y1, rx1, ry1);
         // after ray 0 the run's pixel is ray 0's whether or not it changed
         const bool ch0 = on && (rx0 != rcx || ry0 != rcy);
         const bool ch1 = on && (rx1 != rx0 || ry1 != ry0);
@@ -391,16 +377,15 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         }
     }
     if (k < kend) {                      // odd tail (warp-uniform)
-        const float t0 = __fmul_rn(u, a.l3x_f);
-        float X0, Y0, sx0, sy0, mn0;
-        row_eval<P>(rp, t0, X0, Y0);
-        near(t0, sx0, sy0, mn0);
+        float X0, Y0, mn0;
+        row_eval<P>(rp, u, X0, Y0);
+        near(u, X0, Y0, mn0);
         if (NN > 0 && CLOSE) {
-            const bool c0 = on && mn0 < a.rc2;
-            if (__ballot_sync(0xffffffffu, c0)) close_pass(c0, u, t0, sx0, sy0);
+            const bool c0 = on && mn0 < a.rc2u;
+            if (__ballot_sync(0xffffffffu, c0)) close_pass(c0, u, X0, Y0);
         }
         unsigned rx0, ry0;
-        raw(X0, Y0, sx0, sy0, rx0, ry0);
+        raw(X0, Y0, rx0, ry0);
         const bool ch0 = on && (rx0 != rcx || ry0 != rcy);
         if (__ballot_sync(0xffffffffu, ch0)) {
             if (ch0) {
@@ -428,21 +413,26 @@ __device__ __forceinline__ void walk_any(const RowPoly<P> &rp, const ShootArgs &
     float u = __fadd_rn((float)kbeg, a.c0_f);
     for (int k = kbeg; k < kend; k += 2, u += 2.f) {
         const float u1 = __fadd_rn(u, 1.f);
-        const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
-        float X0, Y0, X1, Y1, sx0, sy0, mn0, sx1, sy1, mn1;
-        row_eval<P>(rp, t0, X0, Y0);
-        row_eval<P>(rp, t1, X1, Y1);
-        near_sum2_f32(nl, nn, t0, t1, dyl, sx0, sy0, mn0, sx1, sy1, mn1);
+        float X0, Y0, X1, Y1, mn0, mn1;
+        row_eval<P>(rp, u, X0, Y0);
+        row_eval<P>(rp, u1, X1, Y1);
+        near_sum2_lat(nl, nn, u, u1, dyl, a.yx_f, X0, Y0, mn0, X1, Y1, mn1);
         const bool v0 = in_range(k, k0, k1), v1 = in_range(k + 1, k0, k1);
-        const bool c0 = v0 && mn0 < a.rc2, c1 = v1 && mn1 < a.rc2;
+        const bool c0 = v0 && mn0 < a.rc2u, c1 = v1 && mn1 < a.rc2u;
         bool ok0 = true, ok1 = true;
         if (__ballot_sync(0xffffffffu, c0 || c1)) {
-            if (c0) ok0 = near_sum_hilo(nl, nn, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx0, sy0);
-            if (c1) ok1 = near_sum_hilo(nl, nn, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx1, sy1);
+            if (c0) {
+                row_eval<P>(rp, u, X0, Y0);
+                ok0 = near_sum_hilo_lat(nl, nn, u, dyl, dyl_lo, a.yx_f, X0, Y0);
+            }
+            if (c1) {
+                row_eval<P>(rp, u1, X1, Y1);
+                ok1 = near_sum_hilo_lat(nl, nn, u1, dyl, dyl_lo, a.yx_f, X1, Y1);
+            }
         }
         int gx0, gy0, gx1, gy1;
-        pixel_xy(__fmaf_rn(-sx0, a.ipx_f, X0), __fmaf_rn(-sy0, a.ipy_f, Y0), rp.bx, rp.by, gx0, gy0);
-        pixel_xy(__fmaf_rn(-sx1, a.ipx_f, X1), __fmaf_rn(-sy1, a.ipy_f, Y1), rp.bx, rp.by, gx1, gy1);
+        pixel_xy(X0, Y0, rp.bx, rp.by, gx0, gy0);
+        pixel_xy(X1, Y1, rp.bx, rp.by, gx1, gy1);
         if (!ok0) { gx0 = -1; gy0 = -1; ++drop; }
         if (!ok1) { gx1 = -1; gy1 = -1; ++drop; }
         run_step(rs, v0, gx0, gy0, a.map_u32, g.mnx, g.mny);
@@ -477,13 +467,13 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
     const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
     const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
     const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
-    const int nn = stage_near_y(a, nr, yref, near, nlo, lane);
+    const int nn = stage_near_y<true>(a, nr, yref, near, nlo, lane);
     const int64_t j = ts.row0 + lane;
     const bool active = j < ts.rows_end && j >= jb && j <= je;
     const int64_t c2y = j / g.n2y;
     const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
     for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
-        stage_near_x(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
+        stage_near_x<true>(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
         const int64_t i0 = c2x * g.n2x;
         int k0 = 0, k1 = (int)(min(i0 + g.n2x, g.n3x) - i0);
         if (j == jb) k0 = max(k0, (int)max((int64_t)0, ib - i0));
@@ -504,13 +494,13 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
             // against the FP32 rounding of the per-ray r^2)
             bool close = false;
             if (on) {
-                const float tlo = __fmul_rn(__fadd_rn((float)kbeg, a.c0_f), a.l3x_f);
-                const float thi = __fmul_rn(__fadd_rn((float)(kend - 1), a.c0_f), a.l3x_f);
+                const float ulo = __fadd_rn((float)kbeg, a.c0_f);
+                const float uhi = __fadd_rn((float)(kend - 1), a.c0_f);
                 for (int q = 0; q < nn; ++q) {
                     const float4 L = near[q];
-                    const float dy = __fsub_rn(dyl, L.y);
-                    const float dx = fmaxf(0.f, fmaxf(tlo - L.x, L.x - thi));
-                    close |= __fmaf_rn(dx, dx, dy * dy) <= 1.01f * a.rc2 + 1e-30f;
+                    const float dy = __fsub_rn(L.y, dyl);
+                    const float dx = fmaxf(0.f, fmaxf(ulo - L.x, L.x - uhi));
+                    close |= __fmaf_rn(dx, dx, dy * dy) <= 1.01f * a.rc2u + 1e-30f;
                 }
             }
             if (__any_sync(0xffffffffu, close)) {
@@ -536,10 +526,11 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
     }
 }
 
-// Lane offset from a task's first row, l3y * lane rounded once from FP64.
-__device__ __forceinline__ void lane_dy(double l3y, int lane, float &dyl, float &dyl_lo)
+// Lane offset from a task's first row in lattice units, lane * l3y / l3x
+// rounded once from FP64, and its remainder.
+__device__ __forceinline__ void lane_dy(double l3yx, int lane, float &dyl, float &dyl_lo)
 {
-    const double d = (double)lane * l3y;
+    const double d = (double)lane * l3yx;
     dyl = pin((float)d);
     dyl_lo = pin((float)(d - (double)(float)d));
 }
@@ -555,7 +546,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
     unsigned drop = 0;
     unsigned long long pairs = 0, tasks = 0;
     float dyl, dyl_lo;
-    lane_dy(a.g.l3y, lane, dyl, dyl_lo);
+    lane_dy(a.l3yx, lane, dyl, dyl_lo);
     for (;;) {
         bool stop;
         const int64_t t = fetch_task(a, lane, stop);
@@ -614,7 +605,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
                 tasks = 0;
             }
             cur = lo;
-            lane_dy(b.args[cur].g.l3y, lane, dyl, dyl_lo);
+            lane_dy(b.args[cur].l3yx, lane, dyl, dyl_lo);
         }
         shoot_task<P>(b.args[cur], t - b.task_base[cur], near, nlo, lane, dyl, dyl_lo, rs, drop,
                       pairs, tasks);
@@ -669,7 +660,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
         ++tasks;
         const NearRuns nr = near_runs(a, ts.c1x, ts.c1y);
         const double yref = g.ry0 + ((double)ts.row0 + 0.5) * g.l3y;
-        const int nn = stage_near_y(a, nr, yref, near, nlo, lane);
+        const int nn = stage_near_y<false>(a, nr, yref, near, nlo, lane);
         const int64_t j = ts.row0 + lane;
         const bool active = j < ts.rows_end && j >= jb && j <= je;
         const double dyl_d = (double)lane * g.l3y;
@@ -678,7 +669,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
         const int64_t c2y = j / g.n2y;
         const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
         for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
-            stage_near_x(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
+            stage_near_x<false>(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
             if (!active) continue;
             const int64_t i0 = c2x * g.n2x;
             int k0 = 0, k1 = (int)(min(i0 + g.n2x, g.n3x) - i0);
@@ -692,7 +683,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
             for (int k = k0; k < k1; ++k, u += 1.f) {
                 const float t0 = __fmul_rn(u, a.l3x_f);
                 float X, Y, ax, ay, mn;
-                row_eval<P>(rp, t0, X, Y);
+                row_eval<P>(rp, u, X, Y);
                 near_sum_f32(nl, nn, t0, dyl, ax, ay, mn);
                 bool ok = true;
                 if (mn < a.rc2) ok = near_sum_hilo(nl, nn, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
@@ -746,29 +737,29 @@ __global__ void k_trace_mixed(ShootArgs a, const int64_t *__restrict__ idx, int6
     int64_t row0 = c1y * g.n1y + 32 * ((j - c1y * g.n1y) / 32);
     double yref = g.ry0 + ((double)row0 + 0.5) * g.l3y;
     double xnode = g.rx0 + ((double)c2x + 0.5) * g.l2x;
-    const double dyl_d = (double)(j - row0) * g.l3y;
+    const double dyl_d = (double)(j - row0) * a.l3yx;
     const float dyl = (float)dyl_d;
     const float dyl_lo = (float)(dyl_d - (double)dyl);
     float qf = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
     RowPoly<P> rp;
     row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), qf, a, rp);
     float u = __fadd_rn((float)(i - c2x * g.n2x), a.c0_f);
-    float tt = __fmul_rn(u, a.l3x_f);
-    float X, Y, ax, ay, mn;
-    row_eval<P>(rp, tt, X, Y);
+    float X, Y, mn;
+    row_eval<P>(rp, u, X, Y);
     const NearRuns nr = near_runs(a, c1x, c1y);
-    const GlobalNear nl{&a.L, nr, xnode, yref};
+    const GlobalNear nl{&a.L, nr, xnode, yref, a.il3x, a.mpx};
     const int nn = nr.total();
-    near_sum_f32(nl, nn, tt, dyl, ax, ay, mn);
-    int gx, gy;
-    unsigned drop = 0;
-    finish_ray<P>(rp, a, nl, nn, u, tt, dyl, dyl_lo, X, Y, ax, ay, mn, gx, gy, drop);
-    // beta in theta_E from the kernel's own pixel-unit value
+    near_sum_lat(nl, nn, u, dyl, a.yx_f, X, Y, mn);
     bool ok = true;
-    if (mn < a.rc2) ok = near_sum_hilo(nl, nn, u, tt, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
-    float Xf = __fmaf_rn(-ax, a.ipx_f, X), Yf = __fmaf_rn(-ay, a.ipy_f, Y);
-    beta[2 * q] = g.mx0 + ((double)rp.bx + (double)Xf) * g.dpx;
-    beta[2 * q + 1] = g.my0 + ((double)rp.by + (double)Yf) * g.dpy;
+    if (mn < a.rc2u) {
+        row_eval<P>(rp, u, X, Y);
+        ok = near_sum_hilo_lat(nl, nn, u, dyl, dyl_lo, a.yx_f, X, Y);
+    }
+    int gx, gy;
+    pixel_xy(X, Y, rp.bx, rp.by, gx, gy);
+    // beta in theta_E from the kernel's own pixel-unit value
+    beta[2 * q] = g.mx0 + ((double)rp.bx + (double)X) * g.dpx;
+    beta[2 * q + 1] = g.my0 + ((double)rp.by + (double)Y) * g.dpy;
     if (!ok) { pix[2 * q] = -2; pix[2 * q + 1] = -2; }
     else if ((unsigned)gx >= (unsigned)g.mnx || (unsigned)gy >= (unsigned)g.mny) {
         pix[2 * q] = -1; pix[2 * q + 1] = -1;

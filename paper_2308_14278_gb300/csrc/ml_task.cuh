@@ -52,7 +52,10 @@ __device__ __forceinline__ NearRuns near_runs(const ShootArgs &a, int64_t c1x, i
 
 // Task staging common to the mixed kernels: near lens list of the task's
 // level-1 cell as FP32 offsets from the first row (y) and, per level-2
-// column, from the node (x), with their rounding remainders.
+// column, from the node (x), with their rounding remainders.  LAT: offsets in
+// lattice units (divided by l3x) and masses in pixel units (m / (l3x dpx)),
+// for the counting kernels; else theta_E units and plain masses.
+template <bool LAT>
 __device__ __forceinline__ int stage_near_y(const ShootArgs &a, const NearRuns &nr, double yref,
                                             float4 *near, float2 *nlo, int lane)
 {
@@ -61,19 +64,23 @@ __device__ __forceinline__ int stage_near_y(const ShootArgs &a, const NearRuns &
     for (int k = lane; k < nn; k += 32) {
         int32_t idx = nr.index(k);
         double dy = a.L.y[idx] - yref;
+        if (LAT) dy *= a.il3x;
         float hi = (float)dy;
-        near[k] = make_float4(0.f, hi, (float)a.L.m[idx], __int_as_float(idx));
+        const double m = LAT ? a.L.m[idx] * a.mpx : a.L.m[idx];
+        near[k] = make_float4(0.f, hi, (float)m, __int_as_float(idx));
         nlo[k].y = (float)(dy - (double)hi);
     }
     return nn;
 }
 
+template <bool LAT>
 __device__ __forceinline__ void stage_near_x(const ShootArgs &a, int nn, double xnode,
                                              float4 *near, float2 *nlo, int lane)
 {
     __syncwarp();
     for (int k = lane; k < nn; k += 32) {
         double dx = a.L.x[__float_as_int(near[k].w)] - xnode;
+        if (LAT) dx *= a.il3x;
         float hi = (float)dx;
         near[k].x = hi;
         nlo[k].x = (float)(dx - (double)hi);
@@ -96,20 +103,23 @@ __device__ __forceinline__ int64_t fetch_task(const ShootArgs &a, int lane, bool
     return t;
 }
 
-// Near records computed from the FP64 lens table, for tracing single rays.
+// Near records computed from the FP64 lens table, for single rays: theta_E
+// units (sc = msc = 1) or lattice units (sc = 1/l3x, msc = 1/(l3x dpx)), the
+// values stage_near_y/x produce.
 struct GlobalNear {
     const LensTable *L;
     NearRuns nr;
-    double xnode, yref;
+    double xnode, yref, sc, msc;
     __device__ __forceinline__ float4 rec(int k) const
     {
         int32_t id = nr.index(k);
-        return make_float4((float)(L->x[id] - xnode), (float)(L->y[id] - yref), (float)L->m[id], 0.f);
+        return make_float4((float)((L->x[id] - xnode) * sc), (float)((L->y[id] - yref) * sc),
+                           (float)(L->m[id] * msc), 0.f);
     }
     __device__ __forceinline__ float2 lo(int k) const
     {
         int32_t id = nr.index(k);
-        double dx = L->x[id] - xnode, dy = L->y[id] - yref;
+        double dx = (L->x[id] - xnode) * sc, dy = (L->y[id] - yref) * sc;
         return make_float2((float)(dx - (double)(float)dx), (float)(dy - (double)(float)dy));
     }
 };
