@@ -53,8 +53,9 @@ struct ml_field {
     std::vector<double> worst;       // truncation bound per Taylor order (worst level-1 cell)
     // device buffers
     double *d_x = nullptr, *d_y = nullptr, *d_m = nullptr;
-    int32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr, *d_cursor = nullptr;
+    int32_t *d_cell = nullptr, *d_count = nullptr, *d_start = nullptr;
     double *d_sx = nullptr, *d_sy = nullptr, *d_sm = nullptr;
+    float *d_f32 = nullptr;          // FP32 copies of the sorted lenses (LensTable xh..mf)
     int32_t *d_scell = nullptr;
     int32_t *d_perm = nullptr;       // sorted position -> index in the caller's lens arrays
     double *d_coef64 = nullptr;
@@ -90,6 +91,7 @@ struct ml_field {
     {
         LensTable L;
         L.x = d_sx; L.y = d_sy; L.m = d_sm; L.cell = d_scell; L.start = d_start; L.n = n_lens;
+        set_f32(L, d_f32, n_lens);
         return L;
     }
 };
@@ -394,10 +396,13 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
     if (d.l1_x == 0.0 && d.l1_y == 0.0) { scales.push_back(0.70710678118654752); scales.push_back(0.5); }
     struct Cand { int sx, sy; double l1x, l1y; Geo g; int32_t *cells; int32_t *counts; double *bound; };
     std::vector<Cand> cands;
-    cudaError_t e = cudaSuccess;
+    float *f32 = nullptr;            // FP32 copies of the (unsorted) lenses for the bounds
+    cudaError_t e = cudaMallocAsync((void **)&f32, sizeof(float) * 5 * (size_t)std::max<int64_t>(n, 1), s);
+    if (e == cudaSuccess) e = launch_split_f32(dx, dy, dm, n, f32, s);
     for (double sc : scales)
     for (int a : fine)
         for (int b : coarse) {
+            if (e != cudaSuccess) break;
             Cand c{};
             c.sx = xlong ? a : b;
             c.sy = xlong ? b : a;
@@ -421,6 +426,7 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
             if (e == cudaSuccess) {
                 LensTable L;
                 L.x = dx; L.y = dy; L.m = dm; L.cell = c.cells; L.start = nullptr; L.n = n;
+                set_f32(L, f32, n);
                 c.g.p = 1;
                 e = launch_p_bound(c.g, L, c.bound, s);
             }
@@ -465,6 +471,7 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
         if (c.counts) cudaFreeAsync(c.counts, s);
         if (c.bound) cudaFreeAsync(c.bound, s);
     }
+    if (f32) cudaFreeAsync(f32, s);
     if (e != cudaSuccess) return cuda_fail(e, "grid autotuner");
     out = res;
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -587,12 +594,12 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     ML_CK(f->alloc(&f->d_cell, n, s));
     ML_CK(f->alloc(&f->d_count, NE + 1, s));
     ML_CK(f->alloc(&f->d_start, NE + 2, s));
-    ML_CK(f->alloc(&f->d_cursor, NE + 1, s));
     ML_CK(f->alloc(&f->d_sx, n, s));
     ML_CK(f->alloc(&f->d_sy, n, s));
     ML_CK(f->alloc(&f->d_sm, n, s));
     ML_CK(f->alloc(&f->d_scell, n, s));
     ML_CK(f->alloc(&f->d_perm, n, s));
+    ML_CK(f->alloc(&f->d_f32, 5 * n, s));
     ML_CK(f->alloc(&f->d_stats, 8, s));
     ML_CK(f->alloc(&f->d_sum, 1, s));
     ML_CK(f->alloc(&f->d_work, 1, s));
@@ -605,8 +612,8 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
     ML_CK(launch_lens_cells(g, f->d_x, f->d_y, n, f->d_cell, f->d_count, s));
     ML_CK(launch_scan(f->d_count, f->d_start, NE + 1, s));
-    ML_CK(launch_scatter(f->d_x, f->d_y, f->d_m, f->d_cell, n, f->d_start, NE + 1, f->d_cursor,
-                         f->d_sx, f->d_sy, f->d_sm, f->d_scell, f->d_perm, s));
+    ML_CK(launch_scatter(f->d_x, f->d_y, f->d_m, f->d_cell, n, f->d_start, NE + 1, f->d_sx,
+                         f->d_sy, f->d_sm, f->d_scell, f->d_perm, f->d_f32, s));
     if (!nearfar) return ML_OK;
 
     // largest near list: the 3 x 3 block of each level-1 cell

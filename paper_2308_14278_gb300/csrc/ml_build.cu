@@ -30,8 +30,9 @@ __global__ void k_lens_cells(Geo g, const double *__restrict__ x, const double *
     atomicAdd(&count[c], 1);
 }
 
-// Exclusive scan of nb bucket counts into start[0..nb] by one CTA.
-__global__ void k_scan(const int32_t *__restrict__ count, int32_t *__restrict__ start, int64_t nb)
+// Exclusive scan of nb bucket counts into start[0..nb] by the calling CTA
+// (start[nb] = the total).  count and start may be the same array.
+__device__ void cta_exclusive_scan(const int32_t *count, int32_t *start, int64_t nb)
 {
     __shared__ int32_t warp_tot[32];
     __shared__ int32_t carry;
@@ -66,46 +67,121 @@ __global__ void k_scan(const int32_t *__restrict__ count, int32_t *__restrict__ 
         __syncthreads();
     }
     if (threadIdx.x == 0) start[nb] = carry;
+    __syncthreads();
 }
 
-// Stable scatter by one warp: lenses are taken 32 at a time in index order;
-// lanes with equal buckets get consecutive slots in lane order.
-__global__ void k_scatter(const double *__restrict__ x, const double *__restrict__ y,
-                          const double *__restrict__ m, const int32_t *__restrict__ cell, int64_t n,
-                          const int32_t *__restrict__ start, int64_t nb, int32_t *cursor_g,
-                          double *__restrict__ sx, double *__restrict__ sy,
-                          double *__restrict__ sm, int32_t *__restrict__ scell,
-                          int32_t *__restrict__ perm, int use_smem)
+__global__ void k_scan(const int32_t *__restrict__ count, int32_t *__restrict__ start, int64_t nb)
 {
-    extern __shared__ int32_t cur_s[];
-    int32_t *cur = use_smem ? cur_s : cursor_g;
-    int lane = threadIdx.x;
-    for (int64_t b = lane; b < nb; b += 32) cur[b] = start[b];
+    cta_exclusive_scan(count, start, nb);
+}
+
+// Stable counting-sort placement by one CTA: item k (of [0, n)) with bucket
+// key(k) >= 0 goes to slot start[key] + (number of earlier items with that
+// key); key < 0 items are skipped.  Warp w takes a contiguous chunk of the
+// items; pass 1 counts each warp's items per bucket into its row of cnt
+// (W x nb), pass 2 turns the rows into each warp's first slot per bucket (warp
+// order), pass 3 walks the chunk again and places 32 items at a time, equal
+// keys in lane order.  With start == nullptr the bucket starts are computed
+// here into ostart[0..nb].
+constexpr int SCAT_THREADS = 1024;
+
+template <class Key, class Emit>
+__device__ void cta_stable_scatter(const Key &key, int64_t n, int64_t nb, const int32_t *start,
+                                   int32_t *ostart, int32_t *cnt, const Emit &emit)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int64_t chunk = (n + W - 1) / W;
+    const int64_t kb = min(n, w * chunk), ke = min(n, kb + chunk);
+    int32_t *my = cnt + w * nb;
+    for (int64_t b = lane; b < nb; b += 32) my[b] = 0;
     __syncwarp();
-    for (int64_t base = 0; base < n; base += 32) {
-        int64_t k = base + lane;
-        bool ok = k < n;
-        int32_t c = ok ? cell[k] : -1;
-        unsigned act = __ballot_sync(0xffffffffu, ok);
-        unsigned peers = __match_any_sync(0xffffffffu, c) & act;
-        int rank = __popc(peers & ((1u << lane) - 1u));
-        int leader = __ffs(peers) - 1;
-        int32_t basepos = 0;
-        if (ok && lane == leader) {
-            basepos = cur[c];
-            cur[c] = basepos + __popc(peers);
-        }
-        basepos = __shfl_sync(0xffffffffu, basepos, leader < 0 ? 0 : leader);
-        if (ok) {
-            int32_t pos = basepos + rank;
-            sx[pos] = x[k];
-            sy[pos] = y[k];
-            sm[pos] = m[k];
-            scell[pos] = c;
-            perm[pos] = (int32_t)k;
-        }
+    for (int64_t base = kb; base < ke; base += 32) {
+        const int64_t k = base + lane;
+        const int32_t c = k < ke ? key(k) : -1;
+        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+        const unsigned peers = __match_any_sync(0xffffffffu, c) & act;
+        if (c >= 0 && lane == __ffs(peers) - 1) my[c] += __popc(peers);
         __syncwarp();
     }
+    __syncthreads();
+    if (start == nullptr) {
+        for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+            int32_t t = 0;
+            for (int q = 0; q < W; ++q) t += cnt[q * nb + b];
+            ostart[b] = t;
+        }
+        __syncthreads();
+        cta_exclusive_scan(ostart, ostart, nb);
+        start = ostart;
+    }
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+        int32_t run = start[b];
+        for (int q = 0; q < W; ++q) {
+            const int32_t t = cnt[q * nb + b];
+            cnt[q * nb + b] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    for (int64_t base = kb; base < ke; base += 32) {
+        const int64_t k = base + lane;
+        const int32_t c = k < ke ? key(k) : -1;
+        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+        const unsigned peers = __match_any_sync(0xffffffffu, c) & act;
+        const int leader = __ffs(peers) - 1;
+        int32_t pos0 = 0;
+        if (c >= 0 && lane == leader) {
+            pos0 = my[c];
+            my[c] = pos0 + __popc(peers);
+        }
+        pos0 = __shfl_sync(0xffffffffu, pos0, leader < 0 ? 0 : leader);
+        if (c >= 0) emit(k, pos0 + __popc(peers & ((1u << lane) - 1u)));
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void split_f32(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+struct CellKey {
+    const int32_t *cell;
+    __device__ int32_t operator()(int64_t k) const { return cell[k]; }
+};
+
+// The sorted lens table: lenses by extended level-1 cell, stable in input order.
+__global__ void __launch_bounds__(SCAT_THREADS) k_scatter(const double *__restrict__ x, const double *__restrict__ y,
+                          const double *__restrict__ m, const int32_t *__restrict__ cell, int64_t n,
+                          const int32_t *__restrict__ start, int64_t nb, int32_t *cnt,
+                          double *__restrict__ sx, double *__restrict__ sy,
+                          double *__restrict__ sm, int32_t *__restrict__ scell,
+                          int32_t *__restrict__ perm, float *__restrict__ f32)
+{
+    auto emit = [&](int64_t k, int32_t pos) {
+        const double xv = x[k], yv = y[k], mv = m[k];
+        sx[pos] = xv;
+        sy[pos] = yv;
+        sm[pos] = mv;
+        scell[pos] = cell[k];
+        perm[pos] = (int32_t)k;
+        split_f32(xv, f32[pos], f32[n + pos]);
+        split_f32(yv, f32[2 * n + pos], f32[3 * n + pos]);
+        f32[4 * n + pos] = (float)mv;
+    };
+    cta_stable_scatter(CellKey{cell}, n, nb, start, nullptr, cnt, emit);
+}
+
+// FP32 copies of unsorted lenses (the autotuner's bound evaluations).
+__global__ void k_split_f32(const double *__restrict__ x, const double *__restrict__ y,
+                            const double *__restrict__ m, int64_t n, float *__restrict__ f32)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    split_f32(x[k], f32[k], f32[n + k]);
+    split_f32(y[k], f32[2 * n + k], f32[3 * n + k]);
+    f32[4 * n + k] = (float)m[k];
 }
 
 cudaError_t launch_lens_cells(const Geo &g, const double *x, const double *y, int64_t n,
@@ -124,19 +200,24 @@ cudaError_t launch_scan(const int32_t *count, int32_t *start, int64_t nb, cudaSt
 
 cudaError_t launch_scatter(const double *x, const double *y, const double *m,
                            const int32_t *cell, int64_t n, const int32_t *start, int64_t nb,
-                           int32_t *cursor, double *sx, double *sy, double *sm, int32_t *scell,
-                           int32_t *perm, cudaStream_t s)
+                           double *sx, double *sy, double *sm, int32_t *scell, int32_t *perm,
+                           float *f32, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    size_t smem = (size_t)nb * sizeof(int32_t);
-    int use_smem = smem <= 96 * 1024;
-    if (use_smem && smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_scatter<<<1, 32, use_smem ? smem : 0, s>>>(x, y, m, cell, n, start, nb, cursor, sx, sy, sm,
-                                                 scell, perm, use_smem);
+    int32_t *cnt = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&cnt, sizeof(int32_t) * (size_t)(SCAT_THREADS / 32) * (size_t)nb, s);
+    if (e != cudaSuccess) return e;
+    k_scatter<<<1, SCAT_THREADS, 0, s>>>(x, y, m, cell, n, start, nb, cnt, sx, sy, sm, scell, perm, f32);
+    e = cudaGetLastError();
+    cudaFreeAsync(cnt, s);
+    return e;
+}
+
+cudaError_t launch_split_f32(const double *x, const double *y, const double *m, int64_t n,
+                             float *f32, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_split_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, m, n, f32);
     return cudaGetLastError();
 }
 
@@ -152,43 +233,70 @@ __device__ __forceinline__ bool is_near_cell(int32_t lc, int64_t NEx, int64_t NE
     return (lx - ex <= 1 && ex - lx <= 1 && ly - ey <= 1 && ey - ly <= 1);
 }
 
+// Approximate square root and reciprocal (PTX sqrt.approx / rcp.approx,
+// relative error below 2^-23 for the normal inputs met here).
+__device__ __forceinline__ float sqrt_approx(float v)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Distance from a lens (hi + lo coordinates) to the interval [a, b] (hi + lo
+// ends) along one axis, in FP32: each hi difference is rounded once (relative
+// 2^-24), the lo terms are below 2^-24 of the coordinates.
+__device__ __forceinline__ float gap_hilo(float ph, float pl, float ah, float al, float bh, float bl)
+{
+    const float below = __fadd_rn(__fsub_rn(ah, ph), __fsub_rn(al, pl));
+    const float above = __fadd_rn(__fsub_rn(ph, bh), __fsub_rn(pl, bl));
+    return fmaxf(0.f, fmaxf(below, above));
+}
+
 // bound[c * PMAX + (p - 1)] = sum_{k far} m_k rho^{p+1} / (D_k^{p+1} (D_k - rho))
 // with rho the largest ray-node distance in a level-2 cell and D_k the
 // distance from lens k to the box of the cell's node centres: an upper bound
 // of the truncation error |sum_{n>p} c_n d^n| for every ray of the cell.
+// It only picks p, so it runs in FP32 on hi + lo lens coordinates: D is
+// rounded down by 1e-6 relative (its FP32 error is below 4e-7), rho up by
+// 1e-6, and the sum up by 1e-5 (rounding of the powers and the sums).  The
+// near lenses are the cell's 3 x 3 block: three runs of extended cell ids.
 __global__ void k_p_bound(Geo g, LensTable L, double *__restrict__ bound)
 {
     int64_t c = blockIdx.x;
     int64_t c1x = c % g.N1x, c1y = c / g.N1x;
-    int64_t ex = c1x + 1, ey = c1y + 1, NE = g.NEx * g.NEy;
     int64_t a2x = c1x * g.l2sx, b2x = min((c1x + 1) * (int64_t)g.l2sx, g.N2x) - 1;
     int64_t a2y = c1y * g.l2sy, b2y = min((c1y + 1) * (int64_t)g.l2sy, g.N2y) - 1;
     double x0 = g.rx0 + (a2x + 0.5) * g.l2x, x1 = g.rx0 + (b2x + 0.5) * g.l2x;
     double y0 = g.ry0 + (a2y + 0.5) * g.l2y, y1 = g.ry0 + (b2y + 0.5) * g.l2y;
     double hx = 0.5 * (double)(g.n2x - 1) * g.l3x, hy = 0.5 * (double)(g.n2y - 1) * g.l3y;
-    // the bound is an estimate used to pick p: FP32 is ample (the distances
-    // are formed in FP64 first); rho is rounded up by 1e-6 relative
     const float rho = (float)(sqrt(hx * hx + hy * hy) * (1.0 + 1e-6));
+    float x0h, x0l, x1h, x1l, y0h, y0l, y1h, y1l;
+    x0h = (float)x0; x0l = (float)(x0 - (double)x0h);
+    x1h = (float)x1; x1l = (float)(x1 - (double)x1h);
+    y0h = (float)y0; y0l = (float)(y0 - (double)y0h);
+    y1h = (float)y1; y1l = (float)(y1 - (double)y1h);
+    // extended ids of the near block: rows c1y..c1y+2, columns c1x..c1x+2
+    const int32_t n0 = (int32_t)(c1y * g.NEx + c1x), nstep = (int32_t)g.NEx;
     float acc[PMAX];
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) acc[q] = 0.f;
     for (int64_t k = threadIdx.x; k < L.n; k += blockDim.x) {
-        if (is_near_cell(L.cell[k], g.NEx, NE, ex, ey)) continue;
-        double px = L.x[k], py = L.y[k];
-        float dx = (float)(px < x0 ? x0 - px : (px > x1 ? px - x1 : 0.0));
-        float dy = (float)(py < y0 ? y0 - py : (py > y1 ? py - y1 : 0.0));
-        float D = sqrtf(dx * dx + dy * dy) * (1.f - 1e-6f);
+        const int32_t lc = L.cell[k] - n0;
+        if ((unsigned)lc < 3u || (unsigned)(lc - nstep) < 3u || (unsigned)(lc - 2 * nstep) < 3u) continue;
+        const float dx = gap_hilo(L.xh[k], L.xl[k], x0h, x0l, x1h, x1l);
+        const float dy = gap_hilo(L.yh[k], L.yl[k], y0h, y0l, y1h, y1l);
+        const float D = __fmul_rn(sqrt_approx(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))), 1.f - 1e-6f);
         if (D <= rho) {
 #pragma unroll
             for (int q = 0; q < PMAX; ++q) acc[q] = INFINITY;
             continue;
         }
-        float u = rho / D;
-        float t = (float)L.m[k] * u / (D - rho);  // times u^{p} below, p >= 1
+        const float u = __fmul_rn(rho, rcp_approx(D));
+        float t = __fmul_rn(__fmul_rn(L.mf[k], u), rcp_approx(__fsub_rn(D, rho)));  // times u^{p} below
 #pragma unroll
         for (int q = 0; q < PMAX; ++q) {
-            t *= u;
-            acc[q] += t;
+            t = __fmul_rn(t, u);
+            acc[q] = __fadd_rn(acc[q], t);
         }
     }
     __shared__ float red[PMAX][32];
@@ -354,6 +462,17 @@ struct BinomTable {
 };
 __constant__ BinomTable c_binom = BinomTable();
 
+// The same rounded to FP32, for the FP32 tail orders of the node shift.
+struct BinomTableF {
+    float v[(HP + 1) * (HP + 1)];
+    constexpr BinomTableF() : v()
+    {
+        BinomTable b;
+        for (int i = 0; i < (HP + 1) * (HP + 1); ++i) v[i] = (float)b.v[i];
+    }
+};
+__constant__ BinomTableF c_binomf = BinomTableF();
+
 struct Hier {
     int64_t bxn, byn;                // level-1 cells per box side
     int64_t NBx, NBy;                // boxes across the level-1 grid
@@ -361,19 +480,25 @@ struct Hier {
     double hB;                       // box scale (half-diagonal)
 };
 
+// Box size: the box series costs (boxes) x (lenses) terms and the sub-block
+// series (sub-blocks) x (lenses of a 3 x 3 box block) terms; for lenses
+// spread over the lattice the sum is smallest near 3 sqrt(sub-blocks) boxes
+// (at least 48), and a box is at least one level-1 cell each way.
 __host__ __device__ inline Hier hier_of(const Geo &g)
 {
     Hier h;
-    double s = fmax(fmax(g.l1x, g.l1y), sqrt((double)g.n3x * g.l3x * (double)g.n3y * g.l3y / 48.0));
-    h.bxn = (int64_t)fmax(1.0, floor(s / g.l1x + 0.5));
-    h.byn = (int64_t)fmax(1.0, floor(s / g.l1y + 0.5));
-    h.NBx = (g.N1x + h.bxn - 1) / h.bxn;
-    h.NBy = (g.N1y + h.byn - 1) / h.byn;
     double ar = g.l1x / g.l1y;
     h.nsx = ar >= 1.0 ? (int64_t)fmin((double)g.l2sx, floor(ar + 0.5)) : 1;
     h.nsy = ar < 1.0 ? (int64_t)fmin((double)g.l2sy, floor(1.0 / ar + 0.5)) : 1;
     if (h.nsx < 1) h.nsx = 1;
     if (h.nsy < 1) h.nsy = 1;
+    const double nsub = (double)g.N1x * (double)g.N1y * (double)(h.nsx * h.nsy);
+    const double nbox = fmax(48.0, 3.0 * sqrt(nsub));
+    double s = fmax(fmax(g.l1x, g.l1y), sqrt((double)g.n3x * g.l3x * (double)g.n3y * g.l3y / nbox));
+    h.bxn = (int64_t)fmax(1.0, floor(s / g.l1x + 0.5));
+    h.byn = (int64_t)fmax(1.0, floor(s / g.l1y + 0.5));
+    h.NBx = (g.N1x + h.bxn - 1) / h.bxn;
+    h.NBy = (g.N1y + h.byn - 1) / h.byn;
     h.hB = 0.5 * sqrt((double)(h.bxn * h.bxn) * g.l1x * g.l1x + (double)(h.byn * h.byn) * g.l1y * g.l1y);
     return h;
 }
@@ -394,15 +519,23 @@ __global__ void k_lens_l1(Geo g, LensTable L, int2 *__restrict__ lc)
     lc[k] = make_int2((int)fx, (int)fy);
 }
 
-// Accumulate -(m/h) w^{j+1}, w = h / (z_k - z_c), j = 0..HP, into acc.
-__device__ __forceinline__ void p2l_add(double m, double dx, double dy, double h,
+// Accumulate -(m/h) w^{j+1}, w = h / (z_k - z_c), into acc for j = 0..J,
+// where J ends the lens's series once |w|^{J+1} < 2^-52: the omitted terms
+// add up to less than 2^-52 (m/h) |w| / (1 - |w|), the rounding level of the
+// lens's own leading term (|w| < 0.6 for every lens of a series set).  With
+// |w|^2 = h * inv the condition is J + 1 >= 72.09 / -ln|w|^2; 74 covers the
+// FP32 logarithm.  ih = 1/h.
+__device__ __forceinline__ void p2l_add(double m, double dx, double dy, double h, double ih,
                                         double *ar, double *ai)
 {
     double inv = h / (dx * dx + dy * dy);
     double wr = dx * inv, wi = -dy * inv;
-    double tr = (m / h) * wr, ti = (m / h) * wi;
+    const float lw = __logf((float)(h * inv));
+    const int J = lw < -74.0f / (float)(HP + 1) ? (int)(-74.0f / lw) : HP;
+    double tr = (m * ih) * wr, ti = (m * ih) * wi;
 #pragma unroll
     for (int j = 0; j <= HP; ++j) {
+        if (j > J) break;
         ar[j] -= tr;
         ai[j] -= ti;
         double nr = tr * wr - ti * wi;
@@ -412,21 +545,46 @@ __device__ __forceinline__ void p2l_add(double m, double dx, double dy, double h
     }
 }
 
-// Sum the (HP+1) complex accumulators of a 128-thread block into out (global).
+// Sum the (HP+1) complex accumulators of a 128-thread block into out
+// (global) in a fixed order.  Within a warp, orders 0..31 (64 values) go
+// through a reduce-scatter: at each of five steps a lane keeps the half of
+// its values that its lane bit selects, sends the other half to its partner
+// and adds what it receives, so that lane l ends with the warp's sums of
+// order l (about 64 additions per lane instead of 320 for a shuffle tree per
+// value); order HP takes a shuffle tree.  The warps' sums are then added in
+// warp order.
+static_assert(HP == 32, "block_sum_store's reduce-scatter assumes 33 orders");
 __device__ void block_sum_store(double *ar, double *ai, double *__restrict__ out, double *red)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double v[64];
 #pragma unroll
-    for (int j = 0; j <= HP; ++j) {
-        double vr = ar[j], vi = ai[j];
-        for (int o = 16; o > 0; o >>= 1) {
-            vr += __shfl_down_sync(0xffffffffu, vr, o);
-            vi += __shfl_down_sync(0xffffffffu, vi, o);
+    for (int j = 0; j < 32; ++j) {
+        v[2 * j] = ar[j];
+        v[2 * j + 1] = ai[j];
+    }
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int o = 16 >> st, half = 32 >> st;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double lo = v[i], hi = v[i + half];
+            const double send = upper ? lo : hi;
+            const double keep = upper ? hi : lo;
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
-        if (lane == 0) {
-            red[(wid * (HP + 1) + j) * 2] = vr;
-            red[(wid * (HP + 1) + j) * 2 + 1] = vi;
-        }
+    }
+    double xr = ar[HP], xi = ai[HP];
+    for (int o = 16; o > 0; o >>= 1) {
+        xr += __shfl_xor_sync(0xffffffffu, xr, o);
+        xi += __shfl_xor_sync(0xffffffffu, xi, o);
+    }
+    red[(wid * (HP + 1) + lane) * 2] = v[0];
+    red[(wid * (HP + 1) + lane) * 2 + 1] = v[1];
+    if (lane == 0) {
+        red[(wid * (HP + 1) + HP) * 2] = xr;
+        red[(wid * (HP + 1) + HP) * 2 + 1] = xi;
     }
     __syncthreads();
     for (int j = threadIdx.x; j <= HP; j += blockDim.x) {
@@ -440,6 +598,33 @@ __device__ void block_sum_store(double *ar, double *ai, double *__restrict__ out
     }
 }
 
+// Lenses outside the binning ring (the last bucket of the sorted table)
+// that lie in some box block: a CSR by box over the box grid extended by one
+// box on each side, stable in table order, so that a sub-block reads just
+// its box block's outer lenses (three runs of bins).
+struct OuterKey {
+    const int2 *lc;
+    Hier h;
+    int64_t k0;
+    __device__ int32_t operator()(int64_t i) const
+    {
+        const int2 c = lc[k0 + i];
+        const int64_t bx = floor_div(c.x, h.bxn), by = floor_div(c.y, h.byn);
+        if (bx < -1 || bx > h.NBx || by < -1 || by > h.NBy) return -1;
+        return (int32_t)((by + 1) * (h.NBx + 2) + (bx + 1));
+    }
+};
+
+__global__ void __launch_bounds__(SCAT_THREADS) k_outer_csr(const int2 *__restrict__ lc, const int32_t *__restrict__ start,
+                                                            int64_t NE, Hier h, int32_t *cnt, int32_t *ostart,
+                                                            int32_t *oidx)
+{
+    const int64_t k0 = start[NE], n = start[NE + 1] - k0;
+    const int64_t nb = (h.NBx + 2) * (h.NBy + 2);
+    auto emit = [&](int64_t i, int32_t pos) { oidx[pos] = (int32_t)(k0 + i); };
+    cta_stable_scatter(OuterKey{lc, h, k0}, n, nb, nullptr, ostart, cnt, emit);
+}
+
 // 1. box series from the lenses outside the box's 3 x 3 box block; grid
 // (NB, HPARTS), each block summing one partition of the lenses.
 __global__ void __launch_bounds__(128) k_box_p2l(Geo g, LensTable L, const int2 *__restrict__ lc,
@@ -449,6 +634,7 @@ __global__ void __launch_bounds__(128) k_box_p2l(Geo g, LensTable L, const int2 
     const int64_t b = blockIdx.x, Bx = b % h.NBx, By = b / h.NBx;
     const double zx = g.rx0 + ((double)Bx + 0.5) * (double)h.bxn * g.l1x;
     const double zy = g.ry0 + ((double)By + 0.5) * (double)h.byn * g.l1y;
+    const double ihB = 1.0 / h.hB;
     double ar[HP + 1], ai[HP + 1];
 #pragma unroll
     for (int j = 0; j <= HP; ++j) { ar[j] = 0.0; ai[j] = 0.0; }
@@ -457,7 +643,7 @@ __global__ void __launch_bounds__(128) k_box_p2l(Geo g, LensTable L, const int2 
         int2 c = lc[k];
         int64_t lbx = floor_div(c.x, h.bxn), lby = floor_div(c.y, h.byn);
         if (lbx - Bx <= 1 && Bx - lbx <= 1 && lby - By <= 1 && By - lby <= 1) continue;
-        p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, h.hB, ar, ai);
+        p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, h.hB, ihB, ar, ai);
     }
     block_sum_store(ar, ai, part + (b * HPARTS + blockIdx.y) * (HP + 1) * 2, red);
 }
@@ -466,7 +652,10 @@ __global__ void __launch_bounds__(128) k_box_p2l(Geo g, LensTable L, const int2 
 // lenses in the box block but outside the cell's 3 x 3 block.
 __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 *__restrict__ lc,
                                                  Hier h, const double *__restrict__ part,
-                                                 double *__restrict__ sub)
+                                                 const int32_t *__restrict__ ostart,
+                                                 const int32_t *__restrict__ oidx,
+                                                 double *__restrict__ sub, float *__restrict__ sub32,
+                                                 int32_t *__restrict__ j64)
 {
     __shared__ double red[4 * (HP + 1) * 2];
     __shared__ double A[(HP + 1) * 2];
@@ -483,6 +672,7 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
     const double zy = g.ry0 + (double)cy * g.l1y + 0.5 * (double)(va + vb) * g.l2y;
     const double hs = 0.5 * sqrt((double)((ub - ua) * (ub - ua)) * g.l2x * g.l2x +
                                  (double)((vb - va) * (vb - va)) * g.l2y * g.l2y);
+    const double ihs = 1.0 / hs;
     const int64_t Bx = cx / h.bxn, By = cy / h.byn;
     double ar[HP + 1], ai[HP + 1];
 #pragma unroll
@@ -493,7 +683,6 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
     // bucket) are scanned only when the box block reaches past the ring.
     const int64_t xlo = (Bx - 1) * h.bxn, xhi = (Bx + 2) * h.bxn - 1;
     const int64_t ylo = (By - 1) * h.byn, yhi = (By + 2) * h.byn - 1;
-    const int64_t NE = g.NEx * g.NEy;
     const int64_t rx0 = max(xlo, (int64_t)-1), rx1 = min(xhi, g.N1x);
     const int64_t ry0 = max(ylo, (int64_t)-1), ry1 = min(yhi, g.N1y);
     for (int64_t ry = ry0; ry <= ry1 && rx0 <= rx1; ++ry) {
@@ -505,16 +694,17 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
                 const int64_t lx = lc[k].x;
                 if (lx - cx <= 1 && cx - lx <= 1) continue;
             }
-            p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ar, ai);
+            p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ihs, ar, ai);
         }
     }
     if (xlo < -1 || xhi > g.N1x || ylo < -1 || yhi > g.N1y) {
-        for (int64_t k = L.start[NE] + threadIdx.x; k < L.start[NE + 1]; k += blockDim.x) {
-            const int2 c = lc[k];
-            const int64_t lbx = floor_div(c.x, h.bxn), lby = floor_div(c.y, h.byn);
-            const bool in_box_block = lbx - Bx <= 1 && Bx - lbx <= 1 && lby - By <= 1 && By - lby <= 1;
-            if (!in_box_block) continue;
-            p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ar, ai);
+        const int64_t obx = h.NBx + 2;
+        for (int64_t by = By - 1; by <= By + 1; ++by) {
+            const int64_t b0 = (by + 1) * obx + Bx;          // bins of boxes Bx-1..Bx+1
+            for (int64_t q = ostart[b0] + threadIdx.x; q < ostart[b0 + 3]; q += blockDim.x) {
+                const int32_t k = oidx[q];
+                p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ihs, ar, ai);
+            }
         }
     }
     // box series of this cell's box: sum of the partitions (fixed order)
@@ -546,53 +736,102 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
             vr = nr;
             vi = ni;
         }
-        double sc = pow(rho, (double)j);
-        sub[(s * (HP + 1) + j) * 2] += vr * sc;
-        sub[(s * (HP + 1) + j) * 2 + 1] += vi * sc;
+        double sc = 1.0, rp = rho;           // rho^j by squaring
+        for (int e = j; e > 0; e >>= 1, rp *= rp)
+            if (e & 1) sc *= rp;
+        const double fr = sub[(s * (HP + 1) + j) * 2] + vr * sc;
+        const double fi = sub[(s * (HP + 1) + j) * 2 + 1] + vi * sc;
+        sub[(s * (HP + 1) + j) * 2] = fr;
+        sub[(s * (HP + 1) + j) * 2 + 1] = fi;
+        sub32[(s * (HP + 1) + j) * 2] = (float)fr;
+        sub32[(s * (HP + 1) + j) * 2 + 1] = (float)fi;
+        red[j] = fabs(fr) + fabs(fi);   // red is free after block_sum_store
+    }
+    __syncthreads();
+    // FP64 length of the node's c_0 sum: the orders above j64 add up (in
+    // |re| + |im|) to at most 2^-35 max(|re a_0|, |im a_0|), so their FP32 sum
+    // (error below 2^-19 of that, |e| <= 1) stays under the FP64 rounding of c_0
+    if (threadIdx.x == 0) {
+        const double lim = 2.9103830456733704e-11 * fmax(fabs(sub[s * (HP + 1) * 2]),
+                                                         fabs(sub[s * (HP + 1) * 2 + 1]));
+        double tail = 0.0;
+        int J = HP;
+        while (J > 0 && tail + red[J] <= lim) tail += red[J--];
+        j64[s] = J;
     }
 }
 
-// 3. node coefficients from the sub-block series.
+// 3. node coefficients from the sub-block series.  Index arithmetic in 32
+// bits (level-2 cells per level-1 side and sub-block counts are small), the
+// scales by reciprocals.
 __global__ void __launch_bounds__(128) k_node_shift(Geo g, Hier h, const double *__restrict__ sub,
+                                                   const float *__restrict__ sub32,
+                                                   const int32_t *__restrict__ j64,
                                                    double *__restrict__ coef)
 {
     // node-uniform loop indices: the binomials come from the constant cache
     const double *binom = c_binom.v;
+    const float *binomf = c_binomf.v;
     int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (node >= g.N2x * g.N2y) return;
-    int64_t c2x = node % g.N2x, c2y = node / g.N2x;
-    int64_t cx = c2x / g.l2sx, cy = c2y / g.l2sy;
-    int64_t u = c2x - cx * g.l2sx, v = c2y - cy * g.l2sy;
-    int64_t sa = u * h.nsx / g.l2sx, sbb = v * h.nsy / g.l2sy;
-    int64_t ua = (sa * g.l2sx + h.nsx - 1) / h.nsx, ub = ((sa + 1) * g.l2sx + h.nsx - 1) / h.nsx;
-    int64_t va = (sbb * g.l2sy + h.nsy - 1) / h.nsy, vb = ((sbb + 1) * g.l2sy + h.nsy - 1) / h.nsy;
-    double hs = 0.5 * sqrt((double)((ub - ua) * (ub - ua)) * g.l2x * g.l2x +
-                           (double)((vb - va) * (vb - va)) * g.l2y * g.l2y);
+    const int64_t c2y64 = node / g.N2x;
+    const int c2x = (int)(node - c2y64 * g.N2x), c2y = (int)c2y64;
+    const int l2sx = g.l2sx, l2sy = g.l2sy, nsx = (int)h.nsx, nsy = (int)h.nsy;
+    const int cx = c2x / l2sx, cy = c2y / l2sy;
+    const int u = c2x - cx * l2sx, v = c2y - cy * l2sy;
+    const int sa = u * nsx / l2sx, sbb = v * nsy / l2sy;
+    const int ua = (sa * l2sx + nsx - 1) / nsx, ub = ((sa + 1) * l2sx + nsx - 1) / nsx;
+    const int va = (sbb * l2sy + nsy - 1) / nsy, vb = ((sbb + 1) * l2sy + nsy - 1) / nsy;
+    const double hs = 0.5 * sqrt((double)((ub - ua) * (ub - ua)) * g.l2x * g.l2x +
+                                 (double)((vb - va) * (vb - va)) * g.l2y * g.l2y);
+    const double ihs = 1.0 / hs;
     // e = (z_node - z_s)/hs
-    double er = ((double)u + 0.5 - 0.5 * (double)(ua + ub)) * g.l2x / hs;
-    double ei = ((double)v + 0.5 - 0.5 * (double)(va + vb)) * g.l2y / hs;
-    const int64_t s = (cy * g.N1x + cx) * h.nsx * h.nsy + sbb * h.nsx + sa;
+    const double er = ((double)u + 0.5 - 0.5 * (double)(ua + ub)) * g.l2x * ihs;
+    const double ei = ((double)v + 0.5 - 0.5 * (double)(va + vb)) * g.l2y * ihs;
+    const int64_t s = ((int64_t)cy * g.N1x + cx) * (nsx * nsy) + sbb * nsx + sa;
     const double *a = sub + s * (HP + 1) * 2;
+    const float *af = sub32 + s * (HP + 1) * 2;
     double *out = coef + node * (int64_t)(g.p + 1) * 2;
     // The mixed mode keeps c_1..c_p in FP32 (node records), so they are summed
     // in FP32 there: the shifted series decays (ratio < 0.6), no term cancels
-    // far below the sum.  c_0, the node's far deflection, stays FP64; the FP64
-    // near/far mode takes every order in FP64.
+    // far below the sum.  c_0, the node's far deflection, is FP64 up to order
+    // j64[s] and FP32 above (the sub-block's bound); the FP64 near/far mode
+    // takes c_1..c_p in FP64.
     const bool fp32_tail = g.precision == ML_PREC_MIXED;
-    double hn = 1.0;
-    for (int n = 0; n <= g.p; ++n) {
-        if (n > 0 && fp32_tail) {
-            const float erf = (float)er, eif = (float)ei;
+    const float erf = (float)er, eif = (float)ei;
+    {
+        const int J = j64[s];
+        float tr = 0.f, ti = 0.f;
+        for (int j = HP; j > J; --j) {
+            const float nr = __fmaf_rn(tr, erf, __fmaf_rn(-ti, eif, af[2 * j]));
+            const float ni = __fmaf_rn(tr, eif, __fmaf_rn(ti, erf, af[2 * j + 1]));
+            tr = nr;
+            ti = ni;
+        }
+        double vr = tr, vi = ti;
+        for (int j = J; j >= 0; --j) {
+            const double nr = vr * er - vi * ei + a[2 * j];
+            const double ni = vr * ei + vi * er + a[2 * j + 1];
+            vr = nr;
+            vi = ni;
+        }
+        out[0] = vr;
+        out[1] = vi;
+    }
+    double ihn = 1.0;
+    for (int n = 1; n <= g.p; ++n) {
+        ihn *= ihs;
+        if (fp32_tail) {
             float vr = 0.f, vi = 0.f;
             for (int j = HP; j >= n; --j) {
-                const float c = (float)binom[j * (HP + 1) + n];
-                const float nr = __fmaf_rn(vr, erf, __fmaf_rn(-vi, eif, c * (float)a[2 * j]));
-                const float ni = __fmaf_rn(vr, eif, __fmaf_rn(vi, erf, c * (float)a[2 * j + 1]));
+                const float c = binomf[j * (HP + 1) + n];
+                const float nr = __fmaf_rn(vr, erf, __fmaf_rn(-vi, eif, c * af[2 * j]));
+                const float ni = __fmaf_rn(vr, eif, __fmaf_rn(vi, erf, c * af[2 * j + 1]));
                 vr = nr;
                 vi = ni;
             }
-            out[2 * n] = (double)vr / hn;
-            out[2 * n + 1] = (double)vi / hn;
+            out[2 * n] = (double)vr * ihn;
+            out[2 * n + 1] = (double)vi * ihn;
         } else {
             double vr = 0.0, vi = 0.0;
             for (int j = HP; j >= n; --j) {
@@ -602,18 +841,19 @@ __global__ void __launch_bounds__(128) k_node_shift(Geo g, Hier h, const double 
                 vr = nr;
                 vi = ni;
             }
-            out[2 * n] = vr / hn;
-            out[2 * n + 1] = vi / hn;
+            out[2 * n] = vr * ihn;
+            out[2 * n + 1] = vi * ihn;
         }
-        hn *= hs;
     }
 }
 
+// FP64 box partials and sub-block series, then the FP32 copy of the latter
+// (half a double per value, rounded up).
 size_t hier_scratch_doubles(const Geo &g)
 {
     Hier h = hier_of(g);
     size_t nb = (size_t)(h.NBx * h.NBy), ns = (size_t)(g.N1x * g.N1y * h.nsx * h.nsy);
-    return (nb * HPARTS + ns) * (HP + 1) * 2;
+    return (nb * HPARTS + ns) * (HP + 1) * 2 + (ns * (HP + 1) * 2 + 1) / 2 + (ns + 1) / 2 + 1;
 }
 
 cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64, double *scratch,
@@ -624,17 +864,26 @@ cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64,
     size_t nb = (size_t)(h.NBx * h.NBy), ns = (size_t)(g.N1x * g.N1y * h.nsx * h.nsy);
     double *part = scratch;
     double *sub = scratch + nb * HPARTS * (HP + 1) * 2;
-    int2 *lc = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&lc, sizeof(int2) * (size_t)(L.n > 0 ? L.n : 1), s);
+    float *sub32 = reinterpret_cast<float *>(sub + ns * (HP + 1) * 2);
+    int32_t *j64 = reinterpret_cast<int32_t *>(sub32 + ns * (HP + 1) * 2);
+    // per-lens level-1 cells, then the outer lenses' CSR by box
+    const size_t nl = (size_t)(L.n > 0 ? L.n : 1);
+    const size_t nob = (size_t)((h.NBx + 2) * (h.NBy + 2));
+    const size_t ints = 2 * nl + (nob + 1) + nl + (size_t)(SCAT_THREADS / 32) * nob;
+    int32_t *iw = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&iw, sizeof(int32_t) * ints, s);
     if (e != cudaSuccess) return e;
+    int2 *lc = reinterpret_cast<int2 *>(iw);
+    int32_t *ostart = iw + 2 * nl, *oidx = ostart + nob + 1, *ocnt = oidx + nl;
     if (L.n > 0) k_lens_l1<<<(unsigned)((L.n + 255) / 256), 256, 0, s>>>(g, L, lc);
+    k_outer_csr<<<1, SCAT_THREADS, 0, s>>>(lc, L.start, g.NEx * g.NEy, h, ocnt, ostart, oidx);
     dim3 gb((unsigned)nb, HPARTS);
     k_box_p2l<<<gb, 128, 0, s>>>(g, L, lc, h, part);
-    k_sub_p2l<<<(unsigned)ns, 128, 0, s>>>(g, L, lc, h, part, sub);
+    k_sub_p2l<<<(unsigned)ns, 128, 0, s>>>(g, L, lc, h, part, ostart, oidx, sub, sub32, j64);
     int64_t nn = g.N2x * g.N2y;
-    k_node_shift<<<(unsigned)((nn + 127) / 128), 128, 0, s>>>(g, h, sub, coef64);
+    k_node_shift<<<(unsigned)((nn + 127) / 128), 128, 0, s>>>(g, h, sub, sub32, j64, coef64);
     e = cudaGetLastError();
-    cudaFreeAsync(lc, s);
+    cudaFreeAsync(iw, s);
     return e;
 }
 

@@ -44,6 +44,9 @@ struct LensTable {
     const int32_t *cell;            // extended cell id of each sorted lens, NE for outside
     const int32_t *start;           // NE + 2 offsets: bucket b holds [start[b], start[b+1])
     int64_t n;
+    // FP32 copies for the truncation bound: x = xh + xl and y = yh + yl to
+    // about 2^-48 relative, mf = m rounded
+    const float *xh, *xl, *yh, *yl, *mf;
 };
 
 // Per-node record of the mixed-precision path, stride 24 + 8p bytes:
@@ -107,8 +110,15 @@ cudaError_t launch_lens_cells(const Geo &g, const double *x, const double *y, in
 cudaError_t launch_scan(const int32_t *count, int32_t *start, int64_t nb, cudaStream_t s);
 cudaError_t launch_scatter(const double *x, const double *y, const double *m,
                            const int32_t *cell, int64_t n, const int32_t *start, int64_t nb,
-                           int32_t *cursor, double *sx, double *sy, double *sm, int32_t *scell,
-                           int32_t *perm, cudaStream_t s);
+                           double *sx, double *sy, double *sm, int32_t *scell, int32_t *perm,
+                           float *f32, cudaStream_t s);
+cudaError_t launch_split_f32(const double *x, const double *y, const double *m, int64_t n,
+                             float *f32, cudaStream_t s);
+// FP32 copies of n lenses in one buffer of 5 n floats: xh, xl, yh, yl, mf
+inline void set_f32(LensTable &L, const float *f32, int64_t n)
+{
+    L.xh = f32; L.xl = f32 + n; L.yh = f32 + 2 * n; L.yl = f32 + 3 * n; L.mf = f32 + 4 * n;
+}
 cudaError_t launch_p_bound(const Geo &g, const LensTable &L, double *bound, cudaStream_t s);
 cudaError_t launch_coeffs_direct(const Geo &g, const LensTable &L, double *coef64, cudaStream_t s);
 cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64, double *scratch,
