@@ -270,7 +270,10 @@ __device__ __forceinline__ void flush_run(RunState &rs, int cx, int cy, unsigned
 // lenses (NN known at compile time: records and the lane's dy, dy^2 in
 // registers).  Rays go in pairs; a run's length is the distance between the
 // indices where it starts and ends, so no per-ray counting is needed; one
-// warp vote per pair decides whether any lane's pixel changed.  Per ray the
+// warp vote per pair decides whether any lane's pixel changed, and one flush
+// serves a pair (a second one only when both rays change pixel).  There is
+// one copy of the pair code and none for an odd tail, which keeps the nine
+// specialisations small enough for the instruction cache.  Per ray the
 // arithmetic is exactly near_sum_lat's and row_eval's.
 //
 // Pixels are compared in their raw floor form: the bit pattern r of
@@ -325,19 +328,30 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         ry = (unsigned)__float_as_int(__fadd_rd(Y, 12582912.0f));
     };
     // a close pass redoes the ray from its row polynomial; a failed one (ray
-    // on a lens) sends the ray far outside the map
-    auto close_pass = [&](bool c, float uu, float &X, float &Y) {
-        if (c) {
-            row_eval<P>(rp, uu, X, Y);
-            if (!near_sum_hilo_lat(nl, NN, uu, dyl, dyl_lo, a.yx_f, X, Y)) {
-                X = -1.0e30f;
-                ++drop;
+    // on a lens) sends the ray far outside the map.  One copy of the code for
+    // both rays of a pair (rare path).
+    auto close_pair = [&](bool c0, bool c1, float u0, float &X0, float &Y0, float &X1, float &Y1) {
+#pragma unroll 1
+        for (int r = 0; r < 2; ++r) {
+            const bool c = r ? c1 : c0;
+            if (c) {
+                const float uu = __fadd_rn(u0, (float)r);
+                float X, Y;
+                row_eval<P>(rp, uu, X, Y);
+                if (!near_sum_hilo_lat(nl, NN, uu, dyl, dyl_lo, a.yx_f, X, Y)) {
+                    X = -1.0e30f;
+                    ++drop;
+                }
+                if (r) { X1 = X; Y1 = Y; } else { X0 = X; Y0 = Y; }
             }
         }
     };
 
-    int k = kbeg;
-    for (; k + 1 < kend; k += 2, u += 2.f) {
+    // pairs of rays; after an odd last ray the pair's second ray is the
+    // lattice's next one (index kend), evaluated but never counted: run
+    // lengths are index differences bounded by kend, so a run it starts has
+    // no rays; it takes no close pass
+    for (int k = kbeg; k < kend; k += 2, u += 2.f) {
         const float u1 = __fadd_rn(u, 1.f);
         float X0, Y0, X1, Y1, mn0, mn1;
         row_eval<P>(rp, u, X0, Y0);
@@ -346,10 +360,7 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         near(u1, X1, Y1, mn1);
         if (NN > 0 && CLOSE) {
             const bool c0 = on && mn0 < a.rc2u, c1 = on && mn1 < a.rc2u;
-            if (__ballot_sync(0xffffffffu, c0 || c1)) {
-                close_pass(c0, u, X0, Y0);
-                close_pass(c1, u1, X1, Y1);
-            }
+            if (__ballot_sync(0xffffffffu, c0 || c1)) close_pair(c0, c1 && k + 1 < kend, u, X0, Y0, X1, Y1);
         }
         unsigned rx0, ry0, rx1, ry1;
         raw(X0, Y0, rx0, ry0);
@@ -358,43 +369,16 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         const bool ch0 = on && (rx0 != rcx || ry0 != rcy);
         const bool ch1 = on && (rx1 != rx0 || ry1 != ry0);
         if (__ballot_sync(0xffffffffu, ch0 || ch1)) {
-            if (ch0) {
-                flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(k - kst),
-                          a.map_u32, g.mnx, g.mny);
+            if (ch0 || ch1) {
+                // the current run ends before ray 0 (ch0) or after it (ray 0
+                // continues it); if both changed, ray 0 is a run of its own
+                flush_run(rs, (int)(rcx + offx), (int)(rcy + offy),
+                          rs.cnt + (unsigned)(k - kst) + (ch0 ? 0u : 1u), a.map_u32, g.mnx, g.mny);
                 rs.cnt = 0;
-                kst = k;
-                rcx = rx0;
-                rcy = ry0;
-            }
-            if (ch1) {
-                flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(k + 1 - kst),
-                          a.map_u32, g.mnx, g.mny);
-                rs.cnt = 0;
-                kst = k + 1;
-                rcx = rx1;
-                rcy = ry1;
-            }
-        }
-    }
-    if (k < kend) {                      // odd tail (warp-uniform)
-        float X0, Y0, mn0;
-        row_eval<P>(rp, u, X0, Y0);
-        near(u, X0, Y0, mn0);
-        if (NN > 0 && CLOSE) {
-            const bool c0 = on && mn0 < a.rc2u;
-            if (__ballot_sync(0xffffffffu, c0)) close_pass(c0, u, X0, Y0);
-        }
-        unsigned rx0, ry0;
-        raw(X0, Y0, rx0, ry0);
-        const bool ch0 = on && (rx0 != rcx || ry0 != rcy);
-        if (__ballot_sync(0xffffffffu, ch0)) {
-            if (ch0) {
-                flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(k - kst),
-                          a.map_u32, g.mnx, g.mny);
-                rs.cnt = 0;
-                kst = k;
-                rcx = rx0;
-                rcy = ry0;
+                if (ch0 && ch1) flush_run(rs, (int)(rx0 + offx), (int)(ry0 + offy), 1u, a.map_u32, g.mnx, g.mny);
+                kst = ch1 ? k + 1 : k;
+                rcx = ch1 ? rx1 : rx0;
+                rcy = ch1 ? ry1 : ry0;
             }
         }
     }
@@ -505,7 +489,7 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
             }
             if (__any_sync(0xffffffffu, close)) {
                 switch (nn) {
-                case 0: walk_fixed<P, 0, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
+                case 0: walk_fixed<P, 0, false>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
                 case 1: walk_fixed<P, 1, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
                 case 2: walk_fixed<P, 2, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
                 case 3: walk_fixed<P, 3, true>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, rs, drop); break;
