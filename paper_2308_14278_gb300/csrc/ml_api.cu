@@ -4,9 +4,11 @@
 
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -294,37 +296,48 @@ bool rays_inside_sheet(const Geo &g)
 // picoseconds, against the Taylor order P, measured at a fixed level-2 grid
 // on three fields: the paper-scale field (1.36 near lenses per ray) and two
 // of the batched maps (2.36 and 3.29), which also have shorter pixel runs.
-// Fields in between are interpolated linearly in the mean near count,
-// fields outside take the nearest curve.  The grid ranking depends on the
-// differences between orders and their size against the node cost.
+// Below 1.36 the paper-scale field's curve is scaled by what its smaller
+// level-1 cells measured (0.19, 0.37 and 0.73 near lenses per ray: 0.81,
+// 0.83 and 0.875 of it at P = 4, 6 and 8 alike).  Fields in between are
+// interpolated linearly in the mean near count; above the last curve each
+// further near lens adds kCostPairPs.
 constexpr int kCostOrders[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
-constexpr double kCostNear[3] = {1.36, 2.36, 3.29};
-constexpr double kCostPs[3][10] = {
-    {1.13, 1.20, 1.25, 1.32, 1.38, 1.44, 1.58, 1.76, 1.92, 2.40},
-    {1.98, 2.01, 2.07, 2.23, 2.30, 2.45, 2.84, 3.26, 3.53, 4.31},
-    {2.11, 2.18, 2.26, 2.39, 2.50, 2.62, 3.25, 3.72, 4.02, 4.79},
+constexpr int kCostRows = 6;
+constexpr double kCostNear[kCostRows] = {0.19, 0.37, 0.73, 1.36, 2.36, 3.29};
+constexpr double kCost136[10] = {0.837, 0.917, 0.969, 1.04, 1.128, 1.186, 1.335, 1.491, 1.732, 1.978};
+constexpr double kCostLow[3] = {0.81, 0.83, 0.875};
+constexpr double kCostPs[2][10] = {
+    {1.52, 1.604, 1.662, 1.746, 1.824, 1.964, 2.14, 2.331, 2.572, 2.805},
+    {1.757, 1.833, 1.894, 1.966, 2.061, 2.235, 2.423, 2.621, 2.832, 3.087},
 };
+constexpr double kCostPairPs = 0.24;
 
-// Beyond the measured near counts each further near lens adds about this
-// much per ray (the Table-1 fold field: 9 near lenses, 3.8 ps per ray at P = 4).
-constexpr double kCostPairPs = 0.25;
+double cost_row(int r, int q)
+{
+    if (r < 3) return kCost136[q] * kCostLow[r];
+    if (r == 3) return kCost136[q];
+    return kCostPs[r - 4][q];
+}
 
 double ray_cost_ps(int P, double near_per_ray)
 {
     int q = 9;
     for (int i = 0; i < 10; ++i)
         if (kCostOrders[i] >= P) { q = i; break; }
-    if (near_per_ray <= kCostNear[0]) return kCostPs[0][q];
-    if (near_per_ray >= kCostNear[2])
-        return kCostPs[2][q] + (near_per_ray - kCostNear[2]) * kCostPairPs;
-    const int r = near_per_ray < kCostNear[1] ? 0 : 1;
+    if (near_per_ray <= kCostNear[0]) return cost_row(0, q);
+    if (near_per_ray >= kCostNear[kCostRows - 1])
+        return cost_row(kCostRows - 1, q) + (near_per_ray - kCostNear[kCostRows - 1]) * kCostPairPs;
+    int r = 0;
+    while (near_per_ray >= kCostNear[r + 1]) ++r;
     const double f = (near_per_ray - kCostNear[r]) / (kCostNear[r + 1] - kCostNear[r]);
-    return (1.0 - f) * kCostPs[r][q] + f * kCostPs[r + 1][q];
+    return (1.0 - f) * cost_row(r, q) + f * cost_row(r + 1, q);
 }
-// whole field build, nanoseconds per level-2 node and coefficient: the
-// paper-scale field's create time grew by 4.6 ms from the (60, 10), p = 5
-// grid to the (80, 20), p = 4 grid, 3.57e6 more node coefficients
-constexpr double kNodeCostNs = 1.3;
+// Field build, nanoseconds: per level-2 node and coefficient, and per
+// level-1 cell (truncation bound, box and sub-block series); measured as the
+// create time's growth with the node count at a fixed order and with the
+// level-1 cell count (paper-scale map and the Table-1 fold field alike).
+constexpr double kNodeCostNs = 0.12;
+constexpr double kCellCostNs = 400.0;
 
 struct GridChoice {
     int sx = 20, sy = 20, p = 0;
@@ -336,14 +349,15 @@ struct GridChoice {
 // Taylor order its truncation bound needs, and its size.
 struct TuneCand {
     int sx, sy, P;
-    double nodes, rays;
+    double nodes, rays, cells;
     double near_per_ray;            // mean near-list length over the level-1 cells
     double l1x, l1y;                // level-1 size; 0 = Eq. 10's
 };
 
 double cand_cost(const TuneCand &c, int P)
 {
-    return c.rays * ray_cost_ps(P, c.near_per_ray) * 1e-3 + c.nodes * (P + 1) * kNodeCostNs;   // ns
+    return c.rays * ray_cost_ps(P, c.near_per_ray) * 1e-3 + c.nodes * (P + 1) * kNodeCostNs +
+           c.cells * kCellCostNs;   // ns
 }
 
 uint64_t mix64(uint64_t h, uint64_t v)
@@ -389,11 +403,12 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
     ml_status st = derive_geometry(d, hx, hy, g0);
     if (st != ML_OK) return st;
     const bool xlong = g0.l1x >= g0.l1y;
-    static const int fine[] = {20, 40, 60, 80};
+    static const int fine[] = {20, 40, 60, 80, 120, 160};
     static const int coarse[] = {10, 20};
     // level-1 scales: Eq. 10's size unless the caller fixed it
     std::vector<double> scales{1.0};
-    if (d.l1_x == 0.0 && d.l1_y == 0.0) { scales.push_back(0.70710678118654752); scales.push_back(0.5); }
+    if (d.l1_x == 0.0 && d.l1_y == 0.0)
+        for (double sc : {0.70710678118654752, 0.5, 0.35355339059327373}) scales.push_back(sc);
     struct Cand { int sx, sy; double l1x, l1y; Geo g; int32_t *cells; int32_t *counts; double *bound; };
     std::vector<Cand> cands;
     float *f32 = nullptr;            // FP32 copies of the (unsorted) lenses for the bounds
@@ -464,7 +479,8 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
         }
         if (d.macro_mode == ML_MACRO_FOLD) p = std::max(p, 2);
         res.push_back(TuneCand{c.sx, c.sy, mixed_p_supported(p), (double)c.g.N2x * (double)c.g.N2y,
-                               (double)c.g.n3x * (double)c.g.n3y, near_per_ray, c.l1x, c.l1y});
+                               (double)c.g.n3x * (double)c.g.n3y, (double)c.g.N1x * (double)c.g.N1y,
+                               near_per_ray, c.l1x, c.l1y});
     }
     for (Cand &c : cands) {
         if (c.cells) cudaFreeAsync(c.cells, s);
@@ -495,14 +511,72 @@ GridChoice best_single(const std::vector<TuneCand> &cands)
     return best;
 }
 
+ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
+                       const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms);
+
+std::unordered_map<uint64_t, GridChoice> g_measured;   // guarded by g_tune_mu
+
+// The model ranks the candidates; with `measure` its best grid at each of
+// the three best level-1 scales is built and timed (measure_grid) and the
+// fastest by measurement is taken.  The
+// model's error is largest between fields of different kinds (walk lengths,
+// pixel runs), which the measurement settles; its cost, about the build and
+// a fiftieth of one shot per candidate, is paid once per process and field.
 ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
                     const std::vector<double> &hm, const double *dx, const double *dy, const double *dm,
-                    cudaStream_t s, GridChoice &best)
+                    cudaStream_t s, bool measure, GridChoice &best)
 {
     std::vector<TuneCand> cands;
     ml_status st = tune_candidates(d, hx, hy, hm, dx, dy, dm, s, cands);
     if (st != ML_OK) return st;
     best = cands.empty() ? GridChoice() : best_single(cands);
+    if (!measure || cands.size() < 2) return ML_OK;
+    const uint64_t key = tune_key(d, hx, hy, hm);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_measured.find(key);
+        if (it != g_measured.end()) { best = it->second; return ML_OK; }
+    }
+    // the model's best grid at each level-1 scale, best scales first: the
+    // level-1 size moves the near-lens count, where the model is least sure
+    std::vector<size_t> order;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        bool placed = false;
+        for (size_t &j : order)
+            if (cands[j].l1x == cands[i].l1x && cands[j].l1y == cands[i].l1y) {
+                if (cand_cost(cands[i], cands[i].P) < cand_cost(cands[j], cands[j].P)) j = i;
+                placed = true;
+                break;
+            }
+        if (!placed) order.push_back(i);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        return cand_cost(cands[a], cands[a].P) < cand_cost(cands[b], cands[b].P);
+    });
+    double best_est = 0.0;
+    bool found = false;
+    for (size_t i = 0; i < std::min<size_t>(3, order.size()); ++i) {
+        const TuneCand &c = cands[order[i]];
+        double est = 0.0;
+        // a candidate that cannot be built (near lists too long for the
+        // mixed kernel's shared memory, memory) is passed over
+        if (measure_grid(d, hx, hy, hm, c, s, est) != ML_OK) {
+            cudaGetLastError();
+            continue;
+        }
+        if (getenv("ML_TUNE_LOG"))
+            fprintf(stderr, "ml tune: l1 %.4g x %.4g  l2 (%d, %d)  p %d  model %.2f ms  measured %.2f ms\n",
+                    c.l1x, c.l1y, c.sx, c.sy, c.P, cand_cost(c, c.P) * 1e-6, est);
+        if (!found || est < best_est) {
+            found = true;
+            best_est = est;
+            best.sx = c.sx; best.sy = c.sy; best.p = c.P; best.cost = cand_cost(c, c.P);
+            best.l1x = c.l1x; best.l1y = c.l1y;
+        }
+    }
+    g_err.clear();
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_measured[key] = best;
     return ML_OK;
 }
 
@@ -567,7 +641,7 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     }
     if (d->tune && d->precision == ML_PREC_MIXED && d->l2_sub_x == 0 && d->l2_sub_y == 0) {
         GridChoice gc;
-        ml_status st = tune_grid(*d, hx, hy, hm, f->d_x, f->d_y, f->d_m, s, gc);
+        ml_status st = tune_grid(*d, hx, hy, hm, f->d_x, f->d_y, f->d_m, s, true, gc);
         if (st != ML_OK) return st;
         d->l2_sub_x = gc.sx;
         d->l2_sub_y = gc.sy;
@@ -726,6 +800,67 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
     ml_status st = create_plan(d, s, f);
     if (st != ML_OK) return st;
     return create_finish(f, d->precision == ML_PREC_DIRECT64 ? 0 : planned_order(f), s);
+}
+
+// Build a candidate grid's field and time it: the build (host clock, the
+// stream synchronised on both sides) plus a centred slice of rays (CUDA
+// events, after a short untimed range that loads the kernel), scaled to the
+// whole lattice.  The lenses come from the tuner's host copies (the
+// descriptor being built has handed its own pointers over already).
+ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
+                       const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms)
+{
+    ml_field_desc dc = d;
+    dc.lens_x = hx.data();
+    dc.lens_y = hy.data();
+    dc.lens_m = hm.data();
+    dc.n_lens = (int64_t)hx.size();
+    dc.lens_mem_is_device = 0;
+    dc.tune = 0;
+    dc.l2_sub_x = c.sx;
+    dc.l2_sub_y = c.sy;
+    dc.l1_x = c.l1x;
+    dc.l1_y = c.l1y;
+    ml_field *f = new (std::nothrow) ml_field();
+    if (!f) return fail(ML_ERR_OOM, "host allocation failed");
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    ml_status st = ML_OK;
+    cudaError_t ce = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e2);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "grid autotuner");
+    const auto t0 = std::chrono::steady_clock::now();
+    if (st == ML_OK) st = create_impl(&dc, s, f);
+    const double create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (st == ML_OK) {
+        // the time per ray is the slope between slices of n and 2n rays, which
+        // cancels a launch's fixed start and tail
+        const Geo &g = f->g;
+        const uint64_t total = (uint64_t)g.n3x * (uint64_t)g.n3y;
+        const uint64_t n = std::min<uint64_t>(total / 2, std::max<uint64_t>(500000000ull, total / 100));
+        const uint64_t r0 = (total - 2 * n) / 2;
+        const uint64_t warm = std::min<uint64_t>(n, 64ull * (uint64_t)g.n3x);
+        float ms[2] = {0.f, 0.f};
+        st = ml_shoot_rays(f, r0, r0 + warm, s);
+        for (int q = 0; q < 2 && st == ML_OK && n > 0; ++q) {
+            ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess) st = ml_shoot_rays(f, r0, r0 + (q + 1) * n, s);
+            if (st == ML_OK && ce == cudaSuccess) ce = cudaEventRecord(e2, s);
+            if (st == ML_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e2);
+            if (st == ML_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms[q], e1, e2);
+            if (st == ML_OK && ce != cudaSuccess) st = cuda_fail(ce, "grid autotuner");
+        }
+        const double per_ray = n > 0 ? std::max(0.0, (double)(ms[1] - ms[0])) / (double)n : 0.0;
+        if (st == ML_OK) est_ms = create_ms + per_ray * (double)total;
+        if (st == ML_OK && getenv("ML_TUNE_LOG"))
+            fprintf(stderr, "ml tune:   create %.2f ms, %.3g and %.3g of %.3g rays in %.3f and %.3f ms\n",
+                    create_ms, (double)n, (double)(2 * n), (double)total, ms[0], ms[1]);
+    }
+    if (e1) cudaEventDestroy(e1);
+    if (e2) cudaEventDestroy(e2);
+    f->release();
+    delete f;
+    return st;
 }
 
 ShootArgs make_args(const ml_field *f)
@@ -925,7 +1060,7 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
             if (e == cudaSuccess) e = cudaMemcpyAsync(dm, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, s);
         }
         GridChoice best;
-        if (e == cudaSuccess) st = tune_grid(plan[i], hx, hy, hm, dx, dy, dm, s, best);
+        if (e == cudaSuccess) st = tune_grid(plan[i], hx, hy, hm, dx, dy, dm, s, false, best);
         cudaFreeAsync(dx, s);
         cudaFreeAsync(dy, s);
         cudaFreeAsync(dm, s);
