@@ -37,10 +37,11 @@ N_TRACKS, TRACK_SAMPLES, SIGMA_PX = 10, 4096, 0.5
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per ray of the shooting kernel, from the ncu capture summarised in
 # profiles/k_shoot_mixed_paper-map-2e10-ray-slice.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 444.1 MB for 2.0e10 rays, tuned grid (80, 20),
-# p = 4), valid for the kernel sources with these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = 444.141824e6 / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "6d8f64ad", "ml_internal.cuh": "967cb42c", "ml_task.cuh": "99f52f61"}
+# dram__bytes_write.sum = 484.6 MB for 2.0e10 rays, the tuned grid: level-1
+# cells 7.77 x 1.22 theta_E, level-2 (80, 20), p = 4), valid for the kernel
+# sources with these sha1 prefixes only.
+TRAFFIC_BYTES_PER_RAY = 484.646400e6 / 2.0e10
+TRAFFIC_SOURCES = {"ml_shoot.cu": "058c9159", "ml_internal.cuh": "5259d9a3", "ml_task.cuh": "e64790a3"}
 
 
 def traffic_per_launch(rays_per_launch: float):
@@ -76,10 +77,23 @@ def parse():
                          "one independent map per rank (weak scaling)")
     ap.add_argument("--no-tune", action="store_true",
                     help="the paper's level-2 grid (L2 = L1/20) instead of the autotuned one")
+    ap.add_argument("--grid", default="",
+                    help="profiling: fix the grid the autotuner chose, 'L1X,L1Y,SX,SY' (level-1 "
+                         "cell size in theta_E, level-2 subdivisions), instead of tuning again")
     ap.add_argument("--shoot-rays", type=float, default=0,
                     help="profiling: shoot only this many rays (a centred slice of the lattice) "
                          "per step; the default shoots them all")
     return ap.parse_args()
+
+
+def grid_kwargs(args, w):
+    """Field keyword arguments for the grid: the autotuner's (default), the
+    paper's (--no-tune) or a fixed one (--grid, which sets w.l1)."""
+    if not args.grid:
+        return dict(tune=not args.no_tune)
+    l1x, l1y, sx, sy = (float(v) for v in args.grid.split(","))
+    w.l1 = (l1x, l1y)
+    return dict(tune=False, l2_sub=(int(sx), int(sy)))
 
 
 def dist_env():
@@ -170,6 +184,7 @@ def run_ours(args, rank, world, local):
         w = inputs.fold_field(seed=seed, n_rays=args.rays, n_tracks=N_TRACKS)
     else:
         w = inputs.paper_map(seed=seed, n_rays=args.rays, map_px=args.map_px, n_tracks=N_TRACKS)
+    grid_kw = grid_kwargs(args, w)
     counts_buf = (torch.empty((w.map_n[1], w.map_n[0]), dtype=torch.int32, device=f"cuda:{local}")
                   if sharded else None)
     dev = torch.device("cuda", local)
@@ -183,7 +198,7 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
 
     def make_desc(device_lenses: bool, host_lenses=None):
-        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host_lenses, tune=not args.no_tune)
+        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host_lenses, **grid_kw)
         if device_lenses:
             d.lens_x, d.lens_y, d.lens_m = (t.data_ptr() for t in lens_dev)
             d.lens_mem_is_device = 1
@@ -312,7 +327,7 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e(ml, w, torch, dev, stream, tracks, args, flush)
 
     if rank == 0 and not args.no_parity:
-        out["map_l1_vs_oracle"] = parity_stripe(ml, w, stream, tune=not args.no_tune)
+        out["map_l1_vs_oracle"] = parity_stripe(ml, w, stream, grid_kw)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w)
     if dist:
@@ -330,8 +345,10 @@ def e2e(ml, w, torch, dev, stream, tracks, args, flush):
     mu_h = torch.empty((w.map_n[1], w.map_n[0]), dtype=torch.float32).pin_memory().numpy()
     lc_h = torch.empty((N_TRACKS, TRACK_SAMPLES), dtype=torch.float32).pin_memory().numpy()
 
+    grid_kw = grid_kwargs(args, w)
+
     def step():
-        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host, tune=not args.no_tune)
+        d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host, **grid_kw)
         h = ml.ml_field_create(d, stream)
         info = ml.ml_field_info(h)
         ml.ml_shoot_rays(h, 0, info["n_rays_x"] * info["n_rays_y"], stream)
@@ -355,11 +372,11 @@ def e2e(ml, w, torch, dev, stream, tracks, args, flush):
             "d2h_bytes_per_step": int(4 * w.map_n[0] * w.map_n[1] + 4 * N_TRACKS * TRACK_SAMPLES)}
 
 
-def parity_stripe(ml, w, stream, tune=False):
+def parity_stripe(ml, w, stream, grid_kw):
     """Map relative L1 error vs the FP64 oracle on a stripe of 1e6 rays shot
     alone, with the benchmark's level-2 grid."""
     import oracle
-    f = ml.Field(w, precision=ml.PREC_MIXED, tune=tune)
+    f = ml.Field(w, precision=ml.PREC_MIXED, **grid_kw)
     info = f.info
     g = oracle.geometry_of(w, p=info["taylor_p"], l2_sub=info["l2_sub_x"], l2_sub_y=info["l2_sub_y"],
                            l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]))
