@@ -329,6 +329,8 @@ def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_A
         l1 = getattr(w, "l1", None)
     if l1 is not None:
         d.l1_x, d.l1_y = l1
+    if tuple(l2_sub) == (0, 0) and getattr(w, "l2", None):
+        l2_sub = w.l2
     d.l2_sub_x, d.l2_sub_y = l2_sub
     d.tune = 1 if tune else 0
     macro = getattr(w, "macro", None)

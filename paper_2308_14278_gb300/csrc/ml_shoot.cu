@@ -605,6 +605,140 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
 // four pixel centres around it; consecutive rays of a lane that share those
 // four pixels (the macro map compresses x) have their weights summed in
 // registers, and the run is added with four atomics when the quad changes.
+struct CicRun {
+    unsigned qx = 0xFFFFFFFFu, qy = 0xFFFFFFFFu;   // lower-left pixel of the quad
+    unsigned rc = 0;                               // rays of the run
+    float W0 = 0.f, W1 = 0.f, W2 = 0.f, W3 = 0.f;  // summed weights
+    unsigned in = 0, out = 0;
+};
+
+__device__ __forceinline__ void cic_flush(CicRun &r, float *map, unsigned mnx, unsigned mny)
+{
+    if (r.rc == 0) return;
+    bool any = false;
+    // the quad's second column and row, in wrapping 32-bit arithmetic
+    // (qx = 0xFFFFFFFF is the column left of the map, whose neighbour is 0)
+    const unsigned px1 = r.qx + 1u, py1 = r.qy + 1u;
+    const bool x0 = r.qx < mnx, x1 = px1 < mnx, y0 = r.qy < mny, y1 = py1 < mny;
+    if (x0 && y0) { atomicAdd(map + ((size_t)r.qy * mnx + r.qx), r.W0); any = true; }
+    if (x1 && y0) { atomicAdd(map + ((size_t)r.qy * mnx + px1), r.W1); any = true; }
+    if (x0 && y1) { atomicAdd(map + ((size_t)py1 * mnx + r.qx), r.W2); any = true; }
+    if (x1 && y1) { atomicAdd(map + ((size_t)py1 * mnx + px1), r.W3); any = true; }
+    if (any) r.in += r.rc; else r.out += r.rc;
+}
+
+__device__ __forceinline__ void cic_start(CicRun &r, unsigned ix, unsigned iy)
+{
+    r.qx = ix;
+    r.qy = iy;
+    r.W0 = r.W1 = r.W2 = r.W3 = 0.f;
+    r.rc = 0;
+}
+
+__device__ __forceinline__ void cic_add(CicRun &r, float wx, float wy)
+{
+    const float ox = 1.f - wx, oy = 1.f - wy;
+    r.W0 = __fmaf_rn(ox, oy, r.W0);
+    r.W1 = __fmaf_rn(wx, oy, r.W1);
+    r.W2 = __fmaf_rn(ox, wy, r.W2);
+    r.W3 = __fmaf_rn(wx, wy, r.W3);
+    ++r.rc;
+}
+
+// Quad (lower-left pixel) and bilinear weights of a ray at pixel-unit (X, Y)
+// off the row bases.
+__device__ __forceinline__ void cic_quad(const int bx, const int by, float X, float Y, unsigned &ix,
+                                         unsigned &iy, float &wx, float &wy)
+{
+    const float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
+    float flx, fly;
+    const int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
+    wx = __fsub_rn(fx, flx);
+    wy = __fsub_rn(fy, fly);
+    ix = (unsigned)bx + (unsigned)kx;
+    iy = (unsigned)by + (unsigned)ky;
+}
+
+// One level-2 column of the CIC walk when every active lane covers the
+// warp's whole range and the near list has NN <= 4 lenses (in registers).
+// Pairs of rays (the second masked off after an odd last ray), one warp vote
+// per pair before any flush.  Per ray the arithmetic is exactly
+// near_sum_f32's, near_sum_hilo's and row_eval's, as the adjoint recomputes.
+template <int P, int NN>
+__device__ __forceinline__ void cic_walk(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
+                                         int kbeg, int kend, bool on, float dyl, float dyl_lo,
+                                         CicRun &cr, unsigned &drop)
+{
+    float lx[NN > 0 ? NN : 1], lm[NN > 0 ? NN : 1], dy[NN > 0 ? NN : 1], dy2[NN > 0 ? NN : 1];
+#pragma unroll
+    for (int q = 0; q < NN; ++q) {
+        const float4 L = nl.near[q];
+        lx[q] = L.x;
+        lm[q] = L.z;
+        dy[q] = __fsub_rn(dyl, L.y);
+        dy2[q] = __fmul_rn(dy[q], dy[q]);
+    }
+    const unsigned mnx = (unsigned)a.g.mnx, mny = (unsigned)a.g.mny;
+    auto near = [&](float t, float &sx, float &sy, float &mn) {
+        sx = 0.f; sy = 0.f; mn = 3.0e38f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const float dx = __fsub_rn(t, lx[q]);
+            const float r2 = __fmaf_rn(dx, dx, dy2[q]);
+            mn = fminf(mn, r2);
+            const float sv = __fmul_rn(lm[q], rcp_approx(r2));
+            sx = __fmaf_rn(dx, sv, sx);
+            sy = __fmaf_rn(dy[q], sv, sy);
+        }
+    };
+    float u = __fadd_rn((float)kbeg, a.c0_f);
+    for (int k = kbeg; k < kend; k += 2, u += 2.f) {
+        const float u1 = __fadd_rn(u, 1.f);
+        bool v0 = on, v1 = on && k + 1 < kend;
+        const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
+        float X0, Y0, X1, Y1, sx0, sy0, mn0, sx1, sy1, mn1;
+        row_eval<P>(rp, u, X0, Y0);
+        row_eval<P>(rp, u1, X1, Y1);
+        near(t0, sx0, sy0, mn0);
+        near(t1, sx1, sy1, mn1);
+        if (NN > 0) {
+            const bool c0 = v0 && mn0 < a.rc2, c1 = v1 && mn1 < a.rc2;
+            if (__ballot_sync(0xffffffffu, c0 || c1)) {
+                if (c0 && !near_sum_hilo(nl, NN, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx0, sy0)) {
+                    v0 = false;
+                    ++drop;
+                }
+                if (c1 && !near_sum_hilo(nl, NN, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, sx1, sy1)) {
+                    v1 = false;
+                    ++drop;
+                }
+            }
+        }
+        X0 = __fmaf_rn(-sx0, a.ipx_f, X0);
+        Y0 = __fmaf_rn(-sy0, a.ipy_f, Y0);
+        X1 = __fmaf_rn(-sx1, a.ipx_f, X1);
+        Y1 = __fmaf_rn(-sy1, a.ipy_f, Y1);
+        unsigned ix0, iy0, ix1, iy1;
+        float wx0, wy0, wx1, wy1;
+        cic_quad(rp.bx, rp.by, X0, Y0, ix0, iy0, wx0, wy0);
+        cic_quad(rp.bx, rp.by, X1, Y1, ix1, iy1, wx1, wy1);
+        // ray 1 compares with the quad after ray 0
+        const bool ch0 = v0 && (ix0 != cr.qx || iy0 != cr.qy);
+        const bool ch1 = v1 && (ix1 != (v0 ? ix0 : cr.qx) || iy1 != (v0 ? iy0 : cr.qy));
+        const bool any = __ballot_sync(0xffffffffu, ch0 || ch1) != 0u;
+        if (any && ch0) {
+            cic_flush(cr, a.map_f32, mnx, mny);
+            cic_start(cr, ix0, iy0);
+        }
+        if (v0) cic_add(cr, wx0, wy0);
+        if (any && ch1) {
+            cic_flush(cr, a.map_f32, mnx, mny);
+            cic_start(cr, ix1, iy1);
+        }
+        if (v1) cic_add(cr, wx1, wy1);
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mixed_cic(ShootArgs a)
 {
@@ -616,25 +750,13 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
     const Geo &g = a.g;
     const int64_t jb = a.ray_begin / g.n3x, ib = a.ray_begin % g.n3x;
     const int64_t je = (a.ray_end - 1) / g.n3x, ie = (a.ray_end - 1) % g.n3x + 1;
-    unsigned in = 0, out = 0, drop = 0;
+    unsigned drop = 0;
     unsigned long long pairs = 0, tasks = 0;
-    // the lane's run: lower-left pixel of the quad, summed weights, rays
-    unsigned qx = 0xFFFFFFFFu, qy = 0xFFFFFFFFu, rc = 0;
-    float W0 = 0.f, W1 = 0.f, W2 = 0.f, W3 = 0.f;
+    CicRun cr;
     const unsigned mnx = (unsigned)g.mnx, mny = (unsigned)g.mny;
-    auto flush = [&]() {
-        if (rc == 0) return;
-        bool any = false;
-        // the quad's second column and row, in wrapping 32-bit arithmetic
-        // (qx = 0xFFFFFFFF is the column left of the map, whose neighbour is 0)
-        const unsigned px1 = qx + 1u, py1 = qy + 1u;
-        const bool x0 = qx < mnx, x1 = px1 < mnx, y0 = qy < mny, y1 = py1 < mny;
-        if (x0 && y0) { atomicAdd(a.map_f32 + ((size_t)qy * mnx + qx), W0); any = true; }
-        if (x1 && y0) { atomicAdd(a.map_f32 + ((size_t)qy * mnx + px1), W1); any = true; }
-        if (x0 && y1) { atomicAdd(a.map_f32 + ((size_t)py1 * mnx + qx), W2); any = true; }
-        if (x1 && y1) { atomicAdd(a.map_f32 + ((size_t)py1 * mnx + px1), W3); any = true; }
-        if (any) in += rc; else out += rc;
-    };
+    const double dyl_d = (double)lane * g.l3y;
+    const float dyl = pin((float)dyl_d);
+    const float dyl_lo = pin((float)(dyl_d - (double)(float)dyl_d));
     for (;;) {
         bool stop;
         const int64_t t = fetch_task(a, lane, stop);
@@ -647,22 +769,35 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
         const int nn = stage_near_y<false>(a, nr, yref, near, nlo, lane);
         const int64_t j = ts.row0 + lane;
         const bool active = j < ts.rows_end && j >= jb && j <= je;
-        const double dyl_d = (double)lane * g.l3y;
-        const float dyl = (float)dyl_d;
-        const float dyl_lo = (float)(dyl_d - (double)dyl);
         const int64_t c2y = j / g.n2y;
         const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
         for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
             stage_near_x<false>(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
-            if (!active) continue;
             const int64_t i0 = c2x * g.n2x;
             int k0 = 0, k1 = (int)(min(i0 + g.n2x, g.n3x) - i0);
             if (j == jb) k0 = max(k0, (int)max((int64_t)0, ib - i0));
             if (j == je) k1 = min(k1, (int)max((int64_t)0, ie - i0));
-            if (k0 >= k1) continue;
+            if (!active || k0 >= k1) { k0 = 0; k1 = 0; }
+            const int kbeg = __reduce_min_sync(0xffffffffu, k1 > k0 ? k0 : 0x7fffffff);
+            const int kend = __reduce_max_sync(0xffffffffu, k1);
+            if (kbeg >= kend) continue;
             RowPoly<P> rp;
-            row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), q, a, rp);
+            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
             pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
+            const bool on = k1 > k0;
+            const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
+            if (uniform && nn <= 4) {
+                switch (nn) {
+                case 0: cic_walk<P, 0>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, cr, drop); break;
+                case 1: cic_walk<P, 1>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, cr, drop); break;
+                case 2: cic_walk<P, 2>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, cr, drop); break;
+                case 3: cic_walk<P, 3>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, cr, drop); break;
+                default: cic_walk<P, 4>(rp, a, nl, kbeg, kend, on, dyl, dyl_lo, cr, drop); break;
+                }
+                continue;
+            }
+            if (!on) continue;
+            // any near-list length, ragged ranges: one ray at a time
             float u = __fadd_rn((float)k0, a.c0_f);
             for (int k = k0; k < k1; ++k, u += 1.f) {
                 const float t0 = __fmul_rn(u, a.l3x_f);
@@ -674,30 +809,19 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
                 if (!ok) { ++drop; continue; }
                 X = __fmaf_rn(-ax, a.ipx_f, X);
                 Y = __fmaf_rn(-ay, a.ipy_f, Y);
-                float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
-                float flx, fly;
-                int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
-                float wx = __fsub_rn(fx, flx), wy = __fsub_rn(fy, fly);
-                const unsigned ix = (unsigned)rp.bx + (unsigned)kx;
-                const unsigned iy = (unsigned)rp.by + (unsigned)ky;
-                if (ix != qx || iy != qy) {
-                    flush();
-                    qx = ix;
-                    qy = iy;
-                    W0 = W1 = W2 = W3 = 0.f;
-                    rc = 0;
+                unsigned ix, iy;
+                float wx, wy;
+                cic_quad(rp.bx, rp.by, X, Y, ix, iy, wx, wy);
+                if (ix != cr.qx || iy != cr.qy) {
+                    cic_flush(cr, a.map_f32, mnx, mny);
+                    cic_start(cr, ix, iy);
                 }
-                const float ox = 1.f - wx, oy = 1.f - wy;
-                W0 = __fmaf_rn(ox, oy, W0);
-                W1 = __fmaf_rn(wx, oy, W1);
-                W2 = __fmaf_rn(ox, wy, W2);
-                W3 = __fmaf_rn(wx, wy, W3);
-                ++rc;
+                cic_add(cr, wx, wy);
             }
         }
     }
-    flush();
-    flush_stats(a, in, out, drop, pairs, lane == 0 ? tasks : 0, 0u);
+    cic_flush(cr, a.map_f32, mnx, mny);
+    flush_stats(a, cr.in, cr.out, drop, pairs, lane == 0 ? tasks : 0, 0u);
 }
 
 // ---- tracing: the same per-ray arithmetic for listed rays -------------------
