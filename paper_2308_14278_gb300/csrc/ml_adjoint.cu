@@ -46,6 +46,50 @@ namespace ml {
 constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_LPT = 4;                          // lenses per thread per pass
 
+// dLoss/dbeta of one ray from its cloud-in-cell weights: with the ray at
+// pixel coordinates (bx + X, by + Y), weights (1-wx)(1-wy), wx(1-wy),
+// (1-wx)wy, wx wy to the four nearest pixel centres, and
+//   dL/dbeta_x = ipx [(G10 - G00)(1 - wy) + (G11 - G01) wy],
+//   dL/dbeta_y = ipy [(G01 - G00)(1 - wx) + (G11 - G10) wx],
+// ipx = (S_I / S_S) / dpx.  Pixels outside the map contribute nothing.
+// The quad's four dL/dM differences (G1 - G0, G3 - G2, G2 - G0, G3 - G1),
+// pixels outside the map counting 0.
+struct QuadG {
+    float e10, e32, e20, e31;
+};
+
+__device__ __forceinline__ QuadG quad_g(const Geo &g, const float *__restrict__ G, unsigned ix, unsigned iy)
+{
+    float Gv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned px = ix + (unsigned)(q & 1), py = iy + (unsigned)(q >> 1);
+        Gv[q] = (px < (unsigned)g.mnx && py < (unsigned)g.mny) ? __ldg(G + (size_t)py * (unsigned)g.mnx + px)
+                                                               : 0.f;
+    }
+    return QuadG{__fsub_rn(Gv[1], Gv[0]), __fsub_rn(Gv[3], Gv[2]), __fsub_rn(Gv[2], Gv[0]),
+                 __fsub_rn(Gv[3], Gv[1])};
+}
+
+// The two formulas above with a fixed operation order, shared by every
+// adjoint path so that they agree ray by ray.
+__device__ __forceinline__ void quad_dbeta(const QuadG &q, float wx, float wy, float ipx, float ipy,
+                                           float &gbx, float &gby)
+{
+    gbx = __fmul_rn(ipx, __fmaf_rn(q.e32, wy, __fmul_rn(q.e10, __fsub_rn(1.f, wy))));
+    gby = __fmul_rn(ipy, __fmaf_rn(q.e31, wx, __fmul_rn(q.e20, __fsub_rn(1.f, wx))));
+}
+
+__device__ __forceinline__ void cic_dbeta(const Geo &g, const float *__restrict__ G, int bx, int by,
+                                          float X, float Y, float ipx, float ipy, float &gbx,
+                                          float &gby)
+{
+    unsigned ix, iy;
+    float wx, wy;
+    cic_quad(bx, by, X, Y, ix, iy, wx, wy);
+    quad_dbeta(quad_g(g, G, ix, iy), wx, wy, ipx, ipy, gbx, gby);
+}
+
 // Position (pixel units) of ray r by exactly the mixed forward's arithmetic.
 template <int P>
 __device__ __forceinline__ bool forward_ray(const ShootArgs &a, int64_t r, float &X, float &Y, int &bx,
@@ -120,22 +164,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_cic_adjoint_direct(ShootArgs a,
         if (it < g.n3x && r >= a.ray_begin && r < a.ray_end) {
             float X, Y;
             int bxi, byi;
-            if (forward_ray<P>(a, r, X, Y, bxi, byi)) {
-                float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
-                float flx, fly;
-                int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
-                float wx = __fsub_rn(fx, flx), wy = __fsub_rn(fy, fly);
-                unsigned ix = (unsigned)bxi + (unsigned)kx, iy = (unsigned)byi + (unsigned)ky;
-                float Gv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    unsigned px = ix + (unsigned)(q & 1), py = iy + (unsigned)(q >> 1);
-                    Gv[q] = (px < (unsigned)g.mnx && py < (unsigned)g.mny)
-                                ? G[(size_t)py * (unsigned)g.mnx + px] : 0.f;
-                }
-                gbx = ipx * ((Gv[1] - Gv[0]) * (1.f - wy) + (Gv[3] - Gv[2]) * wy);
-                gby = ipy * ((Gv[2] - Gv[0]) * (1.f - wx) + (Gv[3] - Gv[1]) * wx);
-            }
+            if (forward_ray<P>(a, r, X, Y, bxi, byi)) cic_dbeta(g, G, bxi, byi, X, Y, ipx, ipy, gbx, gby);
             tx = g.rx0 + ((double)it + 0.5) * g.l3x;
             ty = refy;
         }
@@ -238,32 +267,6 @@ cudaError_t launch_cic_adjoint_direct(const ShootArgs &a, const float *G, const 
 constexpr int ADJ_BUF = 128;          // buffered rays per warp for the near pass
 constexpr int FAR_THREADS = 256;      // lenses per block of k_adj_far
 constexpr int FAR_NODES = 32;         // nodes per shared-memory tile of k_adj_far
-
-// dLoss/dbeta of one ray from its cloud-in-cell weights: with the ray at
-// pixel coordinates (bx + X, by + Y), weights (1-wx)(1-wy), wx(1-wy),
-// (1-wx)wy, wx wy to the four nearest pixel centres, and
-//   dL/dbeta_x = ipx [(G10 - G00)(1 - wy) + (G11 - G01) wy],
-//   dL/dbeta_y = ipy [(G01 - G00)(1 - wx) + (G11 - G10) wx],
-// ipx = (S_I / S_S) / dpx.  Pixels outside the map contribute nothing.
-__device__ __forceinline__ void cic_dbeta(const Geo &g, const float *__restrict__ G, int bx, int by,
-                                          float X, float Y, float ipx, float ipy, float &gbx,
-                                          float &gby)
-{
-    float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
-    float flx, fly;
-    int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
-    float wx = __fsub_rn(fx, flx), wy = __fsub_rn(fy, fly);
-    unsigned ix = (unsigned)bx + (unsigned)kx, iy = (unsigned)by + (unsigned)ky;
-    float Gv[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        unsigned px = ix + (unsigned)(q & 1), py = iy + (unsigned)(q >> 1);
-        Gv[q] = (px < (unsigned)g.mnx && py < (unsigned)g.mny) ? __ldg(G + (size_t)py * (unsigned)g.mnx + px)
-                                                               : 0.f;
-    }
-    gbx = ipx * ((Gv[1] - Gv[0]) * (1.f - wy) + (Gv[3] - Gv[2]) * wy);
-    gby = ipy * ((Gv[2] - Gv[0]) * (1.f - wx) + (Gv[3] - Gv[1]) * wx);
-}
 
 // Near pass: the buffered rays (x offset from the node, y offset from the
 // task's first row, dL/dbeta) against the task's near lenses.  Lane = (lens
@@ -420,13 +423,64 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
             const int64_t i0 = c2x * g.n2x;
             const int kend = (int)(min(i0 + g.n2x, g.n3x) - i0);
             RowPoly<P> rp;
-            if (active) row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), q, a, rp);
+            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
             float T[2 * (P + 1)];
 #pragma unroll
             for (int n = 0; n < 2 * (P + 1); ++n) T[n] = 0.f;
             float sgx = 0.f, sgy = 0.f, stx = 0.f;
             int nb = 0;
             float u = a.c0_f;
+            if (nn == 0) {
+                // no near lenses (most tasks on fine level-1 cells): rays in
+                // pairs, the forward's arithmetic, and the dL/dM differences
+                // of the lane's current pixel quad, reloaded after a warp
+                // vote when a ray leaves it (quad_dbeta as cic_dbeta)
+                unsigned cqx = 0xFFFFFFFFu, cqy = 0xFFFFFFFFu;
+                auto load_quad = [&](unsigned ix, unsigned iy) {
+                    cqx = ix;
+                    cqy = iy;
+                    return quad_g(g, d.G, ix, iy);
+                };
+                // the cache starts as a real quad (the one whose only pixel
+                // in the map is (0, 0)), with its own values
+                QuadG cq = load_quad(cqx, cqy);
+                auto add_ray = [&](float gbx, float gby, float tt) {
+                    sgx += gbx;
+                    sgy += gby;
+                    stx = __fmaf_rn(gbx, tt, stx);
+                    const float th = __fmul_rn(tt, d.hinv);
+                    float pw = 1.f;
+#pragma unroll
+                    for (int n = 0; n <= P; ++n) {
+                        T[2 * n] = __fmaf_rn(gbx, pw, T[2 * n]);
+                        T[2 * n + 1] = __fmaf_rn(gby, pw, T[2 * n + 1]);
+                        pw = __fmul_rn(pw, th);
+                    }
+                };
+                for (int k = 0; k < kend; k += 2, u += 2.f) {
+                    const bool on1 = active && k + 1 < kend;
+                    const float u1 = __fadd_rn(u, 1.f);
+                    const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
+                    float X0, Y0, X1, Y1;
+                    row_eval<P>(rp, u, X0, Y0);
+                    row_eval<P>(rp, u1, X1, Y1);
+                    // the forward subtracts an empty near sum: X - 0 * ipx = X
+                    unsigned ix0, iy0, ix1, iy1;
+                    float wx0, wy0, wx1, wy1;
+                    cic_quad(rp.bx, rp.by, X0, Y0, ix0, iy0, wx0, wy0);
+                    cic_quad(rp.bx, rp.by, X1, Y1, ix1, iy1, wx1, wy1);
+                    const bool ch0 = active && (ix0 != cqx || iy0 != cqy);
+                    const bool ch1 = on1 && (ix1 != ix0 || iy1 != iy0);
+                    const bool any = __ballot_sync(0xffffffffu, ch0 || ch1) != 0u;
+                    float gx0, gy0, gx1, gy1;
+                    if (any && ch0) cq = load_quad(ix0, iy0);
+                    quad_dbeta(cq, wx0, wy0, d.ipx, d.ipy, gx0, gy0);
+                    if (any && ch1) cq = load_quad(ix1, iy1);
+                    quad_dbeta(cq, wx1, wy1, d.ipx, d.ipy, gx1, gy1);
+                    add_ray(active ? gx0 : 0.f, active ? gy0 : 0.f, t0);
+                    add_ray(on1 ? gx1 : 0.f, on1 ? gy1 : 0.f, t1);
+                }
+            } else
             for (int k = 0; k < kend; ++k, u += 1.f) {
                 const float t0 = __fmul_rn(u, a.l3x_f);
                 float gbx = 0.f, gby = 0.f;

@@ -439,6 +439,20 @@ __device__ __forceinline__ int floor_both(float X, float &fl)
     return __float_as_int(s) - 0x4B400000;
 }
 
+// Quad (lower-left pixel) and bilinear weights of a ray at pixel-unit (X, Y)
+// off the row bases.
+__device__ __forceinline__ void cic_quad(const int bx, const int by, float X, float Y, unsigned &ix,
+                                         unsigned &iy, float &wx, float &wy)
+{
+    const float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
+    float flx, fly;
+    const int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
+    wx = __fsub_rn(fx, flx);
+    wy = __fsub_rn(fy, fly);
+    ix = (unsigned)bx + (unsigned)kx;
+    iy = (unsigned)by + (unsigned)ky;
+}
+
 // Nearest-grid-point pixel coordinates of the ray (Eq. 12 binning), before
 // the bounds check; wrapping 32-bit arithmetic keeps far values out of
 // [0, mnx) x [0, mny).

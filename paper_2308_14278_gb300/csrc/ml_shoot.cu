@@ -645,20 +645,6 @@ __device__ __forceinline__ void cic_add(CicRun &r, float wx, float wy)
     ++r.rc;
 }
 
-// Quad (lower-left pixel) and bilinear weights of a ray at pixel-unit (X, Y)
-// off the row bases.
-__device__ __forceinline__ void cic_quad(const int bx, const int by, float X, float Y, unsigned &ix,
-                                         unsigned &iy, float &wx, float &wy)
-{
-    const float fx = __fsub_rn(X, 0.5f), fy = __fsub_rn(Y, 0.5f);
-    float flx, fly;
-    const int kx = floor_both(fx, flx), ky = floor_both(fy, fly);
-    wx = __fsub_rn(fx, flx);
-    wy = __fsub_rn(fy, fly);
-    ix = (unsigned)bx + (unsigned)kx;
-    iy = (unsigned)by + (unsigned)ky;
-}
-
 // One level-2 column of the CIC walk when every active lane covers the
 // warp's whole range and the near list has NN <= 4 lenses (in registers).
 // Pairs of rays (the second masked off after an odd last ray), one warp vote
