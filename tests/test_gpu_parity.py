@@ -330,3 +330,45 @@ def test_wrapped_count_is_reported(ml):
     f.shoot()
     assert f.stats()["rays_in"] == int(f.counts().to(torch.int64).sum())
     f.close()
+
+
+def test_production_map_1e13_rays(ml):
+    """The full production configuration: 13,000 lognormal lenses, 1e13 rays,
+    a 16384^2 map and the autotuned grid.  Sampled rays and a 1e6-ray stripe
+    against the FP64 oracle; then every ray of the lattice is shot and
+    accounted for (in + out + dropped = 1e13; the map's 64-bit sum equals
+    the in-map count, checked by ml_field_stats); and 10 light curves of 4096
+    samples (Gaussian source, sigma 0.5 px) against the oracle's from the same
+    map."""
+    w = inputs.paper_map(0, n_rays=1e13, map_px=16384)
+    f = _field(ml, w, precision=ml.PREC_MIXED, tune=True)
+    info = f.info
+    g = oracle.geometry_of(w, p=info["taylor_p"], l2_sub=info["l2_sub_x"], l2_sub_y=info["l2_sub_y"],
+                           l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]))
+    _check_geometry(f, g)
+    assert info["far_bound"] <= 1e-7
+    assert abs(g.n_rays - 1e13) <= 1e-5 * 1e13
+    idx = np.unique(np.random.default_rng(13).integers(0, g.n_rays, 20000))
+    beta, _ = f.trace(idx)
+    ref, _ = oracle.beta_direct(g, w.lenses.x, w.lenses.y, w.lenses.m, idx)
+    rel = np.hypot(*(beta.cpu().numpy() - ref).T) / np.maximum(_alpha_ref(g, idx, ref), ALPHA_FLOOR)
+    assert np.max(rel) <= REL_DEFLECTION, np.max(rel)
+    r0 = (g.n3y // 2) * g.n3x + 4321
+    r1 = r0 + 1_000_000
+    f.shoot(r0, r1)
+    got = f.counts().cpu().numpy().astype(np.int64)
+    ref_map, _ = oracle.shoot_direct(g, w.lenses.x, w.lenses.y, w.lenses.m, r0, r1)
+    l1 = np.abs(got - ref_map.astype(np.int64)).sum() / max(1, ref_map.sum())
+    assert l1 <= MAP_L1, l1
+    del got, ref_map
+    f.clear()
+    f.shoot()
+    st = f.stats()
+    assert st["rays_in"] + st["rays_out"] + st["rays_dropped"] == g.n_rays
+    tracks = inputs.tracks(10, g.mnx, g.mny, 4 * 0.5 + 1, seed=21)
+    lc = f.light_curves(tracks, 4096, 0.5).cpu().numpy()
+    counts = f.counts().cpu().numpy().view(np.uint32)
+    assert int(counts.sum(dtype=np.uint64)) == st["rays_in"]
+    f.close()
+    ref_lc = oracle.light_curves_sampled(oracle.magnification(g, counts), tracks, 4096, 0.5)
+    assert np.allclose(lc, ref_lc, rtol=2e-6, atol=1e-6 * np.abs(ref_lc).max())

@@ -330,6 +330,26 @@ def test_light_curves_pins():
     assert np.allclose(lc[0], 0.25 * u - 0.5 * v + 3.0, rtol=0, atol=1e-12)
 
 
+def test_light_curves_sampled_equals_whole_map_convolution():
+    """The per-sample convolution (for production-size maps) against the
+    whole-map one, on tracks that run into the map's edges and corners and
+    past them, at two source sizes: identical to the last bit, since the
+    sums are taken in the same order; and the pins above hold for it too."""
+    rng = np.random.default_rng(4)
+    mu = rng.uniform(0.0, 5.0, (37, 53))
+    tr = np.array([[-3.0, -2.0, 60.0, 41.0], [0.0, 36.9, 52.9, 0.2], [0.4, 0.4, 0.6, 36.6],
+                   [25.0, 18.0, 25.0, 18.0], [52.5, 10.0, 40.0, 36.5]])
+    for sigma in (0.5, 1.3):
+        a = oracle.light_curves(mu, tr, 101, sigma)
+        b = oracle.light_curves_sampled(mu, tr, 101, sigma)
+        assert np.array_equal(a, b)
+    delta = np.zeros((21, 21))
+    delta[10, 10] = 1.0
+    w = oracle.gaussian_taps(0.5)
+    lc = oracle.light_curves_sampled(delta, np.array([[8.5, 10.5, 12.5, 10.5]]), 5, 0.5)
+    assert np.allclose(lc[0], w[2] * w, rtol=0, atol=1e-15)
+
+
 # -- Fold macro model (Eq. 4-6) --------------------------------------------------
 
 FOLD = ("fold", 0.83, 0.05, -0.047)   # kappa_0 of Table 1, d scaled up so that the image plane is small
