@@ -28,6 +28,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 namespace ml {
 
@@ -430,11 +431,28 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
             float sgx = 0.f, sgy = 0.f, stx = 0.f;
             int nb = 0;
             float u = a.c0_f;
-            if (nn == 0) {
-                // no near lenses (most tasks on fine level-1 cells): rays in
-                // pairs, the forward's arithmetic, and the dL/dM differences
-                // of the lane's current pixel quad, reloaded after a warp
-                // vote when a ray leaves it (quad_dbeta as cic_dbeta)
+            // Tasks with at most one near lens (nearly all on fine level-1
+            // cells): rays in pairs with the forward's arithmetic, and the
+            // dL/dM differences of the lane's current pixel quad, reloaded
+            // after a warp vote when a ray leaves it (quad_dbeta as
+            // cic_dbeta).  A near lens is held in registers; its forward terms
+            // are near_sum_f32's and its gradient terms near_pair's, summed
+            // per lane over the column and then over the warp.
+            auto walk = [&](auto nn_c) {
+                constexpr int NN = decltype(nn_c)::value;
+                float lx = 0.f, lm = 0.f, fdy = 0.f, fdy2 = 0.f, lxl = 0.f, gdy = 0.f, gdy2 = 0.f;
+                if (NN == 1) {
+                    const float4 L = near[0];
+                    const float2 lo = nlo[0];
+                    lx = L.x;
+                    lm = L.z;
+                    fdy = __fsub_rn(dyl, L.y);
+                    fdy2 = __fmul_rn(fdy, fdy);
+                    lxl = lo.x;
+                    gdy = __fsub_rn(__fsub_rn(dyl, L.y), lo.y);
+                    gdy2 = __fmul_rn(gdy, gdy);
+                }
+                float nax = 0.f, nay = 0.f, nam = 0.f;
                 unsigned cqx = 0xFFFFFFFFu, cqy = 0xFFFFFFFFu;
                 auto load_quad = [&](unsigned ix, unsigned iy) {
                     cqx = ix;
@@ -457,6 +475,26 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
                         pw = __fmul_rn(pw, th);
                     }
                 };
+                auto near_fwd = [&](float tt, float &X, float &Y, float &r2) {
+                    const float dx = __fsub_rn(tt, lx);
+                    r2 = __fmaf_rn(dx, dx, fdy2);
+                    const float sv = __fmul_rn(lm, rcp_approx(r2));
+                    const float sx = __fmaf_rn(dx, sv, 0.f), sy = __fmaf_rn(fdy, sv, 0.f);
+                    X = __fmaf_rn(-sx, a.ipx_f, X);
+                    Y = __fmaf_rn(-sy, a.ipy_f, Y);
+                };
+                auto near_grad = [&](bool ok, float tt, float gbx, float gby) {
+                    const float dx = __fsub_rn(__fsub_rn(tt, lx), lxl);
+                    const float r2 = __fmaf_rn(dx, dx, gdy2);
+                    const float inv = rcp_approx(r2);
+                    const float tq = __fmul_rn(__fmaf_rn(gbx, dx, __fmul_rn(gby, gdy)), inv);
+                    const float v = -2.f * tq;
+                    if (ok) {
+                        nam += tq;
+                        nax = __fmaf_rn(inv, __fmaf_rn(dx, v, gbx), nax);
+                        nay = __fmaf_rn(inv, __fmaf_rn(gdy, v, gby), nay);
+                    }
+                };
                 for (int k = 0; k < kend; k += 2, u += 2.f) {
                     const bool on1 = active && k + 1 < kend;
                     const float u1 = __fadd_rn(u, 1.f);
@@ -464,22 +502,71 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
                     float X0, Y0, X1, Y1;
                     row_eval<P>(rp, u, X0, Y0);
                     row_eval<P>(rp, u1, X1, Y1);
-                    // the forward subtracts an empty near sum: X - 0 * ipx = X
+                    bool ok0 = active, ok1 = on1;
+                    if (NN == 1) {
+                        const float Xp0 = X0, Yp0 = Y0, Xp1 = X1, Yp1 = Y1;
+                        float r20, r21;
+                        near_fwd(t0, X0, Y0, r20);
+                        near_fwd(t1, X1, Y1, r21);
+                        const bool c0 = ok0 && r20 < a.rc2, c1 = ok1 && r21 < a.rc2;
+                        if (__ballot_sync(0xffffffffu, c0 || c1)) {
+                            if (c0) {
+                                float ax, ay;
+                                ok0 = near_sum_hilo(nl, 1, u, t0, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
+                                X0 = __fmaf_rn(-ax, a.ipx_f, Xp0);
+                                Y0 = __fmaf_rn(-ay, a.ipy_f, Yp0);
+                            }
+                            if (c1) {
+                                float ax, ay;
+                                ok1 = near_sum_hilo(nl, 1, u1, t1, dyl, dyl_lo, a.l3x_f, a.l3x_lo, ax, ay);
+                                X1 = __fmaf_rn(-ax, a.ipx_f, Xp1);
+                                Y1 = __fmaf_rn(-ay, a.ipy_f, Yp1);
+                            }
+                        }
+                    }
                     unsigned ix0, iy0, ix1, iy1;
                     float wx0, wy0, wx1, wy1;
                     cic_quad(rp.bx, rp.by, X0, Y0, ix0, iy0, wx0, wy0);
                     cic_quad(rp.bx, rp.by, X1, Y1, ix1, iy1, wx1, wy1);
-                    const bool ch0 = active && (ix0 != cqx || iy0 != cqy);
-                    const bool ch1 = on1 && (ix1 != ix0 || iy1 != iy0);
+                    // ray 1 compares with the quad after ray 0 (unchanged
+                    // when ray 0 is dropped)
+                    const bool ch0 = ok0 && (ix0 != cqx || iy0 != cqy);
+                    const bool ch1 = ok1 && (ix1 != (ok0 ? ix0 : cqx) || iy1 != (ok0 ? iy0 : cqy));
                     const bool any = __ballot_sync(0xffffffffu, ch0 || ch1) != 0u;
                     float gx0, gy0, gx1, gy1;
                     if (any && ch0) cq = load_quad(ix0, iy0);
                     quad_dbeta(cq, wx0, wy0, d.ipx, d.ipy, gx0, gy0);
                     if (any && ch1) cq = load_quad(ix1, iy1);
                     quad_dbeta(cq, wx1, wy1, d.ipx, d.ipy, gx1, gy1);
-                    add_ray(active ? gx0 : 0.f, active ? gy0 : 0.f, t0);
-                    add_ray(on1 ? gx1 : 0.f, on1 ? gy1 : 0.f, t1);
+                    gx0 = ok0 ? gx0 : 0.f;
+                    gy0 = ok0 ? gy0 : 0.f;
+                    gx1 = ok1 ? gx1 : 0.f;
+                    gy1 = ok1 ? gy1 : 0.f;
+                    add_ray(gx0, gy0, t0);
+                    add_ray(gx1, gy1, t1);
+                    if (NN == 1) {
+                        near_grad(ok0, t0, gx0, gy0);
+                        near_grad(ok1, t1, gx1, gy1);
+                    }
                 }
+                if (NN == 1) {
+                    for (int off = 16; off > 0; off >>= 1) {
+                        nax += __shfl_down_sync(0xffffffffu, nax, off);
+                        nay += __shfl_down_sync(0xffffffffu, nay, off);
+                        nam += __shfl_down_sync(0xffffffffu, nam, off);
+                    }
+                    if (lane == 0) {
+                        acc[0] += (double)nax;
+                        acc[1] += (double)nay;
+                        acc[2] += (double)nam;
+                    }
+                    __syncwarp();
+                }
+            };
+            if (nn == 0) {
+                walk(std::integral_constant<int, 0>{});
+            } else if (nn == 1) {
+                walk(std::integral_constant<int, 1>{});
             } else
             for (int k = 0; k < kend; ++k, u += 1.f) {
                 const float t0 = __fmul_rn(u, a.l3x_f);

@@ -109,3 +109,20 @@ def test_struct_layout_matches_header(tmp_path):
     for T, S in (("ml_field_desc", ml.FieldDesc), ("ml_field_params", ml.FieldParams)):
         for name, _ in S._fields_:
             assert got[(T, name)] == getattr(S, name).offset, (T, name)
+
+
+def test_smoke_field_meets_the_near_far_preconditions():
+    """smoke() runs the mixed mode, which needs every ray inside the sheet's
+    disc (the library refuses the field otherwise): the smoke field's ray
+    rectangle, from the oracle's geometry, lies inside its disc."""
+    import math
+    import sys
+    sys.path.insert(0, ROOT)
+    import __graft_entry__ as entry
+    import oracle
+    w = entry.smoke_workload()
+    g = oracle.geometry_of(w)
+    cx, cy, r = w.sheet[:3]
+    far = max(math.hypot(x - cx, y - cy) for x in (g.rx0, g.rx1) for y in (g.ry0, g.ry1))
+    assert far < r
+    assert 0.01 < g.kappa_star < 0.1 and g.n_rays > 100_000
