@@ -420,6 +420,46 @@ __device__ __forceinline__ void row_eval(const RowPoly<P> &rp, float u, float &X
     Y = y;
 }
 
+// Pairs of FP32 values in one 64-bit register for Blackwell's two-lane FP32
+// instructions (add/fma .f32x2): each lane is rounded exactly as the scalar
+// instruction, so a pair computes the same bits as two scalar operations in
+// one issue slot.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Both lanes rounded toward -inf (the floor trick below, on a pair).
+__device__ __forceinline__ f32x2 add2_rd(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // floor(X) as an int using FP32 adds only.  On this GPU float-to-int
 // conversions issue to the narrow FP64 pipe, which a per-ray conversion
 // saturates.  For |X| < 2^22 the sum X + 1.5 * 2^23 rounded toward -inf is

@@ -307,7 +307,22 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
     const unsigned offx = (unsigned)rp.bx - 0x4B400000u, offy = (unsigned)rp.by - 0x4B400000u;
     unsigned rcx = (unsigned)rs.cx - offx, rcy = (unsigned)rs.cy - offy;   // raw form of the run's pixel
     int kst = kbeg;                      // first ray of the current run in this walk
-    float u = __fadd_rn((float)kbeg, a.c0_f);
+    // the row polynomial as (X, Y) coefficient pairs: a ray's two Horner
+    // chains run as one chain of two-lane FMAs (row_eval's arithmetic)
+    f32x2 C[P + 1];
+#pragma unroll
+    for (int m = 0; m <= P; ++m) C[m] = pack2(rp.X[m], rp.Y[m]);
+    auto poly = [&](f32x2 U) {
+        f32x2 v = C[P];
+#pragma unroll
+        for (int m = P - 1; m >= 0; --m) v = fma2(v, U, C[m]);
+        return v;
+    };
+    const f32x2 MAGIC = pack2(12582912.0f, 12582912.0f), TWO = pack2(2.f, 2.f);
+    const float ub = __fadd_rn((float)kbeg, a.c0_f);
+    f32x2 U0 = pack2(ub, ub);
+    const float ub1 = __fadd_rn(ub, 1.f);
+    f32x2 U1 = pack2(ub1, ub1);
 
     // near sum of one ray added to its pixel position (exactly near_sum_lat's
     // arithmetic)
@@ -324,8 +339,10 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
         }
     };
     auto raw = [&](float X, float Y, unsigned &rx, unsigned &ry) {
-        rx = (unsigned)__float_as_int(__fadd_rd(X, 12582912.0f));
-        ry = (unsigned)__float_as_int(__fadd_rd(Y, 12582912.0f));
+        float fx, fy;
+        unpack2(add2_rd(pack2(X, Y), MAGIC), fx, fy);
+        rx = (unsigned)__float_as_int(fx);
+        ry = (unsigned)__float_as_int(fy);
     };
     // a close pass redoes the ray from its row polynomial; a failed one (ray
     // on a lens) sends the ray far outside the map.  One copy of the code for
@@ -337,7 +354,7 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
             if (c) {
                 const float uu = __fadd_rn(u0, (float)r);
                 float X, Y;
-                row_eval<P>(rp, uu, X, Y);
+                unpack2(poly(pack2(uu, uu)), X, Y);
                 if (!near_sum_hilo_lat(nl, NN, uu, dyl, dyl_lo, a.yx_f, X, Y)) {
                     X = -1.0e30f;
                     ++drop;
@@ -351,11 +368,13 @@ __device__ __forceinline__ void walk_fixed(const RowPoly<P> &rp, const ShootArgs
     // lattice's next one (index kend), evaluated but never counted: run
     // lengths are index differences bounded by kend, so a run it starts has
     // no rays; it takes no close pass
-    for (int k = kbeg; k < kend; k += 2, u += 2.f) {
-        const float u1 = __fadd_rn(u, 1.f);
+    for (int k = kbeg; k < kend; k += 2, U0 = add2(U0, TWO), U1 = add2(U1, TWO)) {
+        float u, u1, uh;
+        unpack2(U0, u, uh);
+        unpack2(U1, u1, uh);
         float X0, Y0, X1, Y1, mn0, mn1;
-        row_eval<P>(rp, u, X0, Y0);
-        row_eval<P>(rp, u1, X1, Y1);
+        unpack2(poly(U0), X0, Y0);
+        unpack2(poly(U1), X1, Y1);
         near(u, X0, Y0, mn0);
         near(u1, X1, Y1, mn1);
         if (NN > 0 && CLOSE) {
