@@ -37,11 +37,11 @@ N_TRACKS, TRACK_SAMPLES, SIGMA_PX = 10, 4096, 0.5
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes per ray of the shooting kernel, from the ncu capture summarised in
 # profiles/k_shoot_mixed_paper-map-2e10-ray-slice.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 483.5 MB for 2.0e10 rays, the tuned grid: level-1
+# dram__bytes_write.sum = 484.2 MB for 2.0e10 rays, the tuned grid: level-1
 # cells 7.77 x 1.22 theta_E, level-2 (80, 20), p = 4), valid for the kernel
 # sources with these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = 483.462400e6 / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "6943d911", "ml_internal.cuh": "ab3da16b", "ml_task.cuh": "e64790a3"}
+TRAFFIC_BYTES_PER_RAY = 484.152832e6 / 2.0e10
+TRAFFIC_SOURCES = {"ml_shoot.cu": "08bfccb7", "ml_internal.cuh": "ab3da16b", "ml_task.cuh": "e64790a3"}
 
 
 def traffic_per_launch(rays_per_launch: float):

@@ -684,6 +684,17 @@ __device__ __forceinline__ void cic_walk(const RowPoly<P> &rp, const ShootArgs &
         dy2[q] = __fmul_rn(dy[q], dy[q]);
     }
     const unsigned mnx = (unsigned)a.g.mnx, mny = (unsigned)a.g.mny;
+    // row polynomial as (X, Y) pairs for two-lane FMAs (row_eval's arithmetic)
+    f32x2 C[P + 1];
+#pragma unroll
+    for (int m = 0; m <= P; ++m) C[m] = pack2(rp.X[m], rp.Y[m]);
+    auto poly = [&](f32x2 U) {
+        f32x2 v = C[P];
+#pragma unroll
+        for (int m = P - 1; m >= 0; --m) v = fma2(v, U, C[m]);
+        return v;
+    };
+    const f32x2 TWO = pack2(2.f, 2.f);
     auto near = [&](float t, float &sx, float &sy, float &mn) {
         sx = 0.f; sy = 0.f; mn = 3.0e38f;
 #pragma unroll
@@ -696,14 +707,17 @@ __device__ __forceinline__ void cic_walk(const RowPoly<P> &rp, const ShootArgs &
             sy = __fmaf_rn(dy[q], sv, sy);
         }
     };
-    float u = __fadd_rn((float)kbeg, a.c0_f);
-    for (int k = kbeg; k < kend; k += 2, u += 2.f) {
-        const float u1 = __fadd_rn(u, 1.f);
+    const float ub = __fadd_rn((float)kbeg, a.c0_f), ub1 = __fadd_rn(ub, 1.f);
+    f32x2 U0 = pack2(ub, ub), U1 = pack2(ub1, ub1);
+    for (int k = kbeg; k < kend; k += 2, U0 = add2(U0, TWO), U1 = add2(U1, TWO)) {
+        float u, u1, uh;
+        unpack2(U0, u, uh);
+        unpack2(U1, u1, uh);
         bool v0 = on, v1 = on && k + 1 < kend;
         const float t0 = __fmul_rn(u, a.l3x_f), t1 = __fmul_rn(u1, a.l3x_f);
         float X0, Y0, X1, Y1, sx0, sy0, mn0, sx1, sy1, mn1;
-        row_eval<P>(rp, u, X0, Y0);
-        row_eval<P>(rp, u1, X1, Y1);
+        unpack2(poly(U0), X0, Y0);
+        unpack2(poly(U1), X1, Y1);
         near(t0, sx0, sy0, mn0);
         near(t1, sx1, sy1, mn1);
         if (NN > 0) {
