@@ -38,6 +38,43 @@ ml_status cuda_fail(cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);           \
     } while (0)
 
+// Abort flags live in mapped pinned host memory.  Pinning memory is an
+// operating-system call that costs far more than a field's other set-up, so
+// the flags come from a process-wide pool of pinned pages (one int per field
+// or batch), reused after release.
+struct FlagPool {
+    std::mutex mu;
+    std::vector<int *> free_slots;
+};
+FlagPool g_flags;
+constexpr int kFlagsPerPage = 1024;
+
+cudaError_t flag_get(int **h, int **d)
+{
+    std::lock_guard<std::mutex> lock(g_flags.mu);
+    if (g_flags.free_slots.empty()) {
+        int *page = nullptr;
+        cudaError_t e = cudaHostAlloc((void **)&page, kFlagsPerPage * sizeof(int),
+                                      cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) return e;
+        for (int i = kFlagsPerPage - 1; i >= 0; --i) g_flags.free_slots.push_back(page + i);
+    }
+    int *slot = g_flags.free_slots.back();
+    cudaError_t e = cudaHostGetDevicePointer((void **)d, slot, 0);
+    if (e != cudaSuccess) return e;
+    g_flags.free_slots.pop_back();
+    *slot = 0;
+    *h = slot;
+    return cudaSuccess;
+}
+
+void flag_put(int *h)
+{
+    if (!h) return;
+    std::lock_guard<std::mutex> lock(g_flags.mu);
+    g_flags.free_slots.push_back(h);
+}
+
 }  // namespace
 
 struct ml_field {
@@ -86,7 +123,7 @@ struct ml_field {
         if (!owned.empty() || h_abort) cudaDeviceSynchronize();
         for (void *p : owned) cudaFree(p);
         owned.clear();
-        if (h_abort) cudaFreeHost(h_abort);
+        flag_put(h_abort);
         h_abort = nullptr;
     }
     LensTable table() const
@@ -604,12 +641,14 @@ ml_status load_lenses(const ml_field_desc &d, std::vector<double> &hx, std::vect
 ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
 {
     ML_CK(cudaGetDevice(&f->device));
-    cudaDeviceProp prop;
-    ML_CK(cudaGetDeviceProperties(&prop, f->device));
-    if (prop.major != 10 || prop.minor != 3)
+    // three attributes, not cudaGetDeviceProperties (which queries them all)
+    int cc_major = 0, cc_minor = 0;
+    ML_CK(cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, f->device));
+    ML_CK(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, f->device));
+    ML_CK(cudaDeviceGetAttribute(&f->num_sms, cudaDevAttrMultiProcessorCount, f->device));
+    if (cc_major != 10 || cc_minor != 3)
         return fail(ML_ERR_CUDA, "this library is built for sm_103a (GB300); device is sm_" +
-                                     std::to_string(prop.major) + std::to_string(prop.minor));
-    f->num_sms = prop.multiProcessorCount;
+                                     std::to_string(cc_major) + std::to_string(cc_minor));
     f->desc = *d_in;
     ml_field_desc *d = &f->desc;
 
@@ -678,9 +717,7 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     ML_CK(f->alloc(&f->d_sum, 1, s));
     ML_CK(f->alloc(&f->d_work, 1, s));
     ML_CK(f->alloc(&f->d_status, 1, s));
-    ML_CK(cudaHostAlloc((void **)&f->h_abort, sizeof(int), cudaHostAllocMapped));
-    *f->h_abort = 0;
-    ML_CK(cudaHostGetDevicePointer((void **)&f->d_abort, f->h_abort, 0));
+    ML_CK(flag_get(&f->h_abort, &f->d_abort));
     ML_CK(cudaMemsetAsync(f->d_count, 0, (NE + 1) * sizeof(int32_t), s));
     ML_CK(cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s));
     ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
@@ -975,7 +1012,7 @@ struct ml_batch {
         exec = nullptr; graph = nullptr; ev_in = ev_out = nullptr; s_int = nullptr;
         for (void *q : owned) cudaFree(q);
         owned.clear();
-        if (h_abort) cudaFreeHost(h_abort);
+        flag_put(h_abort);
         h_abort = nullptr;
         for (ml_field *f : fields) {
             if (!f) continue;
@@ -1147,9 +1184,7 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
     }
     ML_CK(b->alloc(&b->d_status, 1, s));
     ML_CK(b->alloc(&b->d_mu, mu_total, s));
-    ML_CK(cudaHostAlloc((void **)&b->h_abort, sizeof(int), cudaHostAllocMapped));
-    *b->h_abort = 0;
-    ML_CK(cudaHostGetDevicePointer((void **)&b->d_abort, b->h_abort, 0));
+    ML_CK(flag_get(&b->h_abort, &b->d_abort));
     if (tpm > 0) {
         float taps[129];
         b->taps_h = light_curve_taps(sigma_px, taps);
