@@ -118,15 +118,24 @@ typedef struct {
     double map_x0, map_y0, map_x1, map_y1;
     int32_t map_nx, map_ny;
 
-    /* Level grids (§3.2).  l1_x, l1_y zero: Eq. 10 on each side.  l2_sub_x,
-     * l2_sub_y: level-2 cells per level-1 cell along x and y; both zero: the
-     * paper's 20 x 20, or the autotuner's choice when tune is set. */
+    /* Level grids (§3.2).  l1_x, l1_y zero: Eq. 10 on each side (or the
+     * autotuner's size when tune is set).  l2_sub_x, l2_sub_y: level-2 cells
+     * per level-1 cell along x and y; both zero: the paper's 20 x 20, or the
+     * autotuner's choice when tune is set. */
     double l1_x, l1_y;
     int32_t l2_sub_x, l2_sub_y;
     double far_tol;             /* target truncation bound for taylor_p = 0; 0 = 1e-7 */
     uint64_t max_launch_rays;   /* rays per shooting launch; 0 = 2^36 */
-    int32_t tune;               /* 1: pick l2_sub_x, l2_sub_y (and with them p) by the
-                                   built-in cost model when both are zero */
+    int32_t tune;               /* 1, with l2_sub_x = l2_sub_y = 0: the autotuner picks
+                                   the level-2 grid (and with it p) and, unless l1_x or
+                                   l1_y is set, the level-1 size (1, 1/sqrt2, 1/2 or
+                                   1/(2 sqrt2) of Eq. 10's): a cost model ranks 48 grids,
+                                   then the best grid of each of the three best level-1
+                                   sizes is built and timed on slices of rays and the
+                                   fastest is taken.  The far-field bound stays within
+                                   far_tol.  The choice is cached per process for the same
+                                   descriptor and lenses; ML_TUNE_LOG=1 in the environment
+                                   prints the timed candidates. */
     int32_t reserved0;
 
     /* Macro model.  ML_MACRO_LINEAR (0): the constant-(kappa, gamma) form of
@@ -417,7 +426,8 @@ ml_status ml_field_destroy(ml_field *f);
  * ml_batch_create - create n fields from descs[0..n) (ML_PREC_MIXED and
  * ML_DEPOSIT_NGP only).  Each field's Taylor order is planned from its own
  * truncation bound; a field with tune != 0 (and no level-2 subdivision given)
- * first takes the level-2 grid the autotuner's cost model ranks first for it.
+ * first takes the grid the autotuner's cost model ranks first for it (the
+ * model alone: timing every map's candidates would cost more than it saves).
  * Maps of one compiled order share one persistent launch.  With
  * tracks_per_map > 0, `tracks` (host, n x tracks_per_map x 4, map pixel
  * coordinates) are kept on the device for the light curves of each run.
