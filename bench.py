@@ -44,6 +44,14 @@ TRAFFIC_BYTES_PER_RAY = 484.152832e6 / 2.0e10
 TRAFFIC_SOURCES = {"ml_shoot.cu": "08bfccb7", "ml_internal.cuh": "ab3da16b", "ml_task.cuh": "e64790a3"}
 
 
+# The library's kernels in one field build: k_lens_cells, k_scan, k_scatter,
+# k_p_bound, k_lens_l1, k_outer_csr, k_box_p2l, k_sub_p2l, k_node_shift,
+# k_node_finalize.  A step adds the shooting launches, mu and the light curves
+# (the fold step: the two peak kernels; the differentiable step: the CIC
+# forward, mu, and k_adj_rays, k_adj_far, k_adj_unsort).
+BUILD_KERNELS = 10
+
+
 def traffic_per_launch(rays_per_launch: float):
     """Measured DRAM bytes per launch, or None once the kernel has changed."""
     import hashlib
@@ -317,7 +325,8 @@ def run_ours(args, rank, world, local):
         "rays_check": {"in": stats["rays_in"], "out": stats["rays_out"],
                        "dropped": stats["rays_dropped"], "total": n_local,
                        "conserved": n_local == expected_local},
-        "gpu_launches": int(args.steps * (6 + stats["launches"] + 2)),
+        "gpu_launches": int(args.steps * (BUILD_KERNELS + stats["launches"] + 2
+                                          + (2 if args.workload == "fold" else 0))),
     }
     clk_sum = clk.summary()
     if clk_sum:
@@ -670,7 +679,7 @@ def run_differentiable(args, rank, world, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_adj_rays + k_adj_far",
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
-        "gpu_launches": int(args.steps * 14),
+        "gpu_launches": int(args.steps * (BUILD_KERNELS + 2 + 3)),
     }
     clk_sum = clk.summary()
     if clk_sum:
