@@ -39,9 +39,10 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # profiles/k_shoot_mixed_paper-map-2e10-ray-slice.md (dram__bytes_read.sum +
 # dram__bytes_write.sum = 484.2 MB for 2.0e10 rays, the tuned grid: level-1
 # cells 7.77 x 1.22 theta_E, level-2 (80, 20), p = 4), valid for the kernel
-# sources with these sha1 prefixes only.
+# sources whose code (comments and blank space left out, code_hash) has these
+# sha1 prefixes only.
 TRAFFIC_BYTES_PER_RAY = 484.152832e6 / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "08bfccb7", "ml_internal.cuh": "ab3da16b", "ml_task.cuh": "e64790a3"}
+TRAFFIC_SOURCES = {"ml_shoot.cu": "e6acd6aa", "ml_internal.cuh": "d7296fe1", "ml_task.cuh": "3d1d5136"}
 
 
 # The library's kernels in one field build: k_lens_cells, k_scan, k_scatter,
@@ -52,13 +53,22 @@ TRAFFIC_SOURCES = {"ml_shoot.cu": "08bfccb7", "ml_internal.cuh": "ab3da16b", "ml
 BUILD_KERNELS = 10
 
 
+def code_hash(text: str) -> str:
+    """sha1 of a C++/CUDA source's code: comments, blank lines and spacing
+    left out, so that editing a comment does not count as a kernel change."""
+    import hashlib
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    lines = (" ".join(re.sub(r"//.*$", "", ln).split()) for ln in text.splitlines())
+    return hashlib.sha1("\n".join(ln for ln in lines if ln).encode()).hexdigest()
+
+
 def traffic_per_launch(rays_per_launch: float):
     """Measured DRAM bytes per launch, or None once the kernel has changed."""
-    import hashlib
     csrc = os.path.join(ROOT, "paper_2308_14278_gb300", "csrc")
     for name, prefix in TRAFFIC_SOURCES.items():
-        with open(os.path.join(csrc, name), "rb") as fh:
-            if not hashlib.sha1(fh.read()).hexdigest().startswith(prefix):
+        with open(os.path.join(csrc, name)) as fh:
+            if not code_hash(fh.read()).startswith(prefix):
                 return None
     return TRAFFIC_BYTES_PER_RAY * rays_per_launch
 

@@ -267,14 +267,16 @@ __device__ __forceinline__ void flush_run(RunState &rs, int cx, int cy, unsigned
 
 // One level-2 column of a warp's walk when every active lane covers the
 // warp's whole range [kbeg, kend) ("on" lanes) and the near list has NN
-// lenses (NN known at compile time: records and the lane's dy, dy^2 in
-// registers).  Rays go in pairs; a run's length is the distance between the
+// lenses (NN known at compile time: records and the lane's dy^2 and scaled
+// dy in registers).  Rays go in pairs; a run's length is the distance between the
 // indices where it starts and ends, so no per-ray counting is needed; one
 // warp vote per pair decides whether any lane's pixel changed, and one flush
 // serves a pair (a second one only when both rays change pixel).  There is
 // one copy of the pair code and none for an odd tail, which keeps the nine
 // specialisations small enough for the instruction cache.  Per ray the
-// arithmetic is exactly near_sum_lat's and row_eval's.
+// arithmetic is exactly near_sum_lat's and row_eval's; the row polynomial's
+// (X, Y) pair and the floor's round-down add run on two-lane FP32
+// instructions, whose lanes round as the scalar ones.
 //
 // Pixels are compared in their raw floor form: the bit pattern r of
 // X + 1.5 * 2^23 rounded toward -inf, so that pixel = r - 0x4B400000 + base
