@@ -126,3 +126,18 @@ def test_smoke_field_meets_the_near_far_preconditions():
     far = max(math.hypot(x - cx, y - cy) for x in (g.rx0, g.rx1) for y in (g.ry0, g.ry1))
     assert far < r
     assert 0.01 < g.kappa_star < 0.1 and g.n_rays > 100_000
+
+
+def test_bench_traffic_check_ignores_comments():
+    """bench.py keeps its measured DRAM traffic only for the kernel sources it
+    was taken on, compared by a hash of their code: comment and spacing edits
+    keep the hash, a changed operation does not; the committed sources match."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_for_test", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    a = "int f(int x)\n{\n    return x + 1;  // one\n}\n"
+    b = "/* doc */\nint f(int x)\n{\n\n    return   x + 1;  // another comment\n}\n"
+    c = "int f(int x)\n{\n    return x + 2;\n}\n"
+    assert bench.code_hash(a) == bench.code_hash(b) != bench.code_hash(c)
+    assert bench.traffic_per_launch(1e9) is not None
