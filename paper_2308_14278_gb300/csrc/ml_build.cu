@@ -887,18 +887,5 @@ cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64,
     return e;
 }
 
-// Convergence ratios of the two series (for checks): largest |z - z_c| / min
-// distance to a lens of the series' set, over boxes and sub-blocks.
-void hier_ratios(const Geo &g, double *box_ratio, double *sub_ratio)
-{
-    Hier h = hier_of(g);
-    double bw = (double)h.bxn * g.l1x, bh = (double)h.byn * g.l1y;
-    double rb = h.hB + 0.5 * sqrt(g.l2x * g.l2x + g.l2y * g.l2y);
-    *box_ratio = rb / (1.5 * fmin(bw, bh));
-    double sw = ceil((double)g.l2sx / h.nsx) * g.l2x, sh = ceil((double)g.l2sy / h.nsy) * g.l2y;
-    double rs = 0.5 * sqrt(sw * sw + sh * sh) + 0.5 * sqrt(g.l2x * g.l2x + g.l2y * g.l2y);
-    double dmin = fmin(g.l1x + 0.5 * (g.l1x - sw), g.l1y + 0.5 * (g.l1y - sh));
-    *sub_ratio = rs / dmin;
-}
 
 }  // namespace ml
