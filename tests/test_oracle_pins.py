@@ -498,3 +498,66 @@ def test_peaks_of_poisson_noise_are_rare():
     N = np.random.default_rng(3).poisson(1000.0, (200, 300))
     m = oracle.peaks(N)
     assert (m & 1).sum() <= 2 and (m & 2).sum() == 0
+
+
+def test_peak_statistics_by_hand():
+    """The ridge map of the peak pins, binned by hand: the three true peaks sit
+    at j = 5 (d = 5.5 with origin 0, step 1, caustic 0); the seven interior
+    curves scan positions j = 1..10, four of them in [0, 5), one in [5, 6),
+    five in [6, 12).  An edge at exactly d = 5.5 puts j = 5 in the upper bin."""
+    N = np.full((9, 12), 1000, np.int64)
+    N[2:7, 5] = 1300
+    N[1, 9] = 1400
+    N[7, 2] = 1200
+    m = oracle.peaks(N)
+    n, s, p = oracle.peak_statistics(N, m, "x", 0.0, 1.0, 0.0, [0.0, 5.0, 6.0, 12.0])
+    assert list(n) == [0, 3, 0] and list(s) == [0, 3900, 0] and list(p) == [28, 7, 35]
+    n, s, p = oracle.peak_statistics(N, m, "x", 0.0, 1.0, 0.0, [0.0, 5.5, 12.0])
+    assert list(n) == [0, 3] and list(p) == [28, 42]
+    # positions beyond the last edge, or before the first, fall in no bin
+    n, s, p = oracle.peak_statistics(N, m, "x", 0.0, 1.0, 0.0, [6.0, 12.0])
+    assert list(n) == [0] and list(p) == [35]
+    # along y: the curves are the columns, the ridge crosses none of them as a peak
+    n, s, p = oracle.peak_statistics(N, oracle.peaks(N, "y"), "y", 0.0, 1.0, 0.0, [0.0, 9.0])
+    assert list(n) == [0] and list(p) == [10 * 7]
+
+
+def test_peak_statistics_of_periodic_crossings():
+    """Ridges across every curve at every fourth position: the crossings per
+    unit length of curve are exactly 1/(4 step) in each bin spanning whole
+    periods, the mean peak count is the ridge's, and a caustic in the middle of
+    the map folds the two sides onto the same distances."""
+    nx, ny, step = 42, 30, 0.25
+    N = np.full((ny, nx), 1000, np.int64)
+    N[:, 3:40:4] = 1400
+    m = oracle.peaks(N)
+    assert (m & 2).sum() // 2 == 10 * (ny - 2)
+    edges = [1.0 * step, 21.0 * step, 41.0 * step]          # j = 1..20 and 21..40
+    n, s, p = oracle.peak_statistics(N, m, "x", 0.0, step, 0.0, edges)
+    assert list(n) == [5 * (ny - 2)] * 2 and list(p) == [20 * (ny - 2)] * 2
+    assert np.all(n * 4 == p) and np.all(s == 1400 * n)
+    # caustic at the map's centre (x = 21 step): positions j and 41 - j are
+    # equidistant; the ridges at j = 3 + 4k map onto j = 38 - 4k, none of which
+    # is a ridge, so every bin of half-width step gathers exactly one side's peaks
+    c = 21.0 * step
+    half = [k * step for k in range(0, 21)]
+    n2, _, p2 = oracle.peak_statistics(N, m, "x", 0.0, step, c, half)
+    assert int(n2.sum()) == 10 * (ny - 2)
+    assert int(p2.sum()) == 40 * (ny - 2) and np.all(p2 == 2 * (ny - 2))
+
+
+def test_peak_statistics_totals_on_a_noisy_map():
+    """Bins that cover every distance add up to the whole mask: all true
+    peaks, the sum of their counts, and (ny - 2)(nx - 2) positions, along
+    either direction."""
+    rng = np.random.default_rng(11)
+    N = rng.poisson(900.0, (50, 70)).astype(np.int64)
+    N[5:20, 30] += 500
+    N[40, 10:30] += 500
+    for along, (nc, ln) in (("x", (50, 70)), ("y", (70, 50))):
+        m = oracle.peaks(N, along)
+        n, s, p = oracle.peak_statistics(N, m, along, -3.0, 0.1, 1.0, [0.0, 0.5, 2.0, 10.0])
+        tp = (m & 2).astype(bool)
+        assert int(n.sum()) == int(tp.sum()) > 0
+        assert int(s.sum()) == int(N[tp].sum())
+        assert int(p.sum()) == (nc - 2) * (ln - 2)
