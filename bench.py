@@ -51,6 +51,22 @@ TRAFFIC_SOURCES = {"ml_shoot.cu": "e6acd6aa", "ml_internal.cuh": "d7296fe1", "ml
 # (the fold step: the two peak kernels; the differentiable step: the CIC
 # forward, mu, and k_adj_rays, k_adj_far, k_adj_unsort).
 BUILD_KERNELS = 10
+# distance bins of the fold step's peak statistics: beta_x from 0.02 to 63 theta_E,
+# four per decade (the fold map spans beta_x in [0, 40])
+FOLD_DISTANCE_EDGES = [0.02 * 10.0 ** (k / 4.0) for k in range(15)]
+
+
+def fold_peak_summary(stats, info):
+    """Per distance bin: true peaks, crossings per theta_E of curve and the
+    mean peak magnification (Figs. 4-5, before the paper's normalisations)."""
+    n, s, pos = (np.asarray(a, np.float64) for a in stats)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        dens = np.where(pos > 0, n / (pos * info["dpx"]), 0.0)
+        mu = np.where(n > 0, s * info["mu_per_count"] / n, 0.0)
+    return {"edges_theta_e": [round(e, 4) for e in FOLD_DISTANCE_EDGES],
+            "n_peaks": [int(v) for v in stats[0]],
+            "crossings_per_theta_e": [round(float(v), 4) for v in dens],
+            "mean_mu_peak": [round(float(v), 3) for v in mu]}
 
 
 def code_hash(text: str) -> str:
@@ -249,6 +265,9 @@ def run_ours(args, rank, world, local):
         if args.workload == "fold":
             # the paper's light-curve statistics start from the 5 sigma peaks (§4.2)
             info_holder["peaks"] = ml.ml_find_peaks(h, ml.ALONG_X, 5.0, peak_mask, 0, stream)[0]
+            # and bin them by distance beta_x from the caustic (Figs. 4-5)
+            info_holder["peak_stats"] = ml.ml_peak_statistics(h, FOLD_DISTANCE_EDGES, ml.ALONG_X, 0.0,
+                                                              mask=peak_mask, stream=stream)
         if e: e[4].record(stream)
         stats, _ = ml.ml_field_stats(h, stream)
         ml.ml_field_destroy(h)
@@ -331,12 +350,14 @@ def run_ours(args, rank, world, local):
                          survey_flops / max(1, stats["launches"]),
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
         "shoot_rays_override": bool(args.shoot_rays),
-        **({"true_peaks_5sigma": info_holder.get("peaks")} if args.workload == "fold" else {}),
+        **({"true_peaks_5sigma": info_holder.get("peaks"),
+            "peak_statistics": fold_peak_summary(info_holder["peak_stats"], info)}
+           if args.workload == "fold" else {}),
         "rays_check": {"in": stats["rays_in"], "out": stats["rays_out"],
                        "dropped": stats["rays_dropped"], "total": n_local,
                        "conserved": n_local == expected_local},
         "gpu_launches": int(args.steps * (BUILD_KERNELS + stats["launches"] + 2
-                                          + (2 if args.workload == "fold" else 0))),
+                                          + (4 if args.workload == "fold" else 0))),
     }
     clk_sum = clk.summary()
     if clk_sum:

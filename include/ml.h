@@ -390,6 +390,44 @@ enum { ML_ALONG_X = 0, ML_ALONG_Y = 1 };
 ml_status ml_find_peaks(ml_field *f, int32_t along, double nsigma, uint8_t *mask, int32_t *peaks,
                         int64_t capacity, int64_t *n_found, void *stream);
 
+/* Largest number of distance bins of ml_peak_statistics. */
+#define ML_PEAK_STATS_MAX_BINS 2048
+
+/*
+ * ml_peak_statistics - the statistics of §4.2 (Figs. 4 and 5): the true peaks
+ * of the field's count map, binned by the distance of the source from the
+ * macro caustic, taken as a straight line across the curves (a local region
+ * of the critical curve, §2).  Position j along a curve has the distance
+ * d = |origin + (j + 1/2) step - caustic| of its pixel centre (origin, step:
+ * map_x0, dpx for ML_ALONG_X; map_y0, dpy for ML_ALONG_Y), each operation
+ * rounded separately in FP64; bin b holds edges[b] <= d < edges[b+1].  For
+ * the fold model (Eq. 5) the caustic is beta_x = 0 to within
+ * (d_y theta_y)^2 / (2 d_x).
+ *  along:       the curve direction, as in ml_find_peaks.
+ *  nsigma:      the peak threshold, used only when mask is NULL.
+ *  mask:        device, the mask of ml_find_peaks for the same direction on
+ *               the current map (read only); NULL to identify the peaks here
+ *               first, in scratch memory.
+ *  caustic:     the caustic's coordinate along the curves.
+ *  edges:       host, nbins + 1 finite, strictly ascending distances.
+ *  nbins:       1 .. ML_PEAK_STATS_MAX_BINS.
+ *  n_peaks:     host, nbins: true peaks per bin.
+ *  sum_counts:  host, nbins: the sum of N_ij over those peaks; the mean peak
+ *               magnification is sum_counts S_I/S_S / n_peaks (Eq. 12).
+ *  n_positions: host, nbins: the positions per bin where a true peak can
+ *               occur (curves other than the first and last, positions other
+ *               than the two ends); crossings per unit length of curve are
+ *               n_peaks / (n_positions step).
+ * Integer sums, so the result does not depend on the order of the work.
+ * Synchronises `stream`.  Errors: ML_ERR_STATE for a CIC field;
+ * ML_ERR_INVALID_ARG (NULL pointers, nbins out of range, edges not finite
+ * and strictly ascending, a caustic not finite, nsigma <= 0 without a mask);
+ * ML_ERR_CUDA.
+ */
+ml_status ml_peak_statistics(ml_field *f, int32_t along, double nsigma, const uint8_t *mask,
+                             double caustic, const double *edges, int32_t nbins, uint64_t *n_peaks,
+                             uint64_t *sum_counts, uint64_t *n_positions, void *stream);
+
 /*
  * ml_field_clear - zero the map and the counters (stream-ordered).
  */

@@ -42,7 +42,8 @@ EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays"
            "ml_light_curves_noalloc", "ml_batch_create", "ml_batch_run", "ml_batch_field",
            "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy",
            "ml_cic_forward", "ml_cic_backward", "ml_cic_backward_ex", "ml_map_light_curves",
-           "ml_map_light_curves_backward", "ml_field_set_counts", "ml_find_peaks")
+           "ml_map_light_curves_backward", "ml_field_set_counts", "ml_find_peaks",
+           "ml_peak_statistics")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -132,6 +133,7 @@ def load(path: str | None = None):
         "ml_cic_backward_ex": ([V, V, V, V, C.c_int32, V], st),
         "ml_field_set_counts": ([V, V, C.c_int32, V], st),
         "ml_find_peaks": ([V, C.c_int32, C.c_double, V, V, C.c_int64, P(C.c_int64), V], st),
+        "ml_peak_statistics": ([V, C.c_int32, C.c_double, V, C.c_double, V, C.c_int32, V, V, V, V], st),
         "ml_map_light_curves": ([V, C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V], st),
         "ml_map_light_curves_backward": ([C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V, V], st),
         "ml_field_clear": ([V, V], st),
@@ -235,6 +237,18 @@ def ml_find_peaks(field, along=ALONG_X, nsigma=5.0, mask=None, capacity=0, strea
                                 _dptr(peaks) if capacity > 0 else None, capacity, C.byref(n),
                                 _stream(stream)))
     return n.value, peaks[:min(n.value, capacity)]
+
+
+def ml_peak_statistics(field, edges, along=ALONG_X, caustic=0.0, mask=None, nsigma=5.0, stream=None):
+    """Peak statistics of §4.2 by distance to the caustic (see ml.h).
+    Returns (n_peaks, sum_counts, n_positions), uint64 arrays of len(edges) - 1."""
+    e = np.ascontiguousarray(edges, np.float64)
+    nb = len(e) - 1
+    out = [np.zeros(max(nb, 1), np.uint64) for _ in range(3)]
+    _check(load().ml_peak_statistics(field, along, float(nsigma), _dptr(mask) if mask is not None else None,
+                                     float(caustic), e.ctypes.data, nb, *(o.ctypes.data for o in out),
+                                     _stream(stream)))
+    return tuple(o[:nb] for o in out)
 
 
 def ml_field_set_counts(field, counts, stream=None):

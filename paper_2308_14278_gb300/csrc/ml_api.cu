@@ -1207,6 +1207,15 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
 
 }  // namespace
 
+namespace ml {
+// peak statistics kernels (ml_maps.cu): out holds n_peaks, sum_counts and
+// n_positions, nbins 64-bit counters each
+cudaError_t launch_peak_stats(const uint32_t *N, int nx, int ny, int along, const uint8_t *mask,
+                              double origin, double step, double caustic, const double *edges,
+                              int nbins, int32_t *bin_of, unsigned long long *out, int num_sms,
+                              cudaStream_t s);
+}  // namespace ml
+
 extern "C" {
 
 ml_status ml_batch_create(const ml_field_desc *descs, int32_t n, int32_t tracks_per_map,
@@ -1621,6 +1630,65 @@ ml_status ml_find_peaks(ml_field *f, int32_t along, double nsigma, uint8_t *mask
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "peak identification");
     *n_found = (int64_t)h_found;
+    return ML_OK;
+}
+
+ml_status ml_peak_statistics(ml_field *f, int32_t along, double nsigma, const uint8_t *mask,
+                             double caustic, const double *edges, int32_t nbins, uint64_t *n_peaks,
+                             uint64_t *sum_counts, uint64_t *n_positions, void *stream)
+{
+    if (!f || !edges || !n_peaks || !sum_counts || !n_positions)
+        return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (!f->d_map_u32) return fail(ML_ERR_STATE, "peak statistics need an NGP count map");
+    if (along != ML_ALONG_X && along != ML_ALONG_Y) return fail(ML_ERR_INVALID_ARG, "unknown curve direction");
+    if (nbins < 1 || nbins > ML_PEAK_STATS_MAX_BINS) return fail(ML_ERR_INVALID_ARG, "nbins out of range");
+    if (!is_fin(caustic)) return fail(ML_ERR_INVALID_ARG, "caustic must be finite");
+    for (int b = 0; b <= nbins; ++b)
+        if (!is_fin(edges[b]) || (b > 0 && !(edges[b] > edges[b - 1])))
+            return fail(ML_ERR_INVALID_ARG, "edges must be finite and strictly ascending");
+    if (!mask && (!(nsigma > 0.0) || !is_fin(nsigma))) return fail(ML_ERR_INVALID_ARG, "nsigma must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nx = f->g.mnx, ny = f->g.mny;
+    const size_t npix = (size_t)nx * ny;
+    const int len = along == ML_ALONG_X ? nx : ny;
+    const double origin = along == ML_ALONG_X ? f->g.mx0 : f->g.my0;
+    const double step = along == ML_ALONG_X ? f->g.dpx : f->g.dpy;
+    // one scratch block: counters, edges, bin of each position, then (when the
+    // caller gives no mask) the mask and the found counter of the peak step
+    const size_t o_edges = 3 * (size_t)nbins * sizeof(unsigned long long);
+    const size_t o_bins = o_edges + ((size_t)(nbins + 1) * sizeof(double) + 15) / 16 * 16;
+    const size_t o_mask = o_bins + ((size_t)len * sizeof(int32_t) + 15) / 16 * 16;
+    const size_t o_found = o_mask + (npix + 4 + 15) / 16 * 16;
+    const size_t bytes = mask ? o_mask : o_found + 16;
+    char *scratch = nullptr;
+    std::vector<unsigned long long> h(3 * (size_t)nbins);
+    cudaError_t e = cudaMallocAsync((void **)&scratch, bytes, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scratch + o_edges, edges, (size_t)(nbins + 1) * sizeof(double),
+                            cudaMemcpyHostToDevice, s);
+    const uint8_t *m = mask;
+    if (e == cudaSuccess && !mask) {
+        uint8_t *mm = reinterpret_cast<uint8_t *>(scratch + o_mask);
+        e = launch_peaks(f->d_map_u32, nx, ny, along, nsigma, mm, nullptr, 0,
+                         reinterpret_cast<unsigned long long *>(scratch + o_found), s);
+        m = mm;
+    }
+    if (e == cudaSuccess)
+        e = launch_peak_stats(f->d_map_u32, nx, ny, along, m, origin, step, caustic,
+                              reinterpret_cast<const double *>(scratch + o_edges), nbins,
+                              reinterpret_cast<int32_t *>(scratch + o_bins),
+                              reinterpret_cast<unsigned long long *>(scratch), f->num_sms, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), scratch, h.size() * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "peak statistics");
+    for (int b = 0; b < nbins; ++b) {
+        n_peaks[b] = h[b];
+        sum_counts[b] = h[(size_t)nbins + b];
+        n_positions[b] = h[2 * (size_t)nbins + b];
+    }
     return ML_OK;
 }
 

@@ -366,6 +366,84 @@ cudaError_t launch_peaks(const uint32_t *N, int nx, int ny, int along, double ns
     return cudaGetLastError();
 }
 
+// ---- peak statistics over distance to the caustic (§4.2, Figs. 4-5) ------------
+//
+// Position j along a curve has the distance d = |origin + (j + 1/2) step - caustic|
+// of its pixel centre, formed with separately rounded FP64 operations (no fused
+// multiply-add), so that the bin it falls in does not depend on the compiler;
+// bin b holds edges[b] <= d < edges[b+1].  The curves' end positions hold no
+// peak and fall in no bin.
+__global__ void k_peak_bins(int len, double origin, double step, double caustic,
+                            const double *__restrict__ edges, int nbins,
+                            unsigned long long per_position, int32_t *__restrict__ bin_of,
+                            unsigned long long *__restrict__ n_positions)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= len) return;
+    int b = -1;
+    if (j > 0 && j < len - 1) {
+        const double c = __dadd_rn(origin, __dmul_rn((double)j + 0.5, step));
+        const double d = fabs(__dadd_rn(c, -caustic));
+        if (d >= edges[0] && d < edges[nbins]) {
+            int lo = 0, hi = nbins;                 // edges[lo] <= d < edges[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (edges[mid] <= d) lo = mid; else hi = mid;
+            }
+            b = lo;
+        }
+    }
+    bin_of[j] = b;
+    if (b >= 0 && per_position) atomicAdd(&n_positions[b], per_position);
+}
+
+// Per bin: the true peaks (mask bit 1) and the sum of their counts, gathered in
+// shared memory (2 nbins 64-bit counters) and added to the global sums once per
+// block.  Integer sums: the result does not depend on the order.
+__global__ void k_peak_stats(const uint8_t *__restrict__ mask, const uint32_t *__restrict__ N, int nx,
+                             int ny, int along, const int32_t *__restrict__ bin_of, int nbins,
+                             unsigned long long *__restrict__ n_peaks,
+                             unsigned long long *__restrict__ sum_counts)
+{
+    extern __shared__ unsigned long long sh_bins[];
+    for (int b = threadIdx.x; b < 2 * nbins; b += blockDim.x) sh_bins[b] = 0;
+    __syncthreads();
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (!(mask[q] & 2)) continue;
+        const int j = along == 0 ? (int)(q % nx) : (int)(q / nx);
+        const int b = bin_of[j];
+        if (b < 0) continue;
+        atomicAdd(&sh_bins[b], 1ull);
+        atomicAdd(&sh_bins[nbins + b], (unsigned long long)N[q]);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        if (sh_bins[b] == 0) continue;
+        atomicAdd(&n_peaks[b], sh_bins[b]);
+        atomicAdd(&sum_counts[b], sh_bins[nbins + b]);
+    }
+}
+
+cudaError_t launch_peak_stats(const uint32_t *N, int nx, int ny, int along, const uint8_t *mask,
+                              double origin, double step, double caustic, const double *edges,
+                              int nbins, int32_t *bin_of, unsigned long long *out, int num_sms,
+                              cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 3 * (size_t)nbins * sizeof(unsigned long long), s);
+    const int len = along == 0 ? nx : ny, ncurves = along == 0 ? ny : nx;
+    if (e != cudaSuccess || len == 0 || ncurves == 0) return e;
+    const unsigned long long per_position = ncurves >= 3 ? (unsigned long long)(ncurves - 2) : 0ull;
+    k_peak_bins<<<(len + 255) / 256, 256, 0, s>>>(len, origin, step, caustic, edges, nbins, per_position,
+                                                  bin_of, out + 2 * (size_t)nbins);
+    const int64_t n = (int64_t)nx * ny;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8));
+    k_peak_stats<<<blocks, 256, 2 * (size_t)nbins * sizeof(unsigned long long), s>>>(
+        mask, N, nx, ny, along, bin_of, nbins, out, out + nbins);
+    return cudaGetLastError();
+}
+
 // ---- adjoint of the light curves ---------------------------------------------
 //
 // A light-curve sample is L = sum_c w_c sum_{dx,dy} taps[dx] taps[dy] M[p_c + (dx, dy)]
