@@ -108,7 +108,8 @@ def parse():
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: shoot ONE paper-scale map across the ranks (contiguous level-1 "
                          "bands per rank, integer map sum over NCCL; strong scaling) instead of "
-                         "one independent map per rank (weak scaling)")
+                         "one independent map per rank (weak scaling); with --workload batched, "
+                         "split one set of 80 maps over the ranks (whole maps balanced by rays)")
     ap.add_argument("--no-tune", action="store_true",
                     help="the paper's level-2 grid (L2 = L1/20) instead of the autotuned one")
     ap.add_argument("--grid", default="",
@@ -467,17 +468,25 @@ def run_batched(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
     import paper_2308_14278_gb300 as ml
-    from paper_2308_14278_gb300 import inputs
+    from paper_2308_14278_gb300 import inputs, shard
     ml.load()
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    n_maps, tpm, map_px = 80, 10, 4096
-    ws = inputs.batched_maps(n_maps=n_maps, seed=rank, map_px=map_px, ray_range=(1e9, 1e10),
+    # --shard: the ranks split one set of 80 maps (whole maps, balanced by
+    # rays, nothing exchanged); otherwise each rank runs its own 80 maps
+    sharded = bool(args.shard and world > 1)
+    seed = 0 if sharded else rank
+    n_all, tpm, map_px = 80, 10, 4096
+    ws = inputs.batched_maps(n_maps=n_all, seed=seed, map_px=map_px, ray_range=(1e9, 1e10),
                              tracks_per_map=tpm)
-    tracks = np.stack([inputs.tracks(tpm, map_px, map_px, 4 * SIGMA_PX + 1, seed=500 + 100 * rank + i)
-                       for i in range(n_maps)])
+    tracks = np.stack([inputs.tracks(tpm, map_px, map_px, 4 * SIGMA_PX + 1, seed=500 + 100 * seed + i)
+                       for i in range(n_all)])
+    if sharded:
+        mine = shard.maps_for_rank([w.n_av * w.map_n[0] * w.map_n[1] for w in ws], rank, world)
+        ws, tracks = [ws[i] for i in mine], tracks[mine]
+    n_maps = len(ws)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     t0 = time.perf_counter()
@@ -506,11 +515,16 @@ def run_batched(args, rank, world, local):
     step_ms = float(np.mean([a.elapsed_time(c) for a, c in times]))
     stats = [b.stats(i) for i in range(n_maps)]
     t_local = step_ms
+    rays_job = rays * world
     if dist:
         t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_local = float(t.item())
-    value = rays * world / (t_local / 1e3)
+        if sharded:
+            r = torch.tensor([rays], device="cuda", dtype=torch.int64)
+            dist.all_reduce(r)
+            rays_job = int(r.item())
+    value = rays_job / (t_local / 1e3)
 
     # the same maps one at a time: own field, own default grid and order
     fields = [ml.Field(w, precision=ml.PREC_MIXED) for w in ws]
@@ -546,15 +560,17 @@ def run_batched(args, rank, world, local):
     out = {
         "metric": "rays/s of 80 batched maps on 1 GB300 (one CUDA graph, a persistent launch per Taylor order)",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_local, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": t_local, "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+        "vs_baseline": None,
         "dtype": "f32 near sum + f64 nodes", "data": "synthetic (seeded lognormal lens discs; no dataset)",
-        "config": {"workload": f"batched: {n_maps} maps, 2,000-20,000 lenses, kappa_* in "
+        "config": {"workload": f"batched: {n_all} maps, 2,000-20,000 lenses, kappa_* in "
                                f"{{0.002, 0.005, 0.01}}, kappa+gamma 0.95-0.99, 1e9-1e10 rays each, "
-                               f"{map_px}^2 uint32, {n_maps * tpm} light curves x {TRACK_SAMPLES}",
-                   "total_rays": int(rays), "taylor_p": orders, "tuned_grids": True,
+                               f"{map_px}^2 uint32, {n_all * tpm} light curves x {TRACK_SAMPLES}",
+                   "total_rays": int(rays_job if sharded else rays), "taylor_p": orders, "tuned_grids": True,
                    "launches_per_step": len(orders),
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"independent batches per GPU x{world}"},
+                   "parallelism": (f"one set of {n_all} maps split over {world} GPUs (whole maps, "
+                                   f"balanced by rays)" if sharded else f"independent batches per GPU x{world}")},
         "create_s": create_s,
         "one_map_at_a_time": {"ms_per_step": single_ms, "value": rays / (single_ms / 1e3),
                               "taylor_p": single_p, "speedup_of_batched": single_ms / step_ms},
@@ -586,7 +602,11 @@ def run_batched(args, rank, world, local):
             te.append(time.perf_counter() - t0)
             bb.close()
         t = float(np.mean(te))
-        out["e2e"] = {"value": rays / t, "unit": UNIT, "ms_per_step": t * 1e3,
+        if dist:
+            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        out["e2e"] = {"value": rays_job / t, "unit": UNIT, "ms_per_step": t * 1e3,
                       "h2d_bytes_per_step": int(sum(24 * w.lenses.n for w in ws) + tracks.nbytes),
                       "d2h_bytes_per_step": int(4 * n_maps * tpm * TRACK_SAMPLES),
                       "note": "includes batch creation (tuned grids cached per process)"}

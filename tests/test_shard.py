@@ -104,3 +104,38 @@ def test_sharded_map_equals_the_one_gpu_map(ml):
     assert torch.equal(parts[0].light_curves(tracks, 256, 0.5), whole.light_curves(tracks, 256, 0.5))
     for f in parts + [whole]:
         f.close()
+
+
+def _batch_rank_main(rank, world, port, out_path):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ws = inputs.batched_maps(n_maps=12, seed=0, map_px=64, ray_range=(1e5, 1e6), tracks_per_map=1)
+    mine = shard.maps_for_rank([w.n_av * w.map_n[0] * w.map_n[1] for w in ws], rank, world)
+    rays = sum(oracle.geometry_of(ws[i]).n_rays for i in mine)
+    r = torch.tensor([rays], dtype=torch.int64)
+    dist.all_reduce(r)
+    owner = torch.zeros(len(ws), dtype=torch.int64)
+    owner[mine] = 1
+    dist.all_reduce(owner)
+    if rank == 0:
+        np.save(out_path, np.concatenate([r.numpy(), owner.numpy()]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_three_gloo_ranks_split_a_batch_by_whole_maps(tmp_path):
+    """The batched workload split over ranks as the bench's --shard does it:
+    every map is shot by exactly one rank, and the ranks' summed ray counts are
+    the whole batch's."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ws = inputs.batched_maps(n_maps=12, seed=0, map_px=64, ray_range=(1e5, 1e6), tracks_per_map=1)
+    total = sum(oracle.geometry_of(w).n_rays for w in ws)
+    out = str(tmp_path / "batch.npy")
+    mp.spawn(_batch_rank_main, args=(3, _free_port(), out), nprocs=3, join=True)
+    got = np.load(out)
+    assert int(got[0]) == total
+    assert list(got[1:]) == [1] * len(ws)
