@@ -141,3 +141,38 @@ def test_bench_traffic_check_ignores_comments():
     c = "int f(int x)\n{\n    return x + 2;\n}\n"
     assert bench.code_hash(a) == bench.code_hash(b) != bench.code_hash(c)
     assert bench.traffic_per_launch(1e9) is not None
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_for_test", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    return bench
+
+
+def test_bench_peak_summary_and_baseline_records():
+    """The fold step's peak summary divides as documented (crossings per
+    theta_E of curve, mean mu at the peaks; empty bins report 0), and the CPU
+    baseline taken from the parity stripe reports that run's rate."""
+    import numpy as np
+    bench = _bench_module()
+    nb = len(bench.FOLD_DISTANCE_EDGES) - 1
+    n = np.zeros(nb, np.uint64)
+    s = np.zeros(nb, np.uint64)
+    p = np.zeros(nb, np.uint64)
+    n[2], s[2], p[2] = 4, 4000, 200
+    p[3] = 50
+    out = bench.fold_peak_summary((n, s, p), {"dpx": 0.02, "mu_per_count": 0.01})
+    assert out["n_peaks"][2] == 4 and out["crossings_per_theta_e"][2] == 1.0
+    assert out["mean_mu_peak"][2] == 10.0
+    assert out["crossings_per_theta_e"][3] == 0.0 and out["mean_mu_peak"][3] == 0.0
+    assert out["crossings_per_theta_e"][0] == 0.0
+    assert len(out["edges_theta_e"]) == nb + 1
+
+    class W:
+        class lenses:
+            n = 13000
+    rec = bench.cpu_baseline_of((10_000_000, 12.5, 16, 1.0e11), W)
+    assert rec["value"] == 800000.0 and rec["cores"] == 16 and rec["kind"] == "oracle"
+    assert "10000000 consecutive rays" in rec["sample"]
