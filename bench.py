@@ -23,6 +23,7 @@ import os
 import signal
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -105,6 +106,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the nvidia-smi clock samples of the timed region "
+                         "(default: a temporary directory); the JSON line carries their summary")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: shoot ONE paper-scale map across the ranks (contiguous level-1 "
                          "bands per rank, integer map sum over NCCL; strong scaling) instead of "
@@ -147,10 +151,11 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, directory: str | None = None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        d = directory or os.path.join(tempfile.gettempdir(), f"ml_bench_clocks_{os.getpid()}")
+        self.path = os.path.join(d, f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
@@ -285,7 +290,7 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
     timers = []
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_dir) as clk:
         torch.cuda.synchronize()
         for _ in range(args.steps):
             flush.zero_()                 # L2 flush between timed steps (outside the events)
@@ -319,7 +324,7 @@ def run_ours(args, rank, world, local):
     flops = 11.0 * stats["near_pairs"] + (4.0 * p + 6.0) * n_local
     achieved = flops / (shoot_ms / 1e3) / 1e12
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    survey_flops = 11.0 * stats["near_pairs"] + (8.0 * p + 10.0) * n_local
+    fixed_convention_flops = 11.0 * stats["near_pairs"] + (8.0 * p + 10.0) * n_local
 
     out = {
         "metric": METRIC if args.workload == "paper" else
@@ -347,8 +352,8 @@ def run_ours(args, rank, world, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": traffic_per_launch(n_local / max(1, stats["launches"])),
-                     "kernel": "k_shoot_mixed", "flops_per_launch_survey_convention":
-                         survey_flops / max(1, stats["launches"]),
+                     "kernel": "k_shoot_mixed", "flops_per_launch_fixed_convention":
+                         fixed_convention_flops / max(1, stats["launches"]),
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
         "shoot_rays_override": bool(args.shoot_rays),
         **({"true_peaks_5sigma": info_holder.get("peaks"),
@@ -524,7 +529,7 @@ def run_batched(args, rank, world, local):
     if dist:
         dist.barrier()
     times = []
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_dir) as clk:
         for _ in range(args.steps):
             flush.zero_()
             e = _events(torch, 2)
@@ -707,7 +712,7 @@ def run_differentiable(args, rank, world, local):
     if dist:
         dist.barrier()
     timers = []
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_dir) as clk:
         for _ in range(args.steps):
             flush.zero_()
             e = _events(torch, 5)
