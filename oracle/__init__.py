@@ -292,7 +292,11 @@ def _lens_arrays(x, y, m):
 
 def shoot_direct(g: Geometry, x, y, m, ray_begin=0, ray_end=None, threads=None):
     """Counts N_ij (uint64, mny x mnx) of rays [ray_begin, ray_end) by direct
-    summation, and stats (in map, out of map, dropped)."""
+    summation, and stats (in map, out of map, dropped): the plain definition
+    the near/far scheme approximates -- every lattice ray (§3.2 Level 3)
+    through the lens equation with the deflection of all lenses (Eq. 6, or
+    Eq. 5's fold term), binned by the nearest grid point into the source-plane
+    pixels whose counts Eq. 12 turns into magnification."""
     x, y, m = _lens_arrays(x, y, m)
     if ray_end is None:
         ray_end = g.n_rays
@@ -340,7 +344,9 @@ def beta_interp(g: Geometry, x, y, m, idx, threads=None):
 
 def node_coeffs(g: Geometry, x, y, m, c2x, c2y):
     """Complex far-field Taylor coefficients c_0..c_p at level-2 nodes
-    (c2x, c2y): array (nnodes, p+1) complex128."""
+    (c2x, c2y): array (nnodes, p+1) complex128.  §3.2 Level 2: the far
+    lenses' deflection expanded in a Taylor series about each level-2 grid
+    point, evaluated per ray by Eq. 9."""
     x, y, m = _lens_arrays(x, y, m)
     c2x = np.ascontiguousarray(c2x, np.int64)
     c2y = np.ascontiguousarray(c2y, np.int64)
@@ -355,14 +361,21 @@ def node_coeffs(g: Geometry, x, y, m, c2x, c2y):
 
 
 def node_position(g: Geometry, c2x, c2y):
-    """Centre of level-2 cell (c2x, c2y), the expansion point of its series."""
+    """Centre of level-2 cell (c2x, c2y), the expansion point of its series
+    (§3.2 Level 2; the paper's "grid point where the ray is located" read as
+    the centre of the ray's level-2 cell)."""
     l2x = g.n2x * g.l3x
     l2y = g.n2y * g.l3y
     return g.rx0 + (np.asarray(c2x) + 0.5) * l2x, g.ry0 + (np.asarray(c2y) + 0.5) * l2y
 
 
 def remainder_bound(g: Geometry, x, y, m, idx):
-    """Upper bound of the far-series truncation error at each ray of idx."""
+    """Upper bound of the far-series truncation error at each ray of idx: the
+    tail of Eq. 9's series beyond order p, summed over the far lenses
+    (sum_k m_k rho^(p+1) / (r_k^(p+1) (r_k - rho)), rho the ray's distance from
+    its node, r_k the lens's).  The paper states the accuracy it reaches
+    (§3.2) but no bound; this is the geometric-series bound of the
+    expansion."""
     x, y, m = _lens_arrays(x, y, m)
     idx = np.ascontiguousarray(idx, np.int64)
     out = np.zeros(len(idx))
@@ -408,7 +421,7 @@ def gaussian_taps(sigma_px: float):
 
 def convolve_gaussian(mu, sigma_px: float):
     """Finite-source map: mu convolved with the Gaussian taps along each axis,
-    zero outside the map."""
+    zero outside the map (the Gaussian source of §4.1)."""
     w = gaussian_taps(sigma_px)
     h = len(w) // 2
     ny, nx = mu.shape
@@ -425,7 +438,9 @@ def convolve_gaussian(mu, sigma_px: float):
 
 def bilinear(img, u, v):
     """Bilinear value at map coordinates (u, v) between pixel centres
-    (pixel (i, j) has its centre at (i + 1/2, j + 1/2)); zero outside."""
+    (pixel (i, j) has its centre at (i + 1/2, j + 1/2)); zero outside.  The
+    light curves of §4.1 sample the finite-source map this way between
+    pixels (the paper does not state its interpolation)."""
     ny, nx = img.shape
     fx = np.asarray(u) - 0.5
     fy = np.asarray(v) - 0.5
@@ -458,7 +473,7 @@ def light_curves(mu, tracks, n_samples: int, sigma_px: float):
 
 
 def light_curves_sampled(mu, tracks, n_samples: int, sigma_px: float):
-    """light_curves for a map too large to convolve whole: the convolved map
+    """light_curves (§4.1) for a map too large to convolve whole: the convolved map
     is evaluated only at the pixels that the bilinear samples read, with the
     same taps, the same zero outside the map and the same order of the sums
     (along x, then along y; then the four bilinear terms), so the two agree
@@ -507,7 +522,11 @@ def light_curves_sampled(mu, tracks, n_samples: int, sigma_px: float):
 # ---------------------------------------------------------------------------
 
 def cic_forward(g: Geometry, x, y, m, ray_begin=0, ray_end=None, threads=None):
-    """Cloud-in-cell ray map (FP64, mny x mnx, units of rays)."""
+    """Cloud-in-cell ray map (FP64, mny x mnx, units of rays): every lattice
+    ray's Eq. 6 source position shared bilinearly among the four nearest
+    pixel centres, the differentiable counterpart of Eq. 12's binning (the
+    paper has no differentiable form; weights of centres outside the map are
+    dropped)."""
     x, y, m = _lens_arrays(x, y, m)
     if ray_end is None:
         ray_end = g.n_rays
@@ -525,14 +544,17 @@ def cic_mu_scale(g: Geometry) -> float:
 
 
 def cic_loss(g: Geometry, x, y, m, target, ray_begin=0, ray_end=None, threads=None):
-    """L = sum_ij (M_ij - T_ij)^2 with M = S_I/S_S * CIC map."""
+    """L = sum_ij (M_ij - T_ij)^2 with M = S_I/S_S * CIC map (Eq. 12 scaling of
+    the cloud-in-cell map)."""
     M = cic_mu_scale(g) * cic_forward(g, x, y, m, ray_begin, ray_end, threads)
     return float(np.sum((M - target) ** 2)), M
 
 
 def cic_grad_dM(g: Geometry, x, y, m, dL_dM, ray_begin=0, ray_end=None, threads=None):
     """FP64 gradient of any loss of the CIC magnification map M given its
-    dL/dM (mny x mnx): (dL/dlens (n, 3), dL/d(kappa, gamma, kappa_*))."""
+    dL/dM (mny x mnx): (dL/dlens (n, 3), dL/d(kappa, gamma, kappa_*)), by
+    differentiating Eq. 6 (macro term, point-mass sum and sheet) and the
+    bilinear weights ray by ray, over all lenses."""
     x, y, m = _lens_arrays(x, y, m)
     if ray_end is None:
         ray_end = g.n_rays
@@ -551,7 +573,7 @@ def cic_grad_dM(g: Geometry, x, y, m, dL_dM, ray_begin=0, ray_end=None, threads=
 
 def cic_grad(g: Geometry, x, y, m, target, ray_begin=0, ray_end=None, threads=None):
     """FP64 reference gradient of cic_loss: (dL/dlens (n, 3), dL/d(kappa,
-    gamma, kappa_*))."""
+    gamma, kappa_*)), Eq. 6 differentiated as in cic_grad_dM."""
     x, y, m = _lens_arrays(x, y, m)
     if ray_end is None:
         ray_end = g.n_rays
