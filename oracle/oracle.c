@@ -119,7 +119,9 @@ static void sheet_deflection(const orc_geom *g, double tx, double ty,
     }
 }
 
-/* The smooth (macro) part of beta. */
+/* The smooth (macro) part of beta: the constant-kappa, gamma lens of Eq. 1,
+ * diag(1 - kappa - gamma, 1 - kappa + gamma) theta, or the fold of Eq. 5 near
+ * the critical curve (the quadratic in theta_x, and 2 (1 - kappa_0) theta_y). */
 static void macro_term(const orc_geom *g, double tx, double ty, double *mx, double *my)
 {
     if (g->macro_mode == 1) {
@@ -131,6 +133,8 @@ static void macro_term(const orc_geom *g, double tx, double ty, double *mx, doub
     }
 }
 
+/* Ray r of the lattice: the centre of level-3 pixel (i, j), r = j n3x + i
+ * (§3.2 Level 3). */
 static void ray_position(const orc_geom *g, int64_t r, double *tx, double *ty)
 {
     int64_t i = r % g->n3x, j = r / g->n3x;
