@@ -265,7 +265,9 @@ ml_status ml_light_curves_noalloc(ml_field *f, const double *tracks, int32_t n_t
 
 /*
  * ml_trace_rays - source positions of single rays by exactly the arithmetic
- * the shooting kernel of the field's precision mode uses (for checking).
+ * the shooting kernel of the field's precision mode uses (for checking):
+ * Eq. 9 in the near/far modes, Eq. 6 summed over all lenses in
+ * ML_PREC_DIRECT64, and the pixel of Eq. 12's binning.
  *  ray_idx: device, n linear ray indices (each < n_rays_x * n_rays_y).
  *  beta:    device, n x 2 float64, source position in theta_E.
  *  pix:     device, n x 2 int32, the pixel the shooting kernel bins the ray
@@ -295,8 +297,9 @@ ml_status ml_map_light_curves(const float *mu, int32_t nx, int32_t ny, const dou
  * ml_map_light_curves_backward - the transpose of ml_map_light_curves: given
  * dL_dcurves (device, n_tracks x n_samples float32), writes dL_dmu (device,
  * ny x nx float32, overwritten) = sum over samples of the sample's gradient
- * times its bilinear and Gaussian weights.  With ml_cic_backward it gives the
- * gradient of a light-curve loss with respect to the lens field.
+ * times its bilinear and Gaussian weights (§4.1's light curves transposed; the
+ * paper has no gradient).  With ml_cic_backward it gives the gradient of a
+ * light-curve loss with respect to the lens field.
  * Stream-ordered; errors as ml_map_light_curves.
  */
 ml_status ml_map_light_curves_backward(int32_t nx, int32_t ny, const double *tracks, int32_t n_tracks,
@@ -343,7 +346,8 @@ enum {
 };
 
 /*
- * ml_cic_backward_ex - ml_cic_backward with a choice of method (above).
+ * ml_cic_backward_ex - ml_cic_backward with a choice of method (above): Eq. 9
+ * transposed, or Eq. 6 differentiated lens by lens.
  * ml_cic_backward is ml_cic_backward_ex(..., ML_ADJOINT_NEARFAR, ...).
  * The near/far method allocates its scratch (3 doubles per lens and
  * 2 (p + 1) doubles per level-2 node) stream-ordered and frees it before
@@ -356,6 +360,8 @@ ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens,
 /*
  * ml_field_set_counts - replace the field's integer count map (NGP fields)
  * with `counts` (map_ny x map_nx uint32, device or host), stream-ordered.
+ * Rays are independent (§3.2 Level 3), so a map's counts are the sum of the
+ * counts of any partition of its rays.
  * For a map shot in shards on several GPUs: each GPU shoots its ray range,
  * the count maps are summed (integer addition, exact), and the sum is set
  * back before ml_magnification_map and ml_light_curves.  The counters
@@ -430,6 +436,7 @@ ml_status ml_peak_statistics(ml_field *f, int32_t along, double nsigma, const ui
 
 /*
  * ml_field_clear - zero the map and the counters (stream-ordered).
+ * Bookkeeping; no counterpart in the paper.
  */
 ml_status ml_field_clear(ml_field *f, void *stream);
 
@@ -439,21 +446,25 @@ ml_status ml_field_clear(ml_field *f, void *stream);
  * sums the map in 64 bits (one pass over the map): a pixel that wrapped
  * makes that sum fall short of the in-map ray count, which sets flag bit 0.
  * Returns ML_ERR_OVERFLOW or ML_ERR_ABORTED when the corresponding flag is
- * set, after filling out.
+ * set, after filling out.  The counts check ray conservation (every lattice
+ * ray of §3.2 Level 3 is in the map, out of it or dropped).
  */
 ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream);
 
-/* ml_field_info - copy the derived parameters into *out (host). */
+/* ml_field_info - copy the derived parameters (§3.1-§3.2: ray rectangle,
+ * lattice, level grids, Taylor order, S_I/S_S of Eq. 12) into *out (host). */
 ml_status ml_field_info(const ml_field *f, ml_field_params *out);
 
 /*
  * ml_field_abort - raise (on != 0) or lower the field's abort flag.  It lives
  * in mapped host memory; running shooting kernels read it between warp tasks
  * and stop early, leaving a valid partial map and setting the aborted flag.
+ * Bookkeeping; no counterpart in the paper.
  */
 ml_status ml_field_abort(ml_field *f, int32_t on);
 
-/* ml_field_destroy - free the field and its device memory.  NULL is a no-op. */
+/* ml_field_destroy - free the field and its device memory.  NULL is a no-op.
+ * Bookkeeping; no counterpart in the paper. */
 ml_status ml_field_destroy(ml_field *f);
 
 /*
@@ -490,27 +501,32 @@ ml_status ml_batch_run(ml_batch *b, int32_t use_graph, void *stream);
 
 /* ml_batch_field - borrowed handle of map i (owned by the batch: do not
  * destroy it); usable with ml_field_stats, ml_field_info, ml_trace_rays,
- * ml_magnification_map, ml_light_curves. */
+ * ml_magnification_map, ml_light_curves.  Bookkeeping; no counterpart in the
+ * paper. */
 ml_status ml_batch_field(ml_batch *b, int32_t i, ml_field **out);
 
-/* ml_batch_mu - copy map i's mu (float32, from the last run) into out
- * (device or host memory; host output synchronises `stream`). */
+/* ml_batch_mu - copy map i's mu (Eq. 12, float32, from the last run) into
+ * out (device or host memory; host output synchronises `stream`). */
 ml_status ml_batch_mu(ml_batch *b, int32_t i, float *out, int32_t out_is_device, void *stream);
 
-/* ml_batch_curves - copy all light curves of the last run, n x
+/* ml_batch_curves - copy all light curves (§4.1) of the last run, n x
  * tracks_per_map x n_samples float32, into out (device or host). */
 ml_status ml_batch_curves(ml_batch *b, float *out, int32_t out_is_device, void *stream);
 
-/* ml_batch_abort - raise or lower the batch's abort flag (see ml_field_abort). */
+/* ml_batch_abort - raise or lower the batch's abort flag (see ml_field_abort).
+ * Bookkeeping; no counterpart in the paper. */
 ml_status ml_batch_abort(ml_batch *b, int32_t on);
 
-/* ml_batch_destroy - free the batch and its fields.  NULL is a no-op. */
+/* ml_batch_destroy - free the batch and its fields.  NULL is a no-op.
+ * Bookkeeping; no counterpart in the paper. */
 ml_status ml_batch_destroy(ml_batch *b);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).  Bookkeeping;
+ * no counterpart in the paper. */
 const char *ml_last_error(void);
 
-/* ABI version the library was built with (ML_ABI_VERSION). */
+/* ABI version the library was built with (ML_ABI_VERSION).  Bookkeeping; no
+ * counterpart in the paper. */
 int32_t ml_abi_version(void);
 
 #ifdef __cplusplus
