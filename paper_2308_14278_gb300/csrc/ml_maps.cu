@@ -10,7 +10,7 @@
 
 namespace ml {
 
-// mu_ij = N_ij * S_I / S_S.  Vectorised: four pixels per thread per step,
+// mu_ij = N_ij * S_I / S_S (Eq. 12).  Vectorised: four pixels per thread per step,
 // uint4 loads and float4 / double2 stores, grid-stride over the map.
 __global__ void k_mu_u32_f32(const uint4 *__restrict__ in, float4 *__restrict__ out, int64_t n4,
                              float scale)
@@ -92,7 +92,7 @@ cudaError_t launch_mu(const Geo &g, const uint32_t *cu, const float *cf, int wan
     return cudaGetLastError();
 }
 
-// Light curves.  For every sample: bilinear interpolation between the four
+// Light curves (§4.1, Fig. 3).  For every sample: bilinear interpolation between the four
 // pixel centres around the point, each value being the map convolved with
 // the separable normalised Gaussian taps (zero outside the map).  Only the
 // pixels the samples need are convolved.  One warp per sample group; taps
