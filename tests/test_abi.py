@@ -176,3 +176,22 @@ def test_bench_peak_summary_and_baseline_records():
     rec = bench.cpu_baseline_of((10_000_000, 12.5, 16, 1.0e11), W)
     assert rec["value"] == 800000.0 and rec["cores"] == 16 and rec["kind"] == "oracle"
     assert "10000000 consecutive rays" in rec["sample"]
+
+
+def test_no_cpu_fallback_without_a_gpu_or_library(libpath, monkeypatch):
+    """The product path fails loudly: without the built library the binding
+    raises, and a valid descriptor on a machine without a usable GPU gets
+    ML_ERR_CUDA and no field, never a result computed elsewhere."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes as C
+    from paper_2308_14278_gb300 import inputs
+    monkeypatch.setattr(ml, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        ml.load(os.path.join(ROOT, "no_such_dir", "libml.so"))
+    lib = ml.load(libpath)
+    d = ml.make_desc(inputs.small_map(0), precision=ml.PREC_MIXED)
+    h = C.c_void_p()
+    assert lib.ml_field_create(C.byref(d), None, C.byref(h)) == 3      # ML_ERR_CUDA
+    assert h.value is None and lib.ml_last_error()
