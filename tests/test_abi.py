@@ -195,3 +195,39 @@ def test_no_cpu_fallback_without_a_gpu_or_library(libpath, monkeypatch):
     h = C.c_void_p()
     assert lib.ml_field_create(C.byref(d), None, C.byref(h)) == 3      # ML_ERR_CUDA
     assert h.value is None and lib.ml_last_error()
+
+
+_CALLER_C = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ml.h"
+int main(void)
+{
+    ml_field *f = (ml_field *)0;
+    ml_field_desc d;
+    memset(&d, 0, sizeof d);
+    if (ml_abi_version() != ML_ABI_VERSION) return 1;
+    if (ml_field_create((const ml_field_desc *)0, (void *)0, &f) != ML_ERR_INVALID_ARG) return 2;
+    if (f != (ml_field *)0 || strlen(ml_last_error()) == 0) return 3;
+    d.abi_version = ML_ABI_VERSION + 1;
+    if (ml_field_create(&d, (void *)0, &f) != ML_ERR_INVALID_ARG) return 4;
+    if (ml_field_destroy((ml_field *)0) != ML_OK) return 5;
+    printf("%s\n", ml_last_error());
+    return 0;
+}
+"""
+
+
+def test_plain_c_program_links_and_calls_the_library(libpath, tmp_path):
+    """The ABI is usable from C: a C11 program includes ml.h, links the
+    shared library and gets the documented statuses (calls that need no GPU)."""
+    src = tmp_path / "caller.c"
+    src.write_text(_CALLER_C)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(libpath)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe), "-L", libdir, "-l:" + os.path.basename(libpath),
+                    "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "abi_version" in r.stdout
