@@ -567,7 +567,8 @@ def cic_grad_dM(g: Geometry, x, y, m, dL_dM, ray_begin=0, ray_end=None, threads=
                             _ptr(G, C.c_double), cic_mu_scale(g), _ptr(gl, C.c_double),
                             _ptr(gp, C.c_double), threads or default_threads())
     if rc != 0:
-        raise ValueError("the oracle's CIC gradient covers the constant-(kappa, gamma) macro only")
+        raise ValueError("the oracle's CIC gradient covers the constant-(kappa, gamma) macro "
+                         "with a disc sheet only")
     return gl, gp
 
 
@@ -587,7 +588,8 @@ def cic_grad(g: Geometry, x, y, m, target, ray_begin=0, ray_end=None, threads=No
                             _ptr(G, C.c_double), cic_mu_scale(g), _ptr(gl, C.c_double),
                             _ptr(gp, C.c_double), threads or default_threads())
     if rc != 0:
-        raise ValueError("the oracle's CIC gradient covers the constant-(kappa, gamma) macro only")
+        raise ValueError("the oracle's CIC gradient covers the constant-(kappa, gamma) macro "
+                         "with a disc sheet only")
     return gl, gp
 
 

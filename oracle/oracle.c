@@ -554,6 +554,7 @@ int orc_cic_grad(const orc_geom *g, const double *x, const double *y, const doub
                  double scale, double *glens, double *gpar, int nthreads)
 {
     if (g->macro_mode != 0) return -2;     /* kappa, gamma terms are those of Eq. 1 */
+    if (g->sheet_shape != 0) return -3;    /* dbeta/dkappa_* above is the disc sheet's */
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     double **gl = (double **)calloc((size_t)nthreads, sizeof(double *));

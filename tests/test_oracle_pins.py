@@ -272,6 +272,87 @@ def test_cic_conserves_rays_in_interior():
     assert abs(M.sum() - g.n_rays) < 1e-8
 
 
+def _one_ray_cic(bx, by):
+    """CIC map of a single ray placed at source position (bx, by): no lenses,
+    kappa = gamma = kappa_* = 0 (beta = theta), one lattice ray at the centre
+    of its ray box, an 8 x 8 map of unit pixels over [0, 8]^2."""
+    g = _geom(0.0, 0.0, 0.0, [], [], (0, 0, 1), (0.0, 0.0, 8.0, 8.0), (8, 8),
+              ray_box=(bx - 0.25, by - 0.25, bx + 0.25, by + 0.25), ray_n=(1, 1))
+    return oracle.cic_forward(g, NO, NO, NO)
+
+
+@pytest.mark.parametrize("bx, by, want", [
+    # pixel (i, j) has its centre at (i + 1/2, j + 1/2); a ray at x shares
+    # 1 - |x - centre| with each of the two nearest centres along x, by hand:
+    # x = 2.75 -> centres 2.5 (0.75) and 3.5 (0.25); y = 3.25 -> 2.5 (0.25), 3.5 (0.75)
+    (2.75, 3.25, {(2, 2): 0.75 * 0.25, (3, 2): 0.25 * 0.25, (2, 3): 0.75 * 0.75, (3, 3): 0.25 * 0.75}),
+    # x = 5.125 -> 4.5 (0.375), 5.5 (0.625); y = 1.625 -> 1.5 (0.875), 2.5 (0.125)
+    (5.125, 1.625, {(4, 1): 0.375 * 0.875, (5, 1): 0.625 * 0.875, (4, 2): 0.375 * 0.125,
+                    (5, 2): 0.625 * 0.125}),
+    # a corner ray: only centre (0.5, 0.5) is in the map, weight 0.75 * 0.75;
+    # the other three centres lie outside and their weights are dropped
+    (0.25, 0.25, {(0, 0): 0.75 * 0.75}),
+    # on the last column's centre line: all of x goes to column 7
+    (7.5, 4.0, {(7, 3): 0.5, (7, 4): 0.5}),
+])
+def test_cic_single_ray_weights_by_hand(bx, by, want):
+    """The four bilinear weights of one ray against hand-computed values:
+    pixel centres at half-integers, and the weight along x going to the
+    nearer centre (a dropped -1/2 or swapped neighbours fail here)."""
+    M = _one_ray_cic(bx, by)
+    expect = np.zeros((8, 8))
+    for (i, j), v in want.items():
+        expect[j, i] = v
+    assert np.array_equal(M, expect), np.argwhere(M != expect)
+
+
+def _tent_weights_1d(centres, positions, spacing):
+    """Sum over positions of the tent kernel max(0, 1 - |p - c| / spacing) at
+    each centre, in exact rational arithmetic."""
+    from fractions import Fraction
+    out = []
+    for c in centres:
+        s = Fraction(0)
+        for p in positions:
+            s += max(Fraction(0), 1 - abs(Fraction(p) - Fraction(c)) / Fraction(spacing))
+        out.append(s)
+    return np.array([float(v) for v in out])
+
+
+def test_cic_dyadic_lattice_is_the_tent_kernel_sum():
+    """No lenses, kappa = gamma = 1/4 (beta = (theta_x / 2, theta_y)): every
+    lattice ray lands at a dyadic fraction of a pixel, and the CIC map equals,
+    pixel by pixel, the outer product of the per-axis sums of the tent kernel
+    over the rays' source positions (the definition of cloud-in-cell
+    weights), computed exactly.  Interior pixels get exactly the rays per
+    pixel (16); edge pixels lose the weight of centres outside the map."""
+    g = _geom(0.25, 0.25, 0.0, [], [], (0, 0, 1), (-1.0, -0.5, 1.0, 0.5), (16, 8),
+              ray_box=(-2.0, -0.5, 2.0, 0.5), ray_n=(64, 32))
+    M = oracle.cic_forward(g, NO, NO, NO)
+    dp = 0.125
+    bx = [0.5 * (-2.0 + (i + 0.5) * 4.0 / 64) for i in range(64)]    # beta_x = theta_x / 2
+    by = [-0.5 + (j + 0.5) / 32 for j in range(32)]                  # beta_y = theta_y
+    wx = _tent_weights_1d([-1.0 + (i + 0.5) * dp for i in range(16)], bx, dp)
+    wy = _tent_weights_1d([-0.5 + (j + 0.5) * dp for j in range(8)], by, dp)
+    assert np.array_equal(M, np.outer(wy, wx))
+    # 4 source positions per pixel along each axis: interior 4, edges 3.5
+    assert np.all(wx[1:-1] == 4.0) and np.all(wy[1:-1] == 4.0)
+    assert wx[0] == wx[-1] == 3.5 and wy[0] == wy[-1] == 3.5
+
+
+def test_cic_gradient_refuses_the_strip_sheet():
+    """dbeta/dkappa_* in the oracle's adjoint is the disc sheet's; a strip
+    sheet is refused rather than given the disc's derivative."""
+    lf = inputs.lens_disc(4, 3.0, 7, "lognormal")
+    g = _geom(0.3, 0.2, 0.05, lf.x, lf.y, (0, 0, 3.0, "strip"), (-1.0, -1.0, 1.0, 1.0), (8, 8),
+              ray_box=(-2, -2, 2, 2), ray_n=(40, 40))
+    assert g.sheet_shape == 1
+    with pytest.raises(ValueError):
+        oracle.cic_grad_dM(g, lf.x, lf.y, lf.m, np.ones((8, 8)))
+    g.sheet_shape = 0
+    oracle.cic_grad_dM(g, lf.x, lf.y, lf.m, np.ones((8, 8)))
+
+
 def test_cic_gradient_matches_finite_differences():
     lf = inputs.lens_disc(6, 5.0, 7, "lognormal")
     lt = inputs.lens_disc(6, 5.0, 8, "lognormal")
