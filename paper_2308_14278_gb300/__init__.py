@@ -193,12 +193,24 @@ def ml_magnification_map(field, want: int, out, stream=None):
         _check(load().ml_magnification_map(field, want, _dptr(out), 1, _stream(stream)))
 
 
+def _check_curves_out(out, n_tracks: int, n_samples: int):
+    """The light-curve kernels write n_tracks x n_samples float32 values."""
+    import torch
+    if out.dtype != torch.float32:
+        raise ValueError(f"light curves are float32, got {out.dtype}")
+    if out.numel() < n_tracks * n_samples:
+        raise ValueError(f"out holds {out.numel()} values, {n_tracks} x {n_samples} needed")
+
+
 def ml_light_curves(field, tracks, n_samples: int, sigma_px: float, out, stream=None):
     tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
     if isinstance(out, np.ndarray):
+        if out.dtype != np.float32 or out.size < len(tr) * n_samples or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float32 array of n_tracks x n_samples")
         _check(load().ml_light_curves(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
                                       out.ctypes.data, 0, _stream(stream)))
     else:
+        _check_curves_out(out, len(tr), n_samples)
         _check(load().ml_light_curves(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
                                       _dptr(out), 1, _stream(stream)))
 
@@ -207,6 +219,7 @@ def ml_light_curves_noalloc(field, tracks, n_samples: int, sigma_px: float, out,
     """Light curves into a device tensor without any allocation in the
     library (for callers that must not allocate device memory; see ml.h)."""
     tr = np.ascontiguousarray(tracks, np.float64).reshape(-1, 4)
+    _check_curves_out(out, len(tr), n_samples)
     _check(load().ml_light_curves_noalloc(field, tr.ctypes.data, len(tr), n_samples, sigma_px,
                                           _dptr(out), _stream(stream)))
 
@@ -260,6 +273,7 @@ def ml_map_light_curves(mu, tracks, n_samples, sigma_px, out, stream=None):
     """Light curves of a device float32 map (see ml.h)."""
     tr, ptr = _tracks_host(tracks)
     ny, nx = mu.shape
+    _check_curves_out(out, len(tr), n_samples)
     _check(load().ml_map_light_curves(_dptr(mu), nx, ny, ptr, len(tr), n_samples, sigma_px,
                                       _dptr(out), _stream(stream)))
 

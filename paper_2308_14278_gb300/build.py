@@ -6,6 +6,7 @@ shared library with the C ABI of include/ml.h.  Nothing else is built here.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import json
 import os
 import shutil
 import subprocess
@@ -39,16 +40,31 @@ def _deps():
     return deps
 
 
-def up_to_date() -> bool:
+STAMP = LIB + ".flags"
+
+
+def built_flags():
+    """The extra nvcc flags the current _build/libml.so was compiled with
+    (None if there is no library or no record of them)."""
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return None
+    with open(STAMP) as fh:
+        return json.load(fh)
+
+
+def up_to_date(extra_flags=()) -> bool:
     if not os.path.exists(LIB):
+        return False
+    if built_flags() != list(extra_flags):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
 def build_library(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Build _build/libml.so unless it is newer than every source."""
-    if not force and up_to_date():
+    """Build _build/libml.so unless it is newer than every source and was
+    built with the same extra flags (recorded next to it in libml.so.flags)."""
+    if not force and up_to_date(extra_flags):
         return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
@@ -73,6 +89,9 @@ def build_library(force: bool = False, verbose: bool = False, extra_flags=()) ->
     tmp = LIB + f".{os.getpid()}.tmp"
     run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp", "w") as fh:
+        json.dump(list(extra_flags), fh)
+    os.replace(STAMP + ".tmp", STAMP)
     return LIB
 
 

@@ -139,7 +139,10 @@ __global__ void k_light_curves(Geo g, const uint32_t *__restrict__ cu, const flo
     out[q] = (float)(acc * scale);
 }
 
-static int gaussian_taps(double sigma_px, float taps[129])
+// Normalised Gaussian source taps of §4.1 at integer offsets |t| <= floor(4 sigma),
+// truncated there and scaled to sum 1; one function for every light-curve path
+// so that they agree bit for bit.  Returns the half-width h, or -1 above 64.
+int light_curve_taps(double sigma_px, float taps[129])
 {
     int h = (int)floor(4.0 * sigma_px);
     if (h > 64) return -1;
@@ -189,7 +192,7 @@ cudaError_t launch_light_curves_noalloc(const Geo &g, const uint32_t *cu, const 
                                         int n_samples, double sigma_px, float *out, cudaStream_t s)
 {
     float taps[129];
-    int h = gaussian_taps(sigma_px, taps);
+    int h = light_curve_taps(sigma_px, taps);
     if (h < 0 || n_tracks > ML_NOALLOC_MAX_TRACKS) return cudaErrorInvalidValue;
     unsigned char *base = nullptr;
     cudaError_t e = lc_scratch_address(&base);
@@ -211,15 +214,9 @@ cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *c
                                 const double *tracks, int n_tracks, int n_samples,
                                 double sigma_px, float *out, cudaStream_t s)
 {
-    int h = (int)floor(4.0 * sigma_px);
-    if (h > 64) return cudaErrorInvalidValue;
     float taps[129];
-    double sum = 0.0, w[129];
-    for (int t = -h; t <= h; ++t) {
-        w[t + h] = exp(-0.5 * ((double)t / sigma_px) * ((double)t / sigma_px));
-        sum += w[t + h];
-    }
-    for (int t = 0; t <= 2 * h; ++t) taps[t] = (float)(w[t] / sum);
+    int h = light_curve_taps(sigma_px, taps);
+    if (h < 0) return cudaErrorInvalidValue;
     float *d_taps = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&d_taps, sizeof(float) * (2 * h + 1), s);
     if (e != cudaSuccess) return e;
@@ -235,19 +232,6 @@ cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *c
 
 // Light curves with the taps and tracks already on the device (the batched
 // step, which is captured in a CUDA graph and must not allocate).
-int light_curve_taps(double sigma_px, float taps[129])
-{
-    int h = (int)floor(4.0 * sigma_px);
-    if (h > 64) return -1;
-    double sum = 0.0, w[129];
-    for (int t = -h; t <= h; ++t) {
-        w[t + h] = exp(-0.5 * ((double)t / sigma_px) * ((double)t / sigma_px));
-        sum += w[t + h];
-    }
-    for (int t = 0; t <= 2 * h; ++t) taps[t] = (float)(w[t] / sum);
-    return h;
-}
-
 cudaError_t launch_light_curves_dev(const Geo &g, const uint32_t *cu, const float *cf, double scale,
                                     const double *d_tracks, int n_tracks, int n_samples, int h,
                                     const float *d_taps, float *out, cudaStream_t s)
@@ -493,7 +477,7 @@ cudaError_t launch_light_curves_adj(int mnx, int mny, const double *d_tracks, in
                                     cudaStream_t s)
 {
     float taps[129];
-    const int h = gaussian_taps(sigma_px, taps);
+    const int h = light_curve_taps(sigma_px, taps);
     if (h < 0) return cudaErrorInvalidValue;
     float *d_taps = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&d_taps, sizeof(float) * (2 * h + 1), s);

@@ -7,6 +7,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 import paper_2308_14278_gb300 as ml
@@ -231,3 +232,19 @@ def test_plain_c_program_links_and_calls_the_library(libpath, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert "abi_version" in r.stdout
+
+
+@pytest.mark.parametrize("entry", ["ml_light_curves", "ml_light_curves_noalloc", "ml_map_light_curves"])
+def test_light_curve_outputs_are_checked_before_any_call(libpath, entry):
+    """A device output of the wrong dtype or too few values is refused in the
+    binding, before the library would write n_tracks x n_samples float32s."""
+    import torch
+    tracks = np.array([[1.0, 1.0, 5.0, 5.0], [2.0, 2.0, 6.0, 3.0]])
+    for out in (torch.empty((2, 16), dtype=torch.float64), torch.empty((2, 15), dtype=torch.float32)):
+        with pytest.raises(ValueError):
+            if entry == "ml_map_light_curves":
+                ml.ml_map_light_curves(torch.zeros((8, 8)), tracks, 16, 0.5, out)
+            else:
+                getattr(ml, entry)(None, tracks, 16, 0.5, out)
+    with pytest.raises(ValueError):
+        ml.ml_light_curves(None, tracks, 16, 0.5, np.zeros((2, 15), np.float32))

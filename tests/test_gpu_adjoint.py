@@ -196,6 +196,52 @@ def test_cic_stripe_of_the_differentiable_field_matches_oracle(ml):
     f.close()
 
 
+def test_cic_adjoint_on_a_stripe_of_the_differentiable_field_matches_oracle(ml):
+    """ml_cic_backward (near/far and direct) against the oracle's FP64
+    gradient on a field whose lattice is 64 rows of the differentiable
+    field's, starting on a level-1 row boundary, with the same level-1 cells
+    (2.5 theta_E) and level-2 subdivisions (10, 10): nine tasks in ten have
+    no near lens, so the adjoint's zero- and one-lens pair walks run as they
+    do on the full field."""
+    import dataclasses
+    import torch
+    full = inputs.differentiable_field(0)
+    f0 = _field(ml, full)
+    fi = f0.info
+    f0.close()
+    rows = 64
+    j0 = fi["n1y"] * (fi["N1y"] // 2)
+    ry0 = fi["ray_y0"] + j0 * fi["l3y"]
+    w = dataclasses.replace(full, ray_box=(fi["ray_x0"], ry0, fi["ray_x1"], ry0 + rows * fi["l3y"]),
+                            ray_n=(fi["n_rays_x"], rows), n_av=0.0,
+                            l1=(fi["n1x"] * fi["l3x"], fi["n1y"] * fi["l3y"]))
+    f = _field(ml, w)
+    info = f.info
+    for k in ("n1x", "n1y", "n2x", "n2y", "l2_sub_x", "l2_sub_y"):
+        assert info[k] == fi[k], k
+    assert info["far_bound"] <= 1e-7
+    g = oracle.geometry_of(w, p=info["taylor_p"], l2_sub=info["l2_sub_x"], l2_sub_y=info["l2_sub_y"])
+    assert (g.n1x, g.n1y, g.n2x, g.n2y) == (info["n1x"], info["n1y"], info["n2x"], info["n2y"])
+    f.shoot()
+    st = f.stats()
+    assert st["rays_dropped"] == 0 and st["rays_in"] > 0.5 * f.n_rays
+    assert 0.02 < st["near_pairs"] / f.n_rays < 0.5
+    G = torch.randn(w.map_n[::-1], generator=torch.Generator().manual_seed(5))
+    gl_ref, gp_ref = oracle.cic_grad_dM(g, w.lenses.x, w.lenses.y, w.lenses.m, G.double().numpy())
+    Gd = G.cuda().contiguous()
+    for method in (ml.ADJOINT_NEARFAR, ml.ADJOINT_DIRECT):
+        gl = torch.empty((w.lenses.n, 3), dtype=torch.float64, device="cuda")
+        gp = torch.empty(3, dtype=torch.float64, device="cuda")
+        ml.ml_cic_backward(f.h, Gd, gl, gp, method=method)
+        gl, gp = gl.cpu().numpy(), gp.cpu().numpy()
+        for c in range(3):
+            scale = np.abs(gl_ref[:, c]).max()
+            err = np.abs(gl[:, c] - gl_ref[:, c]).max() / scale
+            assert err <= 1e-4, (method, c, err)
+        assert np.all(np.abs(gp - gp_ref) <= 1e-4 * np.abs(gp_ref)), (method, gp, gp_ref)
+    f.close()
+
+
 def test_nearfar_adjoint_agrees_with_direct_at_full_size(ml):
     """1,000 lenses, 4e8 rays, 1024^2 CIC: the moment-based adjoint (far
     lenses through the node series) against every ray times every lens with

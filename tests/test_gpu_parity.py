@@ -138,6 +138,34 @@ def test_hierarchical_build_matches_direct(ml, case):
     fh.close()
 
 
+@pytest.mark.parametrize("case", ["paper", "table1"])
+def test_hierarchical_build_matches_interp_oracle(ml, case):
+    """The default hierarchical build traced in the FP64 near/far mode against
+    the oracle's near/far scheme (oracle.beta_interp: the node series of each
+    ray from a direct sum over the far lenses, §3.2 Level 2), on the
+    paper-scale field and on the Table-1 fold field: both evaluate the same
+    truncated series, so they agree to FP64 rounding of the sums."""
+    if case == "paper":
+        w = inputs.paper_map(0, n_rays=1e10, map_px=2048)
+        kw = {}
+    else:
+        w = inputs.fold_field(0, n_rays=2e9, map_px=(512, 2560))
+        kw = dict(l2_sub=(4, 4))
+    f = _field(ml, w, precision=ml.PREC_NEARFAR64, taylor_p=8, build=ml.BUILD_HIERARCHICAL, **kw)
+    info = f.info
+    assert info["build"] == ml.BUILD_HIERARCHICAL and info["taylor_p"] == 8
+    g = oracle.geometry_of(w, p=8, l2_sub=info["l2_sub_x"], l2_sub_y=info["l2_sub_y"],
+                           l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]))
+    _check_geometry(f, g)
+    idx = np.unique(np.random.default_rng(4).integers(0, g.n_rays, 20000))
+    beta, _ = f.trace(idx)
+    ref, flag = oracle.beta_interp(g, w.lenses.x, w.lenses.y, w.lenses.m, idx)
+    assert not flag.any()
+    err = np.abs(beta.cpu().numpy() - ref).max()
+    assert err <= 1e-9, err
+    f.close()
+
+
 def test_nearfar64_map_matches_interp_oracle_stripe(ml):
     lf = inputs.lens_disc(60, 8.0, 4, "lognormal")
     w = inputs.Workload("t", lf, 0.42, 0.31, 0.03, (0.0, 0.0, 8.0), (-1.5, -1.2, 1.7, 1.4),
@@ -211,6 +239,76 @@ def test_mixed_trace_deflection_and_bins(ml, l2_sub):
     dist = _edge_distance_px(g, ref)
     err_px = np.maximum(np.abs(beta - ref)[:, 0] / g.dpx, np.abs(beta - ref)[:, 1] / g.dpy)
     assert np.all(same | (dist <= err_px * (1 + 1e-6) + 1e-9))
+    f.close()
+
+
+def _traced_counts(ml, f, r0, r1, chunk=1 << 22):
+    """Histogram of the pixels ml_trace_rays gives every ray of [r0, r1),
+    with the number of rays outside the map and of dropped rays."""
+    import torch
+    nx, ny = f.info["map_nx"], f.info["map_ny"]
+    counts = torch.zeros(nx * ny, dtype=torch.int64, device="cuda")
+    n_out = n_drop = 0
+    for a in range(r0, r1, chunk):
+        idx = torch.arange(a, min(r1, a + chunk), dtype=torch.int64, device="cuda")
+        beta = torch.empty((idx.numel(), 2), dtype=torch.float64, device="cuda")
+        pix = torch.empty((idx.numel(), 2), dtype=torch.int32, device="cuda")
+        ml.ml_trace_rays(f.h, idx, beta, pix)
+        inside = pix[:, 0] >= 0
+        flat = pix[inside, 1].to(torch.int64) * nx + pix[inside, 0].to(torch.int64)
+        counts += torch.bincount(flat, minlength=nx * ny)
+        n_out += int((pix[:, 0] == -1).sum())
+        n_drop += int((pix[:, 0] == -2).sum())
+    return counts.view(ny, nx).cpu().numpy(), n_out, n_drop
+
+
+def _shot_equals_traced(ml, f, r0, r1):
+    f.clear()
+    f.shoot(r0, r1)
+    shot = f.counts().cpu().numpy().view(np.uint32).astype(np.int64)
+    st = f.stats()
+    traced, n_out, n_drop = _traced_counts(ml, f, r0, r1)
+    assert np.array_equal(shot, traced), int(np.abs(shot - traced).sum())
+    assert (st["rays_in"], st["rays_out"], st["rays_dropped"]) == (int(traced.sum()), n_out, n_drop)
+    return st
+
+
+@pytest.mark.parametrize("l2_sub", [(20, 20), (60, 20)])
+def test_shot_map_is_the_histogram_of_traced_pixels(ml, l2_sub):
+    """The shooting kernel's counts equal, pixel for pixel, the histogram of
+    the pixels the tracing kernel gives each ray one by one.  The tracer's
+    per-ray pixels are the ones the edge criterion above checks against the
+    oracle, so this carries that criterion over to every ray the shooting
+    kernel deposits (its two-lane Horner chains, raw-bit pixel comparisons
+    and run lengths included)."""
+    w = _mixed_case()
+    f = _field(ml, w, precision=ml.PREC_MIXED, l2_sub=l2_sub)
+    n = f.n_rays
+    st = _shot_equals_traced(ml, f, 0, n)
+    assert st["rays_in"] > 0.05 * n and st["near_pairs"] > 0
+    # ragged ranges: a partial first and last row, and a range inside one row
+    nx3 = f.info["n_rays_x"]
+    _shot_equals_traced(ml, f, 5 * nx3 + 17, 70 * nx3 + 3)
+    _shot_equals_traced(ml, f, 40 * nx3 + 100, 40 * nx3 + 900)
+    f.close()
+
+
+@pytest.mark.parametrize("case", ["paper", "table1"])
+def test_shot_stripe_is_the_histogram_of_traced_pixels(ml, case):
+    """The same on 41 lattice rows of the paper-scale field (1e11-ray
+    lattice, autotuned grid, as the benchmark runs it) and 64 rows of the
+    Table-1 fold field (2.3 near lenses per ray: long near lists and close
+    passes), both from a ragged start."""
+    if case == "paper":
+        w, rows = inputs.paper_map(0), 40
+    else:
+        w, rows = inputs.fold_field(0, n_rays=2e10, map_px=(1024, 5120)), 64
+    f = _field(ml, w, precision=ml.PREC_MIXED, tune=True)
+    nx3, ny3 = f.info["n_rays_x"], f.info["n_rays_y"]
+    r0 = (ny3 // 2) * nx3 + 777
+    r1 = r0 + rows * nx3 + 12345
+    st = _shot_equals_traced(ml, f, r0, r1)
+    assert st["rays_in"] > 0.5 * (r1 - r0) and st["near_pairs"] > 0
     f.close()
 
 
