@@ -43,7 +43,7 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # sources whose code (comments and blank space left out, code_hash) has these
 # sha1 prefixes only.
 TRAFFIC_BYTES_PER_RAY = 484.152832e6 / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "e6acd6aa", "ml_internal.cuh": "d7296fe1", "ml_task.cuh": "3d1d5136"}
+TRAFFIC_SOURCES = {"ml_shoot.cu": "e6acd6aa", "ml_internal.cuh": "8235950f", "ml_task.cuh": "3d1d5136"}
 
 
 # The library's kernels in one field build: k_lens_cells, k_scan, k_scatter,
@@ -119,6 +119,9 @@ def parse():
     ap.add_argument("--grid", default="",
                     help="profiling: fix the grid the autotuner chose, 'L1X,L1Y,SX,SY' (level-1 "
                          "cell size in theta_E, level-2 subdivisions), instead of tuning again")
+    ap.add_argument("--walk", default="certified", choices=["certified", "per_ray"],
+                    help="ray walk of the counting kernel: certified spans (default) or every "
+                         "ray evaluated; both give bit-identical maps")
     ap.add_argument("--shoot-rays", type=float, default=0,
                     help="profiling: shoot only this many rays (a centred slice of the lattice) "
                          "per step; the default shoots them all")
@@ -128,11 +131,13 @@ def parse():
 def grid_kwargs(args, w):
     """Field keyword arguments for the grid: the autotuner's (default), the
     paper's (--no-tune) or a fixed one (--grid, which sets w.l1)."""
+    import paper_2308_14278_gb300 as ml
+    walk = ml.WALK_PER_RAY if getattr(args, "walk", "certified") == "per_ray" else ml.WALK_CERTIFIED
     if not args.grid:
-        return dict(tune=not args.no_tune)
+        return dict(tune=not args.no_tune, walk=walk)
     l1x, l1y, sx, sy = (float(v) for v in args.grid.split(","))
     w.l1 = (l1x, l1y)
-    return dict(tune=False, l2_sub=(int(sx), int(sy)))
+    return dict(tune=False, l2_sub=(int(sx), int(sy)), walk=walk)
 
 
 def dist_env():
@@ -151,11 +156,11 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int, directory: str | None = None):
+    def __init__(self, index: int, directory: str | None = None, tag: str = ""):
         self.index = index
         self.proc = None
         d = directory or os.path.join(tempfile.gettempdir(), f"ml_bench_clocks_{os.getpid()}")
-        self.path = os.path.join(d, f"clocks_rank{index}.csv")
+        self.path = os.path.join(d, f"clocks{tag}_rank{index}.csv")
 
     def __enter__(self):
         try:
@@ -199,6 +204,42 @@ class ClockSampler:
         load = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(mx)),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# measured FP32 peak
+# ---------------------------------------------------------------------------
+
+PEAK_ITERS = 1 << 21
+
+
+def measure_fp32_peak(ml, torch, stream, local, clocks_dir=None, launches=5):
+    """FP32 FMA throughput of this GPU measured by the library's probe
+    (ml_fp32_fma_peak: 4 blocks of 256 threads per SM, eight independent FMA
+    chains per thread), best of `launches` CUDA-event-timed launches for
+    scalar FFMA and for the two-lane fma.rn.f32x2, with the SM clock sampled
+    meanwhile.  TFLOP/s, 2 flop per FMA."""
+    sink = torch.zeros(8 * 1024, dtype=torch.float32, device=f"cuda:{local}")
+    out = {}
+    with ClockSampler(local, clocks_dir, tag="_fp32peak") as clk:
+        for two in (False, True):
+            ml.ml_fp32_fma_peak(two, 4, 1 << 12, sink, stream)        # warm-up
+            best = 0.0
+            for _ in range(launches):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                flop = ml.ml_fp32_fma_peak(two, 4, PEAK_ITERS, sink, stream)
+                e1.record(stream)
+                e1.synchronize()
+                best = max(best, flop / (e0.elapsed_time(e1) / 1e3) / 1e12)
+            out["two_lane_tflops" if two else "scalar_tflops"] = best
+        torch.cuda.synchronize()
+    c = clk.summary()
+    if c:
+        out["sm_mhz"] = c["sm_mhz"]
+        out["reasons"] = c["reasons"]
+    out["derived_tflops_at_max_clock"] = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return out
 
 
 # ---------------------------------------------------------------------------

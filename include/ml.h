@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-#define ML_ABI_VERSION 3
+#define ML_ABI_VERSION 4
 
 typedef enum {
     ML_OK = 0,
@@ -74,6 +74,23 @@ typedef enum {
 #define ML_STAT_LAUNCHES    5  /* shooting kernel launches */
 #define ML_STAT_FLAGS       6  /* bit 0: count overflow, bit 1: aborted */
 #define ML_STAT_RAYS_ASKED  7  /* rays requested by ml_shoot_rays so far */
+#define ML_STAT_RAYS_EVAL   8  /* mixed NGP mode: rays whose source position was evaluated
+                                  one by one (the rest were certified, see ML_WALK_CERTIFIED) */
+#define ML_STAT_SPANS       9  /* mixed NGP mode: spans of rays certified to share a pixel */
+#define ML_STAT_COUNT      10  /* length of the ml_field_stats array */
+
+/* Ray walks of the mixed mode's NGP counts (ml_field_desc.walk).  Both give
+ * every ray the pixel of the same per-ray FP32 arithmetic (Eq. 9), so their
+ * count maps are bit-identical.
+ *  ML_WALK_CERTIFIED (0, default): along a lattice row a lane evaluates a
+ *    probe ray ahead of its last evaluated ray; when both land in one pixel
+ *    and a rigorous bound (FP32 rounding of the evaluation, plus the
+ *    curvature of the row's deflection between them) shows that every ray
+ *    between them lands there too, those rays are counted without being
+ *    evaluated.  Otherwise the probe moves closer, down to the next ray.
+ *  ML_WALK_PER_RAY (1): every ray is evaluated. */
+#define ML_WALK_CERTIFIED 0
+#define ML_WALK_PER_RAY   1
 
 typedef struct ml_field ml_field;  /* opaque, owned by the library */
 
@@ -136,7 +153,7 @@ typedef struct {
                                    far_tol.  The choice is cached per process for the same
                                    descriptor and lenses; ML_TUNE_LOG=1 in the environment
                                    prints the timed candidates. */
-    int32_t reserved0;
+    int32_t walk;               /* ML_WALK_*; default ML_WALK_CERTIFIED */
 
     /* Macro model.  ML_MACRO_LINEAR (0): the constant-(kappa, gamma) form of
      * Eq. 1 above.  ML_MACRO_FOLD (1): the fold near the critical curve, Eq. 5
@@ -442,14 +459,14 @@ ml_status ml_field_clear(ml_field *f, void *stream);
 
 /*
  * ml_field_stats - synchronise `stream` and copy the field's counters
- * (ML_STAT_* indices) into out[8] (host).  For a uint32 count map it also
+ * (ML_STAT_* indices) into out[ML_STAT_COUNT] (host).  For a uint32 count map it also
  * sums the map in 64 bits (one pass over the map): a pixel that wrapped
  * makes that sum fall short of the in-map ray count, which sets flag bit 0.
  * Returns ML_ERR_OVERFLOW or ML_ERR_ABORTED when the corresponding flag is
  * set, after filling out.  The counts check ray conservation (every lattice
  * ray of §3.2 Level 3 is in the map, out of it or dropped).
  */
-ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream);
+ml_status ml_field_stats(ml_field *f, uint64_t out[ML_STAT_COUNT], void *stream);
 
 /* ml_field_info - copy the derived parameters (§3.1-§3.2: ray rectangle,
  * lattice, level grids, Taylor order, S_I/S_S of Eq. 12) into *out (host). */
@@ -524,6 +541,23 @@ ml_status ml_batch_destroy(ml_batch *b);
 /* Message of the last failed call on this thread ("" if none).  Bookkeeping;
  * no counterpart in the paper. */
 const char *ml_last_error(void);
+
+/*
+ * ml_fp32_fma_peak - one launch of an FP32 fused multiply-add throughput
+ * probe, the measured denominator of the shooting kernels' roofline.  The
+ * paper has no counterpart: it is a measurement helper.  SMs x blocks_per_sm
+ * blocks of 256 threads each run eight independent chains of `iters` FMAs
+ * (a <- a b + c), as scalar FFMA (two_lane = 0) or as the two-lane
+ * fma.rn.f32x2 instruction (two_lane = 1, two FMAs per instruction).
+ *  sink:  device, >= 8 x SMs floats; written only if a chain reached an
+ *         impossible value (keeps the chains from being optimised away).
+ *  flop:  host, receives the launch's flop count (2 per FMA).
+ * The caller times the launch on `stream` (CUDA events) and divides.
+ * Errors: ML_ERR_INVALID_ARG (NULL, blocks_per_sm outside [1, 8], iters
+ * outside [1, 2^32]); ML_ERR_CUDA.
+ */
+ml_status ml_fp32_fma_peak(int32_t two_lane, int32_t blocks_per_sm, int64_t iters, float *sink,
+                           double *flop, void *stream);
 
 /* ABI version the library was built with (ML_ABI_VERSION).  Bookkeeping; no
  * counterpart in the paper. */

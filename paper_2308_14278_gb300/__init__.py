@@ -23,7 +23,7 @@ from . import inputs  # noqa: F401  (seeded synthetic inputs, no method arithmet
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libml.so")
 
-ABI_VERSION = 3
+ABI_VERSION = 4
 PREC_DIRECT64, PREC_NEARFAR64, PREC_MIXED = 0, 1, 2
 DEPOSIT_NGP, DEPOSIT_CIC = 0, 1
 MACRO_LINEAR, MACRO_FOLD = 0, 1
@@ -31,7 +31,8 @@ SHEET_DISC, SHEET_STRIP = 0, 1
 BUILD_AUTO, BUILD_DIRECT, BUILD_HIERARCHICAL = 0, 1, 2
 MAP_COUNTS_U32, MAP_MU_F32, MAP_MU_F64 = 0, 1, 2
 STAT_NAMES = ("rays_in", "rays_out", "rays_dropped", "near_pairs", "tasks", "launches",
-              "flags", "rays_asked")
+              "flags", "rays_asked", "rays_evaluated", "spans")
+WALK_CERTIFIED, WALK_PER_RAY = 0, 1
 STATUS = {0: "ML_OK", 1: "ML_ERR_INVALID_ARG", 2: "ML_ERR_OOM", 3: "ML_ERR_CUDA",
           4: "ML_ERR_ABORTED", 5: "ML_ERR_OVERFLOW", 6: "ML_ERR_STATE", 7: "ML_ERR_UNSUPPORTED"}
 
@@ -43,7 +44,7 @@ EXPORTS = ("ml_abi_version", "ml_last_error", "ml_field_create", "ml_shoot_rays"
            "ml_batch_mu", "ml_batch_curves", "ml_batch_abort", "ml_batch_destroy",
            "ml_cic_forward", "ml_cic_backward", "ml_cic_backward_ex", "ml_map_light_curves",
            "ml_map_light_curves_backward", "ml_field_set_counts", "ml_find_peaks",
-           "ml_peak_statistics")
+           "ml_peak_statistics", "ml_fp32_fma_peak")
 NOALLOC_MAX_TRACKS = 16384
 
 
@@ -69,7 +70,7 @@ class FieldDesc(C.Structure):
         ("map_y1", C.c_double), ("map_nx", C.c_int32), ("map_ny", C.c_int32),
         ("l1_x", C.c_double), ("l1_y", C.c_double), ("l2_sub_x", C.c_int32),
         ("l2_sub_y", C.c_int32), ("far_tol", C.c_double), ("max_launch_rays", C.c_uint64),
-        ("tune", C.c_int32), ("reserved0", C.c_int32),
+        ("tune", C.c_int32), ("walk", C.c_int32),
         ("macro_mode", C.c_int32), ("sheet_shape", C.c_int32),
         ("kappa0", C.c_double), ("d_x", C.c_double), ("d_y", C.c_double),
     ]
@@ -136,6 +137,7 @@ def load(path: str | None = None):
         "ml_peak_statistics": ([V, C.c_int32, C.c_double, V, C.c_double, V, C.c_int32, V, V, V, V], st),
         "ml_map_light_curves": ([V, C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V], st),
         "ml_map_light_curves_backward": ([C.c_int32, C.c_int32, V, C.c_int32, C.c_int32, C.c_double, V, V, V], st),
+        "ml_fp32_fma_peak": ([C.c_int32, C.c_int32, C.c_int64, V, P(C.c_double), V], st),
         "ml_field_clear": ([V, V], st),
         "ml_field_stats": ([V, P(C.c_uint64), V], st),
         "ml_field_info": ([V, P(FieldParams)], st),
@@ -297,12 +299,20 @@ def ml_trace_rays(field, ray_idx, beta, pix, stream=None):
                                 _stream(stream)))
 
 
+def ml_fp32_fma_peak(two_lane: bool, blocks_per_sm: int, iters: int, sink, stream=None) -> float:
+    """One launch of the FP32 FMA throughput probe (see ml.h); returns its flop count."""
+    flop = C.c_double()
+    _check(load().ml_fp32_fma_peak(1 if two_lane else 0, blocks_per_sm, int(iters), _dptr(sink),
+                                   C.byref(flop), _stream(stream)))
+    return flop.value
+
+
 def ml_field_clear(field, stream=None):
     _check(load().ml_field_clear(field, _stream(stream)))
 
 
 def ml_field_stats(field, stream=None, check=True):
-    out = (C.c_uint64 * 8)()
+    out = (C.c_uint64 * len(STAT_NAMES))()
     st = load().ml_field_stats(field, out, _stream(stream))
     d = dict(zip(STAT_NAMES, list(out)))
     if check:
@@ -328,7 +338,7 @@ def ml_field_destroy(field):
 
 def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_AUTO,
               taylor_p=0, far_tol=0.0, l1=None, l2_sub=(0, 0), max_launch_rays=0, lens_arrays=None,
-              tune=False):
+              tune=False, walk=WALK_CERTIFIED):
     """ml_field_desc for an inputs.Workload (lens arrays from host numpy)."""
     w = workload
     lx, ly, lm = lens_arrays if lens_arrays is not None else (w.lenses.x, w.lenses.y, w.lenses.m)
@@ -361,6 +371,7 @@ def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_A
         l2_sub = w.l2
     d.l2_sub_x, d.l2_sub_y = l2_sub
     d.tune = 1 if tune else 0
+    d.walk = walk
     macro = getattr(w, "macro", None)
     if macro is not None:
         d.macro_mode = MACRO_FOLD

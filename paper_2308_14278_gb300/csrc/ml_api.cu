@@ -297,6 +297,8 @@ ml_status validate(const ml_field_desc *d)
         return fail(ML_ERR_INVALID_ARG, "unknown macro_mode");
     if (d->sheet_shape != ML_SHEET_DISC && d->sheet_shape != ML_SHEET_STRIP)
         return fail(ML_ERR_INVALID_ARG, "unknown sheet_shape");
+    if (d->walk != ML_WALK_CERTIFIED && d->walk != ML_WALK_PER_RAY)
+        return fail(ML_ERR_INVALID_ARG, "unknown walk");
     if (d->macro_mode == ML_MACRO_FOLD &&
         (!is_fin(d->kappa0) || !is_fin(d->d_x) || !is_fin(d->d_y) || d->kappa0 == 1.0 || d->d_x == 0.0))
         return fail(ML_ERR_INVALID_ARG, "fold macro needs finite kappa0 != 1 and d_x != 0");
@@ -415,6 +417,8 @@ uint64_t tune_key(const ml_field_desc &d, const std::vector<double> &hx, const s
     h = mix64(h, (uint64_t)d.n_rays_x); h = mix64(h, (uint64_t)d.n_rays_y);
     h = mix64(h, (uint64_t)d.map_nx); h = mix64(h, (uint64_t)d.map_ny);
     h = mix64(h, (uint64_t)d.taylor_p); h = mix64(h, (uint64_t)hx.size());
+    h = mix64(h, (uint64_t)d.walk); h = mix64(h, (uint64_t)d.macro_mode);
+    h = mix64(h, (uint64_t)d.sheet_shape); mixd(d.kappa0); mixd(d.d_x); mixd(d.d_y);
     for (size_t k = 0; k < hx.size(); ++k) { mixd(hx[k]); mixd(hy[k]); mixd(hm[k]); }
     return h;
 }
@@ -713,13 +717,13 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     ML_CK(f->alloc(&f->d_scell, n, s));
     ML_CK(f->alloc(&f->d_perm, n, s));
     ML_CK(f->alloc(&f->d_f32, 5 * n, s));
-    ML_CK(f->alloc(&f->d_stats, 8, s));
+    ML_CK(f->alloc(&f->d_stats, ML_STAT_COUNT, s));
     ML_CK(f->alloc(&f->d_sum, 1, s));
     ML_CK(f->alloc(&f->d_work, 1, s));
     ML_CK(f->alloc(&f->d_status, 1, s));
     ML_CK(flag_get(&f->h_abort, &f->d_abort));
     ML_CK(cudaMemsetAsync(f->d_count, 0, (NE + 1) * sizeof(int32_t), s));
-    ML_CK(cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s));
+    ML_CK(cudaMemsetAsync(f->d_stats, 0, ML_STAT_COUNT * sizeof(unsigned long long), s));
     ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
     ML_CK(launch_lens_cells(g, f->d_x, f->d_y, n, f->d_cell, f->d_count, s));
     ML_CK(launch_scan(f->d_count, f->d_start, NE + 1, s));
@@ -916,6 +920,7 @@ ShootArgs make_args(const ml_field *f)
     a.abort_flag = f->d_abort;
     const Geo &g = f->g;
     a.near_cap = std::max(1, f->max_near);
+    a.walk = f->desc.walk;
     a.l3x_f = (float)g.l3x;
     a.l3x_lo = (float)(g.l3x - (double)a.l3x_f);
     a.c0_f = (float)(0.5 - 0.5 * (double)g.n2x);
@@ -1032,7 +1037,7 @@ cudaError_t batch_enqueue(ml_batch *b, cudaStream_t s)
     for (ml_field *f : b->fields) {
         const size_t npix = (size_t)f->g.mnx * f->g.mny;
         if ((e = cudaMemsetAsync(f->d_map_u32, 0, npix * sizeof(uint32_t), s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(f->d_stats, 0, ML_STAT_COUNT * sizeof(unsigned long long), s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     }
     if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
@@ -1594,7 +1599,7 @@ ml_status ml_field_set_counts(ml_field *f, const uint32_t *counts, int32_t in_is
     if (!f->d_map_u32) return fail(ML_ERR_STATE, "a CIC field has no integer counts");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t npix = (size_t)f->g.mnx * f->g.mny;
-    unsigned long long sum = 0, st[8];
+    unsigned long long sum = 0, st[ML_STAT_COUNT];
     ML_CK(cudaMemcpyAsync(f->d_map_u32, counts, npix * sizeof(uint32_t),
                           in_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     ML_CK(launch_map_sum(f->d_map_u32, npix, f->d_sum, f->num_sms, s));
@@ -1699,7 +1704,7 @@ ml_status ml_field_clear(ml_field *f, void *stream)
     const size_t npix = (size_t)f->g.mnx * f->g.mny;
     if (f->d_map_u32) ML_CK(cudaMemsetAsync(f->d_map_u32, 0, npix * sizeof(uint32_t), s));
     if (f->d_map_f32) ML_CK(cudaMemsetAsync(f->d_map_f32, 0, npix * sizeof(float), s));
-    ML_CK(cudaMemsetAsync(f->d_stats, 0, 8 * sizeof(unsigned long long), s));
+    ML_CK(cudaMemsetAsync(f->d_stats, 0, ML_STAT_COUNT * sizeof(unsigned long long), s));
     ML_CK(cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s));
     f->rays_asked = 0;
     f->launches = 0;
@@ -1708,11 +1713,11 @@ ml_status ml_field_clear(ml_field *f, void *stream)
     return ML_OK;
 }
 
-ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream)
+ml_status ml_field_stats(ml_field *f, uint64_t out[ML_STAT_COUNT], void *stream)
 {
     if (!f || !out) return fail(ML_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long st[8], sum = 0;
+    unsigned long long st[ML_STAT_COUNT], sum = 0;
     unsigned flags = 0;
     if (f->d_map_u32)
         ML_CK(launch_map_sum(f->d_map_u32, (size_t)f->g.mnx * f->g.mny, f->d_sum, f->num_sms, s));
@@ -1722,7 +1727,7 @@ ml_status ml_field_stats(ml_field *f, uint64_t out[8], void *stream)
     ML_CK(cudaStreamSynchronize(s));
     // a wrapped pixel loses 2^32 from the map's sum
     if (f->d_map_u32 && sum != f->map_base + (st[ML_STAT_RAYS_IN] - f->in_at_set)) flags |= 1u;
-    for (int q = 0; q < 8; ++q) out[q] = st[q];
+    for (int q = 0; q < ML_STAT_COUNT; ++q) out[q] = st[q];
     out[ML_STAT_LAUNCHES] = f->launches;
     out[ML_STAT_FLAGS] = flags;
     out[ML_STAT_RAYS_ASKED] = f->rays_asked;
@@ -1751,6 +1756,21 @@ ml_status ml_field_info(const ml_field *f, ml_field_params *out)
     out->build = f->build_used;
     out->far_bound = f->far_bound;
     out->mu_per_count = (g.l3x * g.l3y) / (g.dpx * g.dpy);
+    return ML_OK;
+}
+
+ml_status ml_fp32_fma_peak(int32_t two_lane, int32_t blocks_per_sm, int64_t iters, float *sink,
+                           double *flop, void *stream)
+{
+    if (!sink || !flop) return fail(ML_ERR_INVALID_ARG, "NULL argument");
+    if (blocks_per_sm < 1 || blocks_per_sm > 8) return fail(ML_ERR_INVALID_ARG, "blocks_per_sm must be in [1, 8]");
+    if (iters < 1 || iters > (int64_t(1) << 32)) return fail(ML_ERR_INVALID_ARG, "iters must be in [1, 2^32]");
+    int dev = 0, sms = 0;
+    ML_CK(cudaGetDevice(&dev));
+    ML_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned blocks = (unsigned)sms * (unsigned)blocks_per_sm;
+    ML_CK(launch_fma_peak(two_lane != 0, blocks, iters, sink, (cudaStream_t)stream));
+    *flop = fma_peak_flop(two_lane != 0, blocks, iters);
     return ML_OK;
 }
 

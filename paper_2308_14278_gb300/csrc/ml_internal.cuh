@@ -77,6 +77,7 @@ struct ShootArgs {
     int64_t rg_first, n_rg, groups_per_band, n_cc, cc_per_l1, l2_per_cc;
     int64_t n_tasks;
     int near_cap;                   // float4 slots of shared memory per warp
+    int walk;                       // ML_WALK_CERTIFIED or ML_WALK_PER_RAY (mixed NGP)
     // float constants of the mixed kernel
     float l3x_f, l3x_lo, c0_f, ipx_f, ipy_f;
     float cxy_f;                    // change of the u slope of beta_x per ray row (fold: d_y l3y l3x / dpx)
@@ -157,6 +158,11 @@ cudaError_t launch_light_curves_dev(const Geo &g, const uint32_t *cu, const floa
                                     const double *d_tracks, int n_tracks, int n_samples, int h,
                                     const float *d_taps, float *out, cudaStream_t s);
 int mixed_p_supported(int p);     // the Taylor order the mixed kernel will use for p
+// FP32 FMA throughput probe: blocks x 256 threads, eight chains of `iters`
+// FMAs each (scalar, or two-lane fma.rn.f32x2); fma_peak_flop is its flop count.
+cudaError_t launch_fma_peak(bool two_lane, unsigned blocks, int64_t iters, float *sink,
+                            cudaStream_t s);
+double fma_peak_flop(bool two_lane, unsigned blocks, int64_t iters);
 
 // ---- shared device arithmetic ---------------------------------------------
 

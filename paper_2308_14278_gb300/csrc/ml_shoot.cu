@@ -172,6 +172,13 @@ __device__ void flush_stats(const ShootArgs &a, unsigned long long in, unsigned 
     }
 }
 
+// Per-lane counts of the certified walk (walk_span): rays whose source
+// position was evaluated one by one, and spans of rays certified to share a
+// pixel without being evaluated.
+struct SpanCount {
+    unsigned long long evals = 0, spans = 0;
+};
+
 // One thread per ray over [ray_begin, ray_end), FP64 (direct or near/far).
 template <bool NEARFAR>
 __global__ void __launch_bounds__(256) k_shoot_fp64(ShootArgs a)
@@ -445,6 +452,312 @@ __device__ __forceinline__ void walk_any(const RowPoly<P> &rp, const ShootArgs &
     }
 }
 
+// Approximate reciprocal square root (rsqrt.approx.ftz.f32); used only in
+// the certification bounds below, which carry a safety factor.
+__device__ __forceinline__ float rsqrt_approx(float y)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+    return r;
+}
+
+constexpr int NN_DYN = 5;   // walk_span: near list of any length, read from shared memory
+
+// Span-walk counts of a warp into the field's counters.
+__device__ void flush_spans(const ShootArgs &a, const SpanCount &sc)
+{
+    unsigned long long ev = sc.evals, sp = sc.spans;
+    for (int o = 16; o > 0; o >>= 1) {
+        ev += __shfl_down_sync(0xffffffffu, ev, o);
+        sp += __shfl_down_sync(0xffffffffu, sp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (ev) atomicAdd(a.stats + ML_STAT_RAYS_EVAL, ev);
+        if (sp) atomicAdd(a.stats + ML_STAT_SPANS, sp);
+    }
+}
+
+// Certified walk of one level-2 column (NGP counts): each lane walks its own
+// ray range [k0, k1) of its row, from an anchor ray whose source position it
+// has evaluated with exactly the per-ray arithmetic of walk_fixed /
+// near_sum_lat / row_eval, and probes a ray kb further on.  When the probe
+// lands in the anchor's pixel and a bound proves that every ray strictly
+// between them lands there too, the whole span joins the current run without
+// being evaluated; otherwise the probe moves closer, down to the next ray,
+// which is then taken as evaluated.  Every ray therefore gets the pixel the
+// per-ray walk gives it, and the counts are bit-identical.
+//
+// The bound.  Along the row the walk's value X(u) (and Y(u)) is the FP32
+// evaluation of F(u) = P(u) + sum_q (lx_q - u) m_q / ((lx_q - u)^2 + dy2_q)
+// (Y: the terms dyy_q m_q / (...)), with P the row polynomial and the FP32
+// lens constants taken as exact reals.  For a ray between the anchor a and
+// the probe b:
+//  - rounding: |X - F| <= E = c eps (S_P + sum_q m_q / rho_q), with
+//    S_P = sum |C_m| U^m (U the lane's largest |u|), eps = 2^-24, rho_q the
+//    lens's smallest distance to the span's rays and c = 2 (P + nn + 8), at
+//    least twice the count of roundings on the path (Horner FMAs, per lens
+//    the offset, r^2, reciprocal, mass product and accumulation);
+//  - shape: F lies within K = (b - a)^2 / 8 max|F''| of the chord between
+//    F(a) and F(b), and |F''| <= sum m(m-1) |C_m| U^(m-2) + sum_q 6 m_q / rho_q^3
+//    (Y: 6 m_q |dyy_q| / rho_q^4);
+//  - so X lies in [min(X_a, X_b) - 2E - K, max(X_a, X_b) + 2E + K] (margin
+//    widened by 1 %, ends rounded outwards); if that interval has one floor,
+//    and the same holds for Y, every ray between shares the anchor's pixel.
+// A span whose rays could come within the close-pass radius of a lens is never
+// certified (those rays would take the hi/lo arithmetic), and anchors outside
+// |X|, |Y| < 2^21 (rays dropped on a lens) are never certified from.
+// The probe distance follows the local slope of (X, Y) to 90 % of the way to
+// the nearest pixel edge; a failed probe moves to 90 % of the linear estimate
+// of the crossing, and halves on repeated failures.
+template <int P, int NN>
+__device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
+                                          int nn_dyn, int k0, int k1, float dyl, float dyl_lo,
+                                          RunState &rs, unsigned &drop, SpanCount &sc)
+{
+    constexpr bool REG = NN < NN_DYN;
+    constexpr int NR = (REG && NN > 0) ? NN : 1;
+    float lx[NR], lm[NR], dy2[NR], dyy[NR];
+    if constexpr (REG) {
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const float4 L = nl.near[q];
+            lx[q] = L.x;
+            lm[q] = L.z;
+            const float dy = __fsub_rn(L.y, dyl);
+            dy2[q] = __fmul_rn(dy, dy);
+            dyy[q] = __fmul_rn(dy, a.yx_f);
+        }
+    }
+    const int nlen = REG ? NN : nn_dyn;
+    // record q of the near list: the registers, or shared memory with the
+    // per-lane terms formed as near_sum_lat forms them
+    auto rec = [&](int q, float &x, float &m, float &d2, float &dd) {
+        if constexpr (REG) {
+            x = lx[q]; m = lm[q]; d2 = dy2[q]; dd = dyy[q];
+        } else {
+            const float4 L = nl.near[q];
+            const float dy = __fsub_rn(L.y, dyl);
+            x = L.x; m = L.z; d2 = __fmul_rn(dy, dy); dd = __fmul_rn(dy, a.yx_f);
+        }
+    };
+    f32x2 C[P + 1];
+#pragma unroll
+    for (int m = 0; m <= P; ++m) C[m] = pack2(rp.X[m], rp.Y[m]);
+    const f32x2 MAGIC = pack2(12582912.0f, 12582912.0f);
+    constexpr float LIM = 2097152.0f;           // 2^21
+
+    // source position of ray k by the per-ray arithmetic; returns true for a
+    // ray on a lens (sent far outside the map, as walk_fixed does).  Called by
+    // all lanes together (the close-pass branch is taken by warp vote).
+    auto eval = [&](int k, bool act, float &X, float &Y) {
+        const float u = __fadd_rn((float)k, a.c0_f);
+        const f32x2 U = pack2(u, u);
+        f32x2 v = C[P];
+#pragma unroll
+        for (int m = P - 1; m >= 0; --m) v = fma2(v, U, C[m]);
+        unpack2(v, X, Y);
+        bool dropped = false;
+        if constexpr (REG && NN == 0) return dropped;
+        float mn = 3.0e38f;
+        auto lens = [&](int q) {
+            float x, m, d2, dd;
+            rec(q, x, m, d2, dd);
+            const float dx = __fsub_rn(x, u);
+            const float r2 = __fmaf_rn(dx, dx, d2);
+            mn = fminf(mn, r2);
+            const float sv = __fmul_rn(m, rcp_approx(r2));
+            X = __fmaf_rn(dx, sv, X);
+            Y = __fmaf_rn(dd, sv, Y);
+        };
+        if constexpr (REG) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) lens(q);
+        } else {
+            for (int q = 0; q < nlen; ++q) lens(q);
+        }
+        const bool close = act && mn < a.rc2u;
+        if (__any_sync(0xffffffffu, close)) {
+            if (close) {
+                unpack2(v, X, Y);
+                if (!near_sum_hilo_lat(nl, nlen, u, dyl, dyl_lo, a.yx_f, X, Y)) {
+                    X = -1.0e30f;
+                    dropped = true;
+                }
+            }
+        }
+        return dropped;
+    };
+    auto raw = [&](float X, float Y, unsigned &rx, unsigned &ry) {
+        float fx, fy;
+        unpack2(add2_rd(pack2(X, Y), MAGIC), fx, fy);
+        rx = (unsigned)__float_as_int(fx);
+        ry = (unsigned)__float_as_int(fy);
+    };
+
+    // bounds of the row polynomial over the lane's range: S = sum |C_m| U^m,
+    // Q = sum_{m>=2} m (m-1) |C_m| U^(m-2), rounded upwards
+    const bool on = k1 > k0;
+    const float ulo = __fadd_rn((float)k0, a.c0_f);
+    const float uhi = __fadd_rn((float)(on ? k1 - 1 : k0), a.c0_f);
+    const float Um = fmaxf(fabsf(ulo), fabsf(uhi));
+    float SX = fabsf(rp.X[P]), SY = fabsf(rp.Y[P]);
+#pragma unroll
+    for (int m = P - 1; m >= 0; --m) {
+        SX = __fmaf_ru(SX, Um, fabsf(rp.X[m]));
+        SY = __fmaf_ru(SY, Um, fabsf(rp.Y[m]));
+    }
+    float QX = 0.f, QY = 0.f;
+    if constexpr (P >= 2) {
+        QX = (float)(P * (P - 1)) * fabsf(rp.X[P]);
+        QY = (float)(P * (P - 1)) * fabsf(rp.Y[P]);
+#pragma unroll
+        for (int m = P - 1; m >= 2; --m) {
+            QX = __fmaf_ru(QX, Um, (float)(m * (m - 1)) * fabsf(rp.X[m]));
+            QY = __fmaf_ru(QY, Um, (float)(m * (m - 1)) * fabsf(rp.Y[m]));
+        }
+    }
+    const float cE = (float)(2 * (P + 8)) * 5.9604645e-8f;     // per-lens part added below
+    const float rcut = __fmaf_ru(1.01f, a.rc2u, 1e-30f);
+
+    auto certify = [&](int ka, int kb, float Xa, float Ya, float Xb, float Yb) {
+        if (!(fabsf(Xa) < LIM && fabsf(Xb) < LIM && fabsf(Ya) < LIM && fabsf(Yb) < LIM)) return false;
+        const float ua = __fadd_rn((float)ka, a.c0_f), ub = __fadd_rn((float)kb, a.c0_f);
+        float tX = 0.f, tY = 0.f, cX = QX, cY = QY;
+        bool clear = true;
+        auto lens = [&](int q) {
+            float x, m, d2, dd;
+            rec(q, x, m, d2, dd);
+            const float dist = fmaxf(0.f, fmaxf(__fsub_rd(ua, x), __fsub_rd(x, ub)));
+            const float rho2 = __fmaf_rd(dist, dist, d2);
+            clear &= rho2 > rcut;
+            const float ir2 = rcp_approx(rho2), ir = rsqrt_approx(rho2);
+            const float mr = m * ir, md = m * fabsf(dd);
+            tX += mr;
+            tY = fmaf(md, ir2, tY);
+            cX = fmaf(6.f * mr, ir2, cX);
+            cY = fmaf(6.f * md, ir2 * ir2, cY);
+        };
+        if constexpr (REG) {
+#pragma unroll
+            for (int q = 0; q < NN; ++q) lens(q);
+        } else {
+            for (int q = 0; q < nlen; ++q) lens(q);
+        }
+        const float c = cE + (float)(2 * nlen) * 5.9604645e-8f;
+        const float w = __fsub_rn(ub, ua);
+        const float kk = 0.125f * w * w;
+        const float MX = 1.01f * fmaf(kk, cX, 2.f * c * (SX + tX));
+        const float MY = 1.01f * fmaf(kk, cY, 2.f * c * (SY + tY));
+        const bool okx = floor_to_int(__fsub_rd(fminf(Xa, Xb), MX)) == floor_to_int(__fadd_ru(fmaxf(Xa, Xb), MX));
+        const bool oky = floor_to_int(__fsub_rd(fminf(Ya, Yb), MY)) == floor_to_int(__fadd_ru(fmaxf(Ya, Yb), MY));
+        return clear && okx && oky;
+    };
+    // rays until the nearest pixel edge at slopes (sX, sY) per ray, 90 %
+    auto ahead = [&](float X, float Y, unsigned rx, unsigned ry, float sX, float sY) {
+        if (!(fabsf(X) < LIM && fabsf(Y) < LIM)) return 1;
+        const float fX = __fsub_rn(X, __fsub_rn(__int_as_float((int)rx), 12582912.0f));
+        const float fY = __fsub_rn(Y, __fsub_rn(__int_as_float((int)ry), 12582912.0f));
+        const float gX = sX > 0.f ? __fsub_rn(1.f, fX) : fX;
+        const float gY = sY > 0.f ? __fsub_rn(1.f, fY) : fY;
+        const float n = fminf(fminf(gX * rcp_approx(fabsf(sX)), gY * rcp_approx(fabsf(sY))), 1048576.f);
+        return max(1, floor_to_int(0.9f * n));
+    };
+
+    const Geo &g = a.g;
+    const unsigned offx = (unsigned)rp.bx - 0x4B400000u, offy = (unsigned)rp.by - 0x4B400000u;
+    unsigned rcx = (unsigned)rs.cx - offx, rcy = (unsigned)rs.cy - offy;   // run pixel, raw form
+    int kst = k0;                                                          // run start in this walk
+    // the lane's first ray
+    float Xa, Ya;
+    const bool d0 = eval(k0, on, Xa, Ya);
+    unsigned rxa, rya;
+    raw(Xa, Ya, rxa, rya);
+    if (on) {
+        ++sc.evals;
+        if (d0) ++drop;
+        if (rxa != rcx || rya != rcy) {
+            flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt, a.map_u32, g.mnx, g.mny);
+            rs.cnt = 0;
+            rcx = rxa;
+            rcy = rya;
+        }
+    }
+    // first probe: the slope of the row polynomial at the first ray
+    int ka = k0, d;
+    {
+        float sX = (float)P * rp.X[P], sY = (float)P * rp.Y[P];
+#pragma unroll
+        for (int m = P - 1; m >= 1; --m) {
+            sX = __fmaf_rn(sX, ulo, (float)m * rp.X[m]);
+            sY = __fmaf_rn(sY, ulo, (float)m * rp.Y[m]);
+        }
+        d = ahead(Xa, Ya, rxa, rya, sX, sY);
+    }
+    bool failed = false;
+    for (;;) {
+        const bool act = on && ka + 1 < k1;
+        if (!__any_sync(0xffffffffu, act)) break;
+        const int kb = act ? min(ka + d, k1 - 1) : ka;
+        float Xb, Yb;
+        const bool db = eval(kb, act, Xb, Yb);
+        unsigned rxb, ryb;
+        raw(Xb, Yb, rxb, ryb);
+        if (act) {
+            ++sc.evals;
+            const bool same = rxb == rxa && ryb == rya;
+            bool take = kb == ka + 1;
+            if (!take && same) {
+                take = certify(ka, kb, Xa, Ya, Xb, Yb);
+                sc.spans += take ? 1ull : 0ull;
+            }
+            const int span = kb - ka;
+            if (take) {
+                if (!same) {
+                    // the probe is the next ray and starts a new run
+                    flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(kb - kst),
+                              a.map_u32, g.mnx, g.mny);
+                    rs.cnt = 0;
+                    kst = kb;
+                    rcx = rxb;
+                    rcy = ryb;
+                }
+                if (db) ++drop;
+                const float inv = rcp_approx((float)span);
+                d = ahead(Xb, Yb, rxb, ryb, __fsub_rn(Xb, Xa) * inv, __fsub_rn(Yb, Ya) * inv);
+                ka = kb;
+                Xa = Xb;
+                Ya = Yb;
+                rxa = rxb;
+                rya = ryb;
+                failed = false;
+            } else {
+                int dn = span >> 1;
+                if (!same && !failed && fabsf(Xa) < LIM && fabsf(Xb) < LIM && fabsf(Ya) < LIM &&
+                    fabsf(Yb) < LIM) {
+                    // linear estimate of the first edge crossing between the two
+                    float t = 1.f;
+                    const float fa = __fsub_rn(__int_as_float((int)rxa), 12582912.0f);
+                    const float ga = __fsub_rn(__int_as_float((int)rya), 12582912.0f);
+                    if (rxb != rxa) {
+                        const float e = Xb > Xa ? __fadd_rn(fa, 1.f) : fa;
+                        t = fminf(t, __fsub_rn(e, Xa) * rcp_approx(__fsub_rn(Xb, Xa)));
+                    }
+                    if (ryb != rya) {
+                        const float e = Yb > Ya ? __fadd_rn(ga, 1.f) : ga;
+                        t = fminf(t, __fsub_rn(e, Ya) * rcp_approx(__fsub_rn(Yb, Ya)));
+                    }
+                    dn = floor_to_int(0.9f * fmaxf(t, 0.f) * (float)span);
+                }
+                d = max(1, min(dn, span - 1));
+                failed = true;
+            }
+        }
+    }
+    if (on) rs.cnt += (unsigned)(k1 - kst);
+    rs.cx = (int)(rcx + offx);
+    rs.cy = (int)(rcy + offy);
+}
+
 // Keeps a value in a register: the compiler may not recompute it (it would
 // otherwise rebuild FP64-derived constants inside the walk, and FP64
 // arithmetic is slow on this GPU).
@@ -461,7 +774,7 @@ template <int P>
 __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4 *near, float2 *nlo,
                                            int lane, float dyl, float dyl_lo, RunState &rs,
                                            unsigned &drop, unsigned long long &pairs,
-                                           unsigned long long &tasks)
+                                           unsigned long long &tasks, SpanCount &sc)
 {
     const Geo &g = a.g;
     TaskShape ts;
@@ -491,6 +804,18 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
         RowPoly<P> rp;
         row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
         pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
+        if (a.walk == ML_WALK_CERTIFIED) {
+            switch (nn) {
+            case 0: walk_span<P, 0>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
+            case 1: walk_span<P, 1>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
+            case 2: walk_span<P, 2>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
+            case 3: walk_span<P, 3>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
+            case 4: walk_span<P, 4>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
+            default: walk_span<P, NN_DYN>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
+            }
+            continue;
+        }
+        sc.evals += (unsigned long long)(k1 - k0);
         const bool on = k1 > k0;
         const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
         if (uniform && nn <= 4) {
@@ -550,17 +875,19 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
     RunState rs{-1, -1, 0u, 0u, 0u};
     unsigned drop = 0;
     unsigned long long pairs = 0, tasks = 0;
+    SpanCount sc;
     float dyl, dyl_lo;
     lane_dy(a.l3yx, lane, dyl, dyl_lo);
     for (;;) {
         bool stop;
         const int64_t t = fetch_task(a, lane, stop);
         if (stop || t >= a.n_tasks) break;
-        shoot_task<P>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks);
+        shoot_task<P>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks, sc);
     }
     run_flush(rs, a.map_u32, a.g.mnx, a.g.mny);
-    // dropped rays were sent to (-1, -1) and counted as out above
+    // dropped rays were sent far outside the map and counted as out above
     flush_stats(a, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
+    flush_spans(a, sc);
 }
 
 // Batched persistent kernel: one launch over the tasks of many maps (all
@@ -577,6 +904,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
     RunState rs{-1, -1, 0u, 0u, 0u};
     unsigned drop = 0;
     unsigned long long pairs = 0, tasks = 0;
+    SpanCount sc;
     float dyl = 0.f, dyl_lo = 0.f;
     int cur = -1;
     const int64_t total = b.task_base[b.n_maps];
@@ -603,22 +931,25 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
             if (cur >= 0) {
                 const ShootArgs &ac = b.args[cur];
                 run_flush(rs, ac.map_u32, ac.g.mnx, ac.g.mny);
-                            flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
+                flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
+                flush_spans(ac, sc);
                 rs = RunState{-1, -1, 0u, 0u, 0u};
                 drop = 0;
                 pairs = 0;
                 tasks = 0;
+                sc = SpanCount{};
             }
             cur = lo;
             lane_dy(b.args[cur].l3yx, lane, dyl, dyl_lo);
         }
         shoot_task<P>(b.args[cur], t - b.task_base[cur], near, nlo, lane, dyl, dyl_lo, rs, drop,
-                      pairs, tasks);
+                      pairs, tasks, sc);
     }
     if (cur >= 0) {
         const ShootArgs &ac = b.args[cur];
         run_flush(rs, ac.map_u32, ac.g.mnx, ac.g.mny);
-            flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
+        flush_stats(ac, rs.in, rs.out - drop, drop, pairs, lane == 0 ? tasks : 0, 0u);
+        flush_spans(ac, sc);
     }
 }
 

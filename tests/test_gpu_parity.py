@@ -312,6 +312,51 @@ def test_shot_stripe_is_the_histogram_of_traced_pixels(ml, case):
     f.close()
 
 
+@pytest.mark.parametrize("case", ["mixed", "paper", "table1"])
+def test_certified_walk_equals_per_ray_walk(ml, case):
+    """The certified walk (rays between two evaluated rays counted without
+    being evaluated when a bound proves they share the pixel) gives the same
+    count map, bit for bit, and the same in/out/dropped totals as the walk
+    that evaluates every ray, on the same grid; and it evaluates only a small
+    fraction of the rays of the paper-scale and Table-1 lattices."""
+    if case == "mixed":
+        w, kw = _mixed_case(), dict(l2_sub=(40, 20))
+    elif case == "paper":
+        w, kw = inputs.paper_map(0), dict(tune=True)
+    else:
+        w, kw = inputs.fold_field(0, n_rays=2e10, map_px=(1024, 5120)), dict(tune=True)
+    fc = _field(ml, w, precision=ml.PREC_MIXED, walk=ml.WALK_CERTIFIED, **kw)
+    info = fc.info
+    grid = dict(l1=(info["n1x"] * info["l3x"], info["n1y"] * info["l3y"]),
+                l2_sub=(info["l2_sub_x"], info["l2_sub_y"]))
+    fp = _field(ml, w, precision=ml.PREC_MIXED, walk=ml.WALK_PER_RAY, **grid)
+    for k in ("n1x", "n1y", "n2x", "n2y", "taylor_p"):
+        assert fp.info[k] == info[k], k
+    n = fc.n_rays
+    nx3 = info["n_rays_x"]
+    ranges = [(0, n)] if case == "mixed" else [
+        ((info["n_rays_y"] // 2) * nx3 + 777, (info["n_rays_y"] // 2 + 64) * nx3 + 12345),
+        (n // 7, n // 7 + 3 * nx3 + 5)]
+    for r0, r1 in ranges:
+        fc.clear()
+        fp.clear()
+        fc.shoot(r0, r1)
+        fp.shoot(r0, r1)
+        a = fc.counts().cpu().numpy()
+        b = fp.counts().cpu().numpy()
+        assert np.array_equal(a, b), int(np.abs(a.astype(np.int64) - b.astype(np.int64)).sum())
+        sa, sb = fc.stats(), fp.stats()
+        for k in ("rays_in", "rays_out", "rays_dropped", "near_pairs"):
+            assert sa[k] == sb[k], k
+        assert sb["rays_evaluated"] == r1 - r0
+        assert 0 < sa["rays_evaluated"] <= r1 - r0
+        if case != "mixed":
+            assert sa["rays_evaluated"] < 0.2 * (r1 - r0), sa["rays_evaluated"] / (r1 - r0)
+            assert sa["spans"] > 0
+    fc.close()
+    fp.close()
+
+
 def test_mixed_map_matches_oracle_and_split_invariance(ml):
     w = _mixed_case(6)
     f = _field(ml, w, precision=ml.PREC_MIXED)
