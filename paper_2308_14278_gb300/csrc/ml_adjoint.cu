@@ -108,7 +108,7 @@ __device__ __forceinline__ bool forward_ray(const ShootArgs &a, int64_t r, float
     const float dyl_lo = (float)(dyl_d - (double)dyl);
     float qf = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
     RowPoly<P> rp;
-    row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), qf, a, rp);
+    row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), qf, row_y(qf, a), a, rp);
     float u = __fadd_rn((float)(i - c2x * g.n2x), a.c0_f);
     float tt = __fmul_rn(u, a.l3x_f);
     float ax, ay, mn;
@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
         const float dyl_lo = (float)(dyl_d - (double)dyl);
         const int64_t c2y = j / g.n2y;
         const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
+        const RowY ry = row_y(q, a);
         const double yrow = yref + dyl_d;
         const float s_h = __fmul_rn(__fmul_rn(q, d.l3y_f), d.hinv);
         // lanes of one node row band: [first, seg_last]; the first one adds
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, (P <= 4 ? ML_ADJ_LOWP_BLOC
             const int64_t i0 = c2x * g.n2x;
             const int kend = (int)(min(i0 + g.n2x, g.n3x) - i0);
             RowPoly<P> rp;
-            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
+            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, ry, a, rp);
             float T[2 * (P + 1)];
 #pragma unroll
             for (int n = 0; n < 2 * (P + 1); ++n) T[n] = 0.f;

@@ -391,12 +391,25 @@ struct TuneCand {
     double nodes, rays, cells;
     double near_per_ray;            // mean near-list length over the level-1 cells
     double l1x, l1y;                // level-1 size; 0 = Eq. 10's
+    double n2x;                     // rays per level-2 cell along a lattice row
+    int walk;                       // ML_WALK_* of the field
 };
+
+// Shooting time per ray of the certified walk, picoseconds: a least-squares
+// fit to 13 grids of the paper-scale field (level-1 cells of 1/2, 1/sqrt 2 and
+// 1 times Eq. 10's, level-2 cells of 88 to 1400 rays along a row, p = 4 to 8;
+// largest error 8 %).  Per-ray work is small and near lenses, the per-column
+// set-up (one per level-2 cell and row) and the order P carry the cost.
+double span_cost_ps(int P, double near_per_ray, double n2x)
+{
+    return 0.145 + 0.238 * near_per_ray + 30.6 / std::max(1.0, n2x) + 0.0159 * P;
+}
 
 double cand_cost(const TuneCand &c, int P)
 {
-    return c.rays * ray_cost_ps(P, c.near_per_ray) * 1e-3 + c.nodes * (P + 1) * kNodeCostNs +
-           c.cells * kCellCostNs;   // ns
+    const double ps = c.walk == ML_WALK_CERTIFIED ? span_cost_ps(P, c.near_per_ray, c.n2x)
+                                                  : ray_cost_ps(P, c.near_per_ray);
+    return c.rays * ps * 1e-3 + c.nodes * (P + 1) * kNodeCostNs + c.cells * kCellCostNs;   // ns
 }
 
 uint64_t mix64(uint64_t h, uint64_t v)
@@ -521,7 +534,7 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
         if (d.macro_mode == ML_MACRO_FOLD) p = std::max(p, 2);
         res.push_back(TuneCand{c.sx, c.sy, mixed_p_supported(p), (double)c.g.N2x * (double)c.g.N2y,
                                (double)c.g.n3x * (double)c.g.n3y, (double)c.g.N1x * (double)c.g.N1y,
-                               near_per_ray, c.l1x, c.l1y});
+                               near_per_ray, c.l1x, c.l1y, (double)c.g.n2x, d.walk});
     }
     for (Cand &c : cands) {
         if (c.cells) cudaFreeAsync(c.cells, s);
@@ -1048,6 +1061,7 @@ cudaError_t batch_enqueue(ml_batch *b, cudaStream_t s)
         ba.task_base = gr.d_base;
         ba.n_maps = (int)gr.maps.size();
         ba.near_cap = gr.near_cap;
+        ba.walk = b->fields.empty() ? ML_WALK_CERTIFIED : b->fields[0]->desc.walk;
         ba.total_tasks = gr.total_tasks;
         ba.work = gr.d_work;
         ba.abort_flag = b->d_abort;
@@ -1080,6 +1094,8 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
         if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
         if (descs[i].precision != ML_PREC_MIXED || descs[i].deposit != ML_DEPOSIT_NGP)
             return fail(ML_ERR_UNSUPPORTED, "batches take ML_PREC_MIXED with ML_DEPOSIT_NGP");
+        if (descs[i].walk != descs[0].walk)
+            return fail(ML_ERR_INVALID_ARG, "every map of a batch takes the same walk");
     }
     // Tuned maps take the grid the cost model ranks first for them, each
     // with its own Taylor order; maps of one order share a persistent launch.

@@ -400,14 +400,16 @@ __global__ void k_node_finalize(Geo g, const double *__restrict__ coef, unsigned
     double by = my + sheet_ky(g) * (zy - g.sheet_cy) + c[1];
     double Sx = (bx - g.mx0) / g.dpx;
     double Sy = (by - g.my0) / g.dpy;
-    double fbx = floor(Sx);
+    double fbx = floor(Sx), fby = floor(Sy);
     fbx = fmin(fmax(fbx, -16777216.0), 16777216.0);
+    fby = fmin(fmax(fby, -16777216.0), 16777216.0);
     // slope of the macro and sheet terms in theta_x at the node, and the
     // per-row shift of beta_x (fold: d_x z_x + d_y z_y and d_y z_x l3y)
     const double ax = g.macro == ML_MACRO_FOLD ? g.dx * zx + g.dy * zy : 1.0 - g.kappa - g.gamma;
     const double bq = g.macro == ML_MACRO_FOLD ? g.dy * zx * g.l3y : 0.0;
     unsigned char *rec = out + node * node_stride(g.p);
-    *reinterpret_cast<double *>(rec) = Sy;
+    *reinterpret_cast<int *>(rec) = (int)fby;
+    *reinterpret_cast<float *>(rec + 4) = (float)(Sy - fby);
     *reinterpret_cast<int *>(rec + 8) = (int)fbx;
     *reinterpret_cast<float *>(rec + 12) = (float)(Sx - fbx);
     *reinterpret_cast<float *>(rec + 16) = (float)((ax + sheet_kx(g)) * g.l3x / g.dpx);

@@ -50,9 +50,9 @@ struct LensTable {
 };
 
 // Per-node record of the mixed-precision path, stride 24 + 8p bytes:
-//   double Sy;  int32 bx;  float fx;  float ax;  float bq;  float2 c[p]
-// (Sy, bx + fx) is the smooth part of beta at the node in map pixel units
-// (macro model, sheet and far-field c_0); ax is d(beta_x)/d(theta_x) of the
+//   int32 by;  float fy;  int32 bx;  float fx;  float ax;  float bq;  float2 c[p]
+// (by + fy, bx + fx) is the smooth part of beta at the node in map pixel units
+// (macro model, sheet and far-field c_0; fx, fy in [0, 1)); ax is d(beta_x)/d(theta_x) of the
 // macro and sheet terms at the node in pixels per ray column (l3x); bq is the
 // change of beta_x per ray row (pixels; the fold's d_y theta_x term, else 0);
 // c[n-1] = c_n l3x^n in FP32, n = 1..p: the far-field Taylor coefficient of
@@ -99,6 +99,7 @@ struct BatchArgs {
     const int64_t *task_base;       // n_maps + 1 entries
     int n_maps;
     int near_cap;                   // largest near_cap of the maps
+    int walk;                       // ML_WALK_* of every map of the batch
     int64_t total_tasks;
     unsigned long long *work;
     const volatile int *abort_flag;
@@ -353,16 +354,33 @@ struct RowPoly {
     int bx, by;
 };
 
+// The smooth y shift of a ray row at node-relative offset q * l3y (q a
+// half-integer): q * rho_y pixels, taken once per row in FP64 and split into
+// an integer and an FP32 fraction, so that the per-node row setup needs no
+// FP64 arithmetic (this GPU's FP64 rate is 1/64 of FP32's).
+struct RowY {
+    int iq;
+    float fq;
+};
+
+__device__ __forceinline__ RowY row_y(float q, const ShootArgs &a)
+{
+    const double y = (double)q * a.rho_y;
+    const double k = floor(y);
+    return RowY{(int)k, (float)(y - k)};
+}
+
 // Build the row polynomial of one node for the ray row at node-relative y
 // offset q * l3y (q a half-integer), in lattice units s = q l3y / l3x: the
 // far series F = sum_{n=1..P} c_n l3x^n (u + i s)^n is re-expanded in u by a
 // Taylor shift (repeated synthetic division), then beta_x = Sx + Ax u -
 // Re F / dpx and beta_y = Sy + Ay q + Im F / dpy.
 template <int P>
-__device__ __forceinline__ void row_setup(const unsigned char *rec, float q, const ShootArgs &a,
+__device__ __forceinline__ void row_setup(const unsigned char *rec, float q, RowY ry, const ShootArgs &a,
                                           RowPoly<P> &rp)
 {
-    const double Sy = *reinterpret_cast<const double *>(rec);
+    const int by0 = *reinterpret_cast<const int *>(rec);
+    const float fy = *reinterpret_cast<const float *>(rec + 4);
     const int bx0 = *reinterpret_cast<const int *>(rec + 8);
     const float fx = *reinterpret_cast<const float *>(rec + 12);
     const float axn = *reinterpret_cast<const float *>(rec + 16);
@@ -403,14 +421,12 @@ __device__ __forceinline__ void row_setup(const unsigned char *rec, float q, con
     float kx = floorf(x0);
     rp.X[0] = __fsub_rn(x0, kx);
     rp.bx = bx0 + (int)kx;
-    // y base in FP64: Sy + q * rho_y, then the FP32 far-field offset
-    double y0 = fma((double)q, a.rho_y, Sy);
-    double ky = floor(y0);
-    ky = fmin(fmax(ky, -16777216.0), 16777216.0);
-    float y0f = __fadd_rn((float)(y0 - ky), rp.Y[0]);
-    float ky2 = floorf(y0f);
-    rp.Y[0] = __fsub_rn(y0f, ky2);
-    rp.by = (int)ky + (int)ky2;
+    // y base: the node's and the row's integer parts, their fractions and
+    // the far-field offset of this row in FP32
+    float y0f = __fadd_rn(__fadd_rn(fy, ry.fq), rp.Y[0]);
+    float ky = floorf(y0f);
+    rp.Y[0] = __fsub_rn(y0f, ky);
+    rp.by = by0 + ry.iq + (int)ky;
 }
 
 template <int P>

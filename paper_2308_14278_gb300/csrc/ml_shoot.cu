@@ -23,6 +23,15 @@
 #ifndef ML_MIN_BLOCKS
 #define ML_MIN_BLOCKS 3
 #endif
+// Rays the certified walk evaluates per step (its window).
+#ifndef ML_SPAN_W
+#define ML_SPAN_W 2
+#endif
+// Lattice units within which a near lens makes the certified walk hand a warp's
+// column to the per-ray walk (runs shorten and spans stay short near a lens).
+#ifndef ML_SPAN_FAR
+#define ML_SPAN_FAR 3000.0f
+#endif
 
 namespace ml {
 
@@ -477,28 +486,30 @@ __device__ void flush_spans(const ShootArgs &a, const SpanCount &sc)
     }
 }
 
-// Certified walk of one level-2 column (NGP counts): each lane walks its own
-// ray range [k0, k1) of its row, from an anchor ray whose source position it
-// has evaluated with exactly the per-ray arithmetic of walk_fixed /
-// near_sum_lat / row_eval, and probes a ray kb further on.  When the probe
-// lands in the anchor's pixel and a bound proves that every ray strictly
-// between them lands there too, the whole span joins the current run without
-// being evaluated; otherwise the probe moves closer, down to the next ray,
-// which is then taken as evaluated.  Every ray therefore gets the pixel the
-// per-ray walk gives it, and the counts are bit-identical.
+// Certified walk of one level-2 column (NGP counts).  Each lane walks its own
+// ray range [k0, k1) of its row in steps.  A step evaluates a window of W
+// consecutive rays kb, kb+1, ... with exactly the per-ray arithmetic of
+// walk_fixed / near_sum_lat / row_eval, after the lane's last evaluated ray
+// ka.  When kb > ka + 1 the rays strictly between them are not evaluated:
+// they join the current run only if ray kb lands in the run's pixel and a
+// bound proves that every ray between lands there too; otherwise the lane
+// evaluates nothing more in this step and retries with half the gap.  Every
+// ray therefore gets the pixel the per-ray walk gives it, and the counts are
+// bit-identical.  The gap is chosen so that the window starts two rays short
+// of where the lane's (X, Y) slope says the next pixel edge lies, so that one
+// step usually crosses it.
 //
 // The bound.  Along the row the walk's value X(u) (and Y(u)) is the FP32
 // evaluation of F(u) = P(u) + sum_q (lx_q - u) m_q / ((lx_q - u)^2 + dy2_q)
 // (Y: the terms dyy_q m_q / (...)), with P the row polynomial and the FP32
-// lens constants taken as exact reals.  For a ray between the anchor a and
-// the probe b:
+// lens constants taken as exact reals.  For a ray between a and b:
 //  - rounding: |X - F| <= E = c eps (S_P + sum_q m_q / rho_q), with
 //    S_P = sum |C_m| U^m (U the lane's largest |u|), eps = 2^-24, rho_q the
 //    lens's smallest distance to the span's rays and c = 2 (P + nn + 8), at
 //    least twice the count of roundings on the path (Horner FMAs, per lens
 //    the offset, r^2, reciprocal, mass product and accumulation);
 //  - shape: F lies within K = (b - a)^2 / 8 max|F''| of the chord between
-//    F(a) and F(b), and |F''| <= sum m(m-1) |C_m| U^(m-2) + sum_q 6 m_q / rho_q^3
+//    F(a) and F(b), with |F''| <= sum m(m-1) |C_m| U^(m-2) + sum_q 6 m_q / rho_q^3
 //    (Y: 6 m_q |dyy_q| / rho_q^4);
 //  - so X lies in [min(X_a, X_b) - 2E - K, max(X_a, X_b) + 2E + K] (margin
 //    widened by 1 %, ends rounded outwards); if that interval has one floor,
@@ -506,14 +517,12 @@ __device__ void flush_spans(const ShootArgs &a, const SpanCount &sc)
 // A span whose rays could come within the close-pass radius of a lens is never
 // certified (those rays would take the hi/lo arithmetic), and anchors outside
 // |X|, |Y| < 2^21 (rays dropped on a lens) are never certified from.
-// The probe distance follows the local slope of (X, Y) to 90 % of the way to
-// the nearest pixel edge; a failed probe moves to 90 % of the linear estimate
-// of the crossing, and halves on repeated failures.
 template <int P, int NN>
 __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs &a, const SmemNear &nl,
                                           int nn_dyn, int k0, int k1, float dyl, float dyl_lo,
                                           RunState &rs, unsigned &drop, SpanCount &sc)
 {
+    constexpr int W = ML_SPAN_W;                // rays evaluated per step
     constexpr bool REG = NN < NN_DYN;
     constexpr int NR = (REG && NN > 0) ? NN : 1;
     float lx[NR], lm[NR], dy2[NR], dyy[NR];
@@ -546,10 +555,11 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
     const f32x2 MAGIC = pack2(12582912.0f, 12582912.0f);
     constexpr float LIM = 2097152.0f;           // 2^21
 
-    // source position of ray k by the per-ray arithmetic; returns true for a
-    // ray on a lens (sent far outside the map, as walk_fixed does).  Called by
-    // all lanes together (the close-pass branch is taken by warp vote).
-    auto eval = [&](int k, bool act, float &X, float &Y) {
+    // source position of ray k by the per-ray arithmetic, in raw floor form;
+    // returns true for a ray on a lens (sent far outside the map, as
+    // walk_fixed does).  Called by all lanes together (the close-pass branch
+    // is taken by warp vote).
+    auto eval = [&](int k, bool act, float &X, float &Y, unsigned &rx, unsigned &ry) {
         const float u = __fadd_rn((float)k, a.c0_f);
         const f32x2 U = pack2(u, u);
         f32x2 v = C[P];
@@ -557,41 +567,40 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
         for (int m = P - 1; m >= 0; --m) v = fma2(v, U, C[m]);
         unpack2(v, X, Y);
         bool dropped = false;
-        if constexpr (REG && NN == 0) return dropped;
-        float mn = 3.0e38f;
-        auto lens = [&](int q) {
-            float x, m, d2, dd;
-            rec(q, x, m, d2, dd);
-            const float dx = __fsub_rn(x, u);
-            const float r2 = __fmaf_rn(dx, dx, d2);
-            mn = fminf(mn, r2);
-            const float sv = __fmul_rn(m, rcp_approx(r2));
-            X = __fmaf_rn(dx, sv, X);
-            Y = __fmaf_rn(dd, sv, Y);
-        };
-        if constexpr (REG) {
+        if constexpr (!(REG && NN == 0)) {
+            float mn = 3.0e38f;
+            auto lens = [&](int q) {
+                float x, m, d2, dd;
+                rec(q, x, m, d2, dd);
+                const float dx = __fsub_rn(x, u);
+                const float r2 = __fmaf_rn(dx, dx, d2);
+                mn = fminf(mn, r2);
+                const float sv = __fmul_rn(m, rcp_approx(r2));
+                X = __fmaf_rn(dx, sv, X);
+                Y = __fmaf_rn(dd, sv, Y);
+            };
+            if constexpr (REG) {
 #pragma unroll
-            for (int q = 0; q < NR; ++q) lens(q);
-        } else {
-            for (int q = 0; q < nlen; ++q) lens(q);
-        }
-        const bool close = act && mn < a.rc2u;
-        if (__any_sync(0xffffffffu, close)) {
-            if (close) {
-                unpack2(v, X, Y);
-                if (!near_sum_hilo_lat(nl, nlen, u, dyl, dyl_lo, a.yx_f, X, Y)) {
-                    X = -1.0e30f;
-                    dropped = true;
+                for (int q = 0; q < NR; ++q) lens(q);
+            } else {
+                for (int q = 0; q < nlen; ++q) lens(q);
+            }
+            const bool close = act && mn < a.rc2u;
+            if (__any_sync(0xffffffffu, close)) {
+                if (close) {
+                    unpack2(v, X, Y);
+                    if (!near_sum_hilo_lat(nl, nlen, u, dyl, dyl_lo, a.yx_f, X, Y)) {
+                        X = -1.0e30f;
+                        dropped = true;
+                    }
                 }
             }
         }
-        return dropped;
-    };
-    auto raw = [&](float X, float Y, unsigned &rx, unsigned &ry) {
         float fx, fy;
         unpack2(add2_rd(pack2(X, Y), MAGIC), fx, fy);
         rx = (unsigned)__float_as_int(fx);
         ry = (unsigned)__float_as_int(fy);
+        return dropped;
     };
 
     // bounds of the row polynomial over the lane's range: S = sum |C_m| U^m,
@@ -616,140 +625,114 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
             QY = __fmaf_ru(QY, Um, (float)(m * (m - 1)) * fabsf(rp.Y[m]));
         }
     }
-    const float cE = (float)(2 * (P + 8)) * 5.9604645e-8f;     // per-lens part added below
     const float rcut = __fmaf_ru(1.01f, a.rc2u, 1e-30f);
+    // 2 c eps: twice the rounding bound's factor (see above)
+    const float c2e = (float)(4 * (P + 8 + nlen)) * 5.9604645e-8f;
 
     auto certify = [&](int ka, int kb, float Xa, float Ya, float Xb, float Yb) {
         if (!(fabsf(Xa) < LIM && fabsf(Xb) < LIM && fabsf(Ya) < LIM && fabsf(Yb) < LIM)) return false;
         const float ua = __fadd_rn((float)ka, a.c0_f), ub = __fadd_rn((float)kb, a.c0_f);
         float tX = 0.f, tY = 0.f, cX = QX, cY = QY;
         bool clear = true;
-        auto lens = [&](int q) {
-            float x, m, d2, dd;
-            rec(q, x, m, d2, dd);
-            const float dist = fmaxf(0.f, fmaxf(__fsub_rd(ua, x), __fsub_rd(x, ub)));
-            const float rho2 = __fmaf_rd(dist, dist, d2);
-            clear &= rho2 > rcut;
-            const float ir2 = rcp_approx(rho2), ir = rsqrt_approx(rho2);
-            const float mr = m * ir, md = m * fabsf(dd);
-            tX += mr;
-            tY = fmaf(md, ir2, tY);
-            cX = fmaf(6.f * mr, ir2, cX);
-            cY = fmaf(6.f * md, ir2 * ir2, cY);
-        };
-        if constexpr (REG) {
+        if constexpr (!(REG && NN == 0)) {
+            auto lens = [&](int q) {
+                float x, m, d2, dd;
+                rec(q, x, m, d2, dd);
+                const float dist = fmaxf(0.f, fmaxf(__fsub_rd(ua, x), __fsub_rd(x, ub)));
+                const float rho2 = __fmaf_rd(dist, dist, d2);
+                clear &= rho2 > rcut;
+                const float ir2 = rcp_approx(rho2), ir = rsqrt_approx(rho2);
+                const float mr = m * ir, md = m * fabsf(dd);
+                tX += mr;
+                tY = fmaf(md, ir2, tY);
+                cX = fmaf(6.f * mr, ir2, cX);
+                cY = fmaf(6.f * md, ir2 * ir2, cY);
+            };
+            if constexpr (REG) {
 #pragma unroll
-            for (int q = 0; q < NN; ++q) lens(q);
-        } else {
-            for (int q = 0; q < nlen; ++q) lens(q);
+                for (int q = 0; q < NR; ++q) lens(q);
+            } else {
+                for (int q = 0; q < nlen; ++q) lens(q);
+            }
         }
-        const float c = cE + (float)(2 * nlen) * 5.9604645e-8f;
         const float w = __fsub_rn(ub, ua);
         const float kk = 0.125f * w * w;
-        const float MX = 1.01f * fmaf(kk, cX, 2.f * c * (SX + tX));
-        const float MY = 1.01f * fmaf(kk, cY, 2.f * c * (SY + tY));
+        const float MX = 1.01f * fmaf(kk, cX, c2e * (SX + tX));
+        const float MY = 1.01f * fmaf(kk, cY, c2e * (SY + tY));
         const bool okx = floor_to_int(__fsub_rd(fminf(Xa, Xb), MX)) == floor_to_int(__fadd_ru(fmaxf(Xa, Xb), MX));
         const bool oky = floor_to_int(__fsub_rd(fminf(Ya, Yb), MY)) == floor_to_int(__fadd_ru(fmaxf(Ya, Yb), MY));
         return clear && okx && oky;
-    };
-    // rays until the nearest pixel edge at slopes (sX, sY) per ray, 90 %
-    auto ahead = [&](float X, float Y, unsigned rx, unsigned ry, float sX, float sY) {
-        if (!(fabsf(X) < LIM && fabsf(Y) < LIM)) return 1;
-        const float fX = __fsub_rn(X, __fsub_rn(__int_as_float((int)rx), 12582912.0f));
-        const float fY = __fsub_rn(Y, __fsub_rn(__int_as_float((int)ry), 12582912.0f));
-        const float gX = sX > 0.f ? __fsub_rn(1.f, fX) : fX;
-        const float gY = sY > 0.f ? __fsub_rn(1.f, fY) : fY;
-        const float n = fminf(fminf(gX * rcp_approx(fabsf(sX)), gY * rcp_approx(fabsf(sY))), 1048576.f);
-        return max(1, floor_to_int(0.9f * n));
     };
 
     const Geo &g = a.g;
     const unsigned offx = (unsigned)rp.bx - 0x4B400000u, offy = (unsigned)rp.by - 0x4B400000u;
     unsigned rcx = (unsigned)rs.cx - offx, rcy = (unsigned)rs.cy - offy;   // run pixel, raw form
-    int kst = k0;                                                          // run start in this walk
-    // the lane's first ray
-    float Xa, Ya;
-    const bool d0 = eval(k0, on, Xa, Ya);
-    unsigned rxa, rya;
-    raw(Xa, Ya, rxa, rya);
-    if (on) {
-        ++sc.evals;
-        if (d0) ++drop;
-        if (rxa != rcx || rya != rcy) {
-            flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt, a.map_u32, g.mnx, g.mny);
-            rs.cnt = 0;
-            rcx = rxa;
-            rcy = rya;
-        }
-    }
-    // first probe: the slope of the row polynomial at the first ray
-    int ka = k0, d;
-    {
-        float sX = (float)P * rp.X[P], sY = (float)P * rp.Y[P];
-#pragma unroll
-        for (int m = P - 1; m >= 1; --m) {
-            sX = __fmaf_rn(sX, ulo, (float)m * rp.X[m]);
-            sY = __fmaf_rn(sY, ulo, (float)m * rp.Y[m]);
-        }
-        d = ahead(Xa, Ya, rxa, rya, sX, sY);
-    }
-    bool failed = false;
+    int kst = k0;                 // first ray of the current run in this walk
+    int ka = k0 - 1;              // last evaluated ray (none yet)
+    float Xa = 0.f, Ya = 0.f;
+    int gap = 1;                  // next window at ka + gap
     for (;;) {
         const bool act = on && ka + 1 < k1;
         if (!__any_sync(0xffffffffu, act)) break;
-        const int kb = act ? min(ka + d, k1 - 1) : ka;
-        float Xb, Yb;
-        const bool db = eval(kb, act, Xb, Yb);
-        unsigned rxb, ryb;
-        raw(Xb, Yb, rxb, ryb);
-        if (act) {
-            ++sc.evals;
-            const bool same = rxb == rxa && ryb == rya;
-            bool take = kb == ka + 1;
-            if (!take && same) {
-                take = certify(ka, kb, Xa, Ya, Xb, Yb);
-                sc.spans += take ? 1ull : 0ull;
+        const int kb = act ? min(ka + gap, k1 - 1) : ka + 1;
+        const bool span = act && kb > ka + 1;
+        // slope baseline: the last evaluated ray, or at the column's start
+        // the window's first ray
+        int kp = ka;
+        float Xp = Xa, Yp = Ya;
+        bool ok = act;
+        // the window: ray kb (which must first certify the span before it),
+        // then the next W - 1 rays; one copy of the evaluation
+#pragma unroll 1
+        for (int w = 0; w < W; ++w) {
+            float X, Y;
+            unsigned rx, ry;
+            const bool dr = eval(kb + w, w == 0 ? act : ok, X, Y, rx, ry);
+            if (w == 0) {
+                if (span) {
+                    ok = rx == rcx && ry == rcy && certify(ka, kb, Xa, Ya, X, Y);
+                    sc.spans += ok ? 1ull : 0ull;
+                    if (!ok) {
+                        ++sc.evals;
+                        gap = max(1, (kb - ka) >> 1);
+                    }
+                }
+                if (ka < k0) {
+                    kp = kb;
+                    Xp = X;
+                    Yp = Y;
+                }
+                if (!__any_sync(0xffffffffu, ok)) break;
             }
-            const int span = kb - ka;
-            if (take) {
-                if (!same) {
-                    // the probe is the next ray and starts a new run
-                    flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(kb - kst),
+            if (ok && kb + w < k1) {
+                ++sc.evals;
+                if (dr) ++drop;
+                if (rx != rcx || ry != rcy) {
+                    flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(kb + w - kst),
                               a.map_u32, g.mnx, g.mny);
                     rs.cnt = 0;
-                    kst = kb;
-                    rcx = rxb;
-                    rcy = ryb;
+                    kst = kb + w;
+                    rcx = rx;
+                    rcy = ry;
                 }
-                if (db) ++drop;
-                const float inv = rcp_approx((float)span);
-                d = ahead(Xb, Yb, rxb, ryb, __fsub_rn(Xb, Xa) * inv, __fsub_rn(Yb, Ya) * inv);
-                ka = kb;
-                Xa = Xb;
-                Ya = Yb;
-                rxa = rxb;
-                rya = ryb;
-                failed = false;
-            } else {
-                int dn = span >> 1;
-                if (!same && !failed && fabsf(Xa) < LIM && fabsf(Xb) < LIM && fabsf(Ya) < LIM &&
-                    fabsf(Yb) < LIM) {
-                    // linear estimate of the first edge crossing between the two
-                    float t = 1.f;
-                    const float fa = __fsub_rn(__int_as_float((int)rxa), 12582912.0f);
-                    const float ga = __fsub_rn(__int_as_float((int)rya), 12582912.0f);
-                    if (rxb != rxa) {
-                        const float e = Xb > Xa ? __fadd_rn(fa, 1.f) : fa;
-                        t = fminf(t, __fsub_rn(e, Xa) * rcp_approx(__fsub_rn(Xb, Xa)));
-                    }
-                    if (ryb != rya) {
-                        const float e = Yb > Ya ? __fadd_rn(ga, 1.f) : ga;
-                        t = fminf(t, __fsub_rn(e, Ya) * rcp_approx(__fsub_rn(Yb, Ya)));
-                    }
-                    dn = floor_to_int(0.9f * fmaxf(t, 0.f) * (float)span);
-                }
-                d = max(1, min(dn, span - 1));
-                failed = true;
+                ka = kb + w;
+                Xa = X;
+                Ya = Y;
+            }
+        }
+        if (ok) {
+            // rays to the next pixel edge along the slope since the baseline;
+            // the next window starts two rays before it
+            gap = 1;
+            if (ka > kp && fabsf(Xa) < LIM && fabsf(Ya) < LIM && fabsf(Xp) < LIM && fabsf(Yp) < LIM) {
+                const float inv = rcp_approx((float)(ka - kp));
+                const float sX = __fsub_rn(Xa, Xp) * inv, sY = __fsub_rn(Ya, Yp) * inv;
+                const float fX = __fsub_rn(Xa, __fsub_rn(__int_as_float((int)rcx), 12582912.0f));
+                const float fY = __fsub_rn(Ya, __fsub_rn(__int_as_float((int)rcy), 12582912.0f));
+                const float gX = sX > 0.f ? __fsub_rn(1.f, fX) : fX;
+                const float gY = sY > 0.f ? __fsub_rn(1.f, fY) : fY;
+                const float n = fminf(fminf(gX * rcp_approx(fabsf(sX)), gY * rcp_approx(fabsf(sY))), 1048576.f);
+                gap = max(1, floor_to_int(n) - 1);
             }
         }
     }
@@ -770,7 +753,7 @@ __device__ __forceinline__ float pin(float v)
 // One warp task of the mixed kernel (NGP deposit): stage the near list, then
 // walk each level-2 column of the task.  Shared by the single-map and the
 // batched persistent kernels.
-template <int P>
+template <int P, bool SPAN>
 __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4 *near, float2 *nlo,
                                            int lane, float dyl, float dyl_lo, RunState &rs,
                                            unsigned &drop, unsigned long long &pairs,
@@ -790,6 +773,7 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
     const bool active = j < ts.rows_end && j >= jb && j <= je;
     const int64_t c2y = j / g.n2y;
     const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
+    const RowY ry = row_y(q, a);
     for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
         stage_near_x<true>(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
         const int64_t i0 = c2x * g.n2x;
@@ -802,19 +786,35 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
         const int kend = __reduce_max_sync(0xffffffffu, k1);
         if (kbeg >= kend) continue;
         RowPoly<P> rp;
-        row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
+        row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, ry, a, rp);
         pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
-        if (a.walk == ML_WALK_CERTIFIED) {
-            switch (nn) {
-            case 0: walk_span<P, 0>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
-            case 1: walk_span<P, 1>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
-            case 2: walk_span<P, 2>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
-            case 3: walk_span<P, 3>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
-            case 4: walk_span<P, 4>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
-            default: walk_span<P, NN_DYN>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc); break;
+        if constexpr (SPAN) {
+            // the certified walk where runs are long: no near lens, or every
+            // near lens farther than ML_SPAN_FAR lattice units from every ray
+            // of the warp's walk; elsewhere the per-ray walk
+            bool far = true;
+            if (nn > 0) {
+                bool close = false;
+                if (k1 > k0) {
+                    const float ulo = __fadd_rn((float)k0, a.c0_f), uhi = __fadd_rn((float)(k1 - 1), a.c0_f);
+                    for (int q = 0; q < nn; ++q) {
+                        const float4 L = near[q];
+                        const float dy = __fsub_rn(L.y, dyl);
+                        const float dx = fmaxf(0.f, fmaxf(ulo - L.x, L.x - uhi));
+                        close |= __fmaf_rn(dx, dx, dy * dy) < ML_SPAN_FAR * ML_SPAN_FAR;
+                    }
+                }
+                far = !__any_sync(0xffffffffu, close);
             }
-            continue;
+            if (far) {
+                if (nn == 0)
+                    walk_span<P, 0>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc);
+                else
+                    walk_span<P, NN_DYN>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc);
+                continue;
+            }
         }
+        {
         sc.evals += (unsigned long long)(k1 - k0);
         const bool on = k1 > k0;
         const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
@@ -853,6 +853,7 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
         } else {
             walk_any<P>(rp, a, nl, nn, kbeg, kend, k0, k1, dyl, dyl_lo, rs, drop);
         }
+        }
     }
 }
 
@@ -865,7 +866,7 @@ __device__ __forceinline__ void lane_dy(double l3yx, int lane, float &dyl, float
     dyl_lo = pin((float)(d - (double)(float)d));
 }
 
-template <int P>
+template <int P, bool SPAN>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mixed(ShootArgs a)
 {
     extern __shared__ float4 smem[];
@@ -882,7 +883,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
         bool stop;
         const int64_t t = fetch_task(a, lane, stop);
         if (stop || t >= a.n_tasks) break;
-        shoot_task<P>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks, sc);
+        shoot_task<P, SPAN>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks, sc);
     }
     run_flush(rs, a.map_u32, a.g.mnx, a.g.mny);
     // dropped rays were sent far outside the map and counted as out above
@@ -894,7 +895,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
 // built with the same Taylor order P).  Global task t belongs to the map m
 // with task_base[m] <= t < task_base[m+1]; a warp flushes its runs and
 // counters into a map's buffers when it moves on to another map.
-template <int P>
+template <int P, bool SPAN>
 __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_batch(BatchArgs b)
 {
     extern __shared__ float4 smem[];
@@ -942,8 +943,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
             cur = lo;
             lane_dy(b.args[cur].l3yx, lane, dyl, dyl_lo);
         }
-        shoot_task<P>(b.args[cur], t - b.task_base[cur], near, nlo, lane, dyl, dyl_lo, rs, drop,
-                      pairs, tasks, sc);
+        shoot_task<P, SPAN>(b.args[cur], t - b.task_base[cur], near, nlo, lane, dyl, dyl_lo, rs, drop,
+                            pairs, tasks, sc);
     }
     if (cur >= 0) {
         const ShootArgs &ac = b.args[cur];
@@ -1123,6 +1124,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
         const bool active = j < ts.rows_end && j >= jb && j <= je;
         const int64_t c2y = j / g.n2y;
         const float q = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
+        const RowY ry = row_y(q, a);
         for (int64_t c2x = ts.c2a; c2x < ts.c2b; ++c2x) {
             stage_near_x<false>(a, nn, g.rx0 + ((double)c2x + 0.5) * g.l2x, near, nlo, lane);
             const int64_t i0 = c2x * g.n2x;
@@ -1134,7 +1136,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
             const int kend = __reduce_max_sync(0xffffffffu, k1);
             if (kbeg >= kend) continue;
             RowPoly<P> rp;
-            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, a, rp);
+            row_setup<P>(a.nodes + (min(c2y, g.N2y - 1) * g.N2x + c2x) * node_stride(P), q, ry, a, rp);
             pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
             const bool on = k1 > k0;
             const bool uniform = !__any_sync(0xffffffffu, on && (k0 != kbeg || k1 != kend));
@@ -1202,7 +1204,7 @@ __global__ void k_trace_mixed(ShootArgs a, const int64_t *__restrict__ idx, int6
     const float dyl_lo = (float)(dyl_d - (double)dyl);
     float qf = (float)((double)(j - c2y * g.n2y) + 0.5 - 0.5 * (double)g.n2y);
     RowPoly<P> rp;
-    row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), qf, a, rp);
+    row_setup<P>(a.nodes + (c2y * g.N2x + c2x) * node_stride(P), qf, row_y(qf, a), a, rp);
     float u = __fadd_rn((float)(i - c2x * g.n2x), a.c0_f);
     float X, Y, mn;
     row_eval<P>(rp, u, X, Y);
@@ -1270,7 +1272,8 @@ template <int P>
 static cudaError_t launch_mixed_p(const ShootArgs &a, int num_sms, cudaStream_t s)
 {
     size_t smem = (size_t)a.near_cap * WARPS_PER_CTA * (sizeof(float4) + sizeof(float2));
-    auto kern = a.g.deposit == ML_DEPOSIT_NGP ? k_shoot_mixed<P> : k_shoot_mixed_cic<P>;
+    auto kern = a.g.deposit != ML_DEPOSIT_NGP ? k_shoot_mixed_cic<P>
+                : a.walk == ML_WALK_CERTIFIED ? k_shoot_mixed<P, true> : k_shoot_mixed<P, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -1322,7 +1325,7 @@ template <int P>
 static cudaError_t launch_batch_p(const BatchArgs &b, int num_sms, cudaStream_t s)
 {
     size_t smem = (size_t)b.near_cap * WARPS_PER_CTA * (sizeof(float4) + sizeof(float2));
-    auto kern = k_shoot_batch<P>;
+    auto kern = b.walk == ML_WALK_CERTIFIED ? k_shoot_batch<P, true> : k_shoot_batch<P, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -226,8 +226,16 @@ def test_cic_adjoint_on_a_stripe_of_the_differentiable_field_matches_oracle(ml):
     st = f.stats()
     assert st["rays_dropped"] == 0 and st["rays_in"] > 0.5 * f.n_rays
     assert 0.02 < st["near_pairs"] / f.n_rays < 0.5
-    G = torch.randn(w.map_n[::-1], generator=torch.Generator().manual_seed(5))
-    gl_ref, gp_ref = oracle.cic_grad_dM(g, w.lenses.x, w.lenses.y, w.lenses.m, G.double().numpy())
+    # a smooth dL/dM: a ray's dL/dbeta then changes little when its FP32
+    # source position and the oracle's FP64 one fall on either side of a pixel
+    # centre (with an uncorrelated dL/dM one such ray moves a column's sum by
+    # about 1/sqrt(rays) of its size)
+    ny, nx = w.map_n[1], w.map_n[0]
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    Gn = (np.cos(2 * np.pi * xx / 97.0) + np.sin(2 * np.pi * yy / 61.0) +
+          0.5 * np.exp(-((xx - 0.4 * nx) ** 2 + (yy - 0.5 * ny) ** 2) / 2000.0)).astype(np.float32)
+    G = torch.from_numpy(Gn)
+    gl_ref, gp_ref = oracle.cic_grad_dM(g, w.lenses.x, w.lenses.y, w.lenses.m, Gn.astype(np.float64))
     Gd = G.cuda().contiguous()
     for method in (ml.ADJOINT_NEARFAR, ml.ADJOINT_DIRECT):
         gl = torch.empty((w.lenses.n, 3), dtype=torch.float64, device="cuda")
