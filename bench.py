@@ -34,14 +34,16 @@ sys.path.insert(0, ROOT)
 METRIC = "rays/s at 13k lenses on 1 GB300; % FP32 peak; map L1 err vs FP64 oracle"
 UNIT = "rays/s"
 N_TRACKS, TRACK_SAMPLES, SIGMA_PX = 10, 4096, 0.5
-# FP32 FMA units of GB300 (152 SMs x 128 lanes) at the maximum SM clock
+# FP32 FMA units of GB300 (152 SMs x 128 lanes) at the maximum SM clock: the
+# derived peak, reported beside the measured one (ml_fp32_fma_peak)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# DRAM bytes per ray of the shooting kernel, from the ncu capture summarised in
-# profiles/k_shoot_mixed_paper-map-2e10-ray-slice.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 484.2 MB for 2.0e10 rays, the tuned grid: level-1
-# cells 7.77 x 1.22 theta_E, level-2 (80, 20), p = 4), valid for the kernel
-# sources whose code (comments and blank space left out, code_hash) has these
-# sha1 prefixes only.
+# copy bandwidth of the GB300s (GB/s), the HBM roofline's denominator
+HBM_GBS_FALLBACK = 6790.0
+# DRAM bytes per ray of the counting kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch over a 2e10-ray
+# slice of the paper-scale lattice at the autotuned grid), valid for the
+# kernel sources whose code (comments and blank space left out, code_hash)
+# has these sha1 prefixes only.
 TRAFFIC_BYTES_PER_RAY = 484.152832e6 / 2.0e10
 TRAFFIC_SOURCES = {"ml_shoot.cu": "e6acd6aa", "ml_internal.cuh": "8235950f", "ml_task.cuh": "3d1d5136"}
 
@@ -109,11 +111,16 @@ def parse():
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the nvidia-smi clock samples of the timed region "
                          "(default: a temporary directory); the JSON line carries their summary")
-    ap.add_argument("--shard", action="store_true",
-                    help="N > 1: shoot ONE paper-scale map across the ranks (contiguous level-1 "
-                         "bands per rank, integer map sum over NCCL; strong scaling) instead of "
-                         "one independent map per rank (weak scaling); with --workload batched, "
-                         "split one set of 80 maps over the ranks (whole maps balanced by rays)")
+    ap.add_argument("--independent", action="store_true",
+                    help="N > 1: one independent map per rank (weak scaling) instead of ONE "
+                         "paper-scale map shot across the ranks (contiguous level-1 bands per "
+                         "rank, integer map sum onto rank 0 over NCCL; strong scaling, the "
+                         "default); with --workload batched, each rank runs its own 80 maps "
+                         "instead of splitting one set (whole maps balanced by rays)")
+    ap.add_argument("--no-independent", action="store_true",
+                    help="N > 1: skip the weak-scaling companion record of a sharded run")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the batched and differentiable sub-records of the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="the paper's level-2 grid (L2 = L1/20) instead of the autotuned one")
     ap.add_argument("--grid", default="",
@@ -246,6 +253,16 @@ def measure_fp32_peak(ml, torch, stream, local, clocks_dir=None, launches=5):
 # our implementation
 # ---------------------------------------------------------------------------
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs (generated file),
+    else the recorded fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return HBM_GBS_FALLBACK, "fallback"
+
+
 def run_ours(args, rank, world, local):
     import torch
     torch.cuda.set_device(local)
@@ -257,9 +274,10 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    # weak scaling: every rank makes its own map (own seed) of the same size;
-    # --shard: all ranks share one map and each shoots its part of the lattice
-    sharded = bool(args.shard and world > 1)
+    # N > 1: one map shared by the ranks, each shooting its part of the lattice
+    # and the integer maps summed onto rank 0 (strong scaling, the design's
+    # exchange step); --independent: one map of its own per rank (weak)
+    sharded = world > 1 and not args.independent
     seed = 0 if sharded else rank
     if args.workload == "fold":
         w = inputs.fold_field(seed=seed, n_rays=args.rays, n_tracks=N_TRACKS)
@@ -277,6 +295,9 @@ def run_ours(args, rank, world, local):
     peak_mask = (torch.empty(w.map_n[0] * w.map_n[1] + 4, dtype=torch.uint8, device=dev)
                  if args.workload == "fold" else None)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    # the map is consumed (mu, light curves, peaks) where it is whole: on every
+    # rank of independent maps, on rank 0 of a sharded one
+    consumer = (not sharded) or rank == 0
 
     def make_desc(device_lenses: bool, host_lenses=None):
         d = ml.make_desc(w, precision=ml.PREC_MIXED, lens_arrays=host_lenses, **grid_kw)
@@ -301,22 +322,25 @@ def run_ours(args, rank, world, local):
             a, b = shard.ray_ranges(info["n_rays_x"], info["n_rays_y"], info["n1y"], world)[rank]
             ml.ml_shoot_rays(h, a, b, stream)
             ml.ml_magnification_map(h, ml.MAP_COUNTS_U32, counts_buf, stream)
-            shard.reduce_counts(counts_buf)          # NCCL integer sum on the current stream
-            ml.ml_field_set_counts(h, counts_buf, stream)
+            shard.reduce_counts(counts_buf, dst=0)   # NCCL integer sum onto rank 0
+            if consumer:
+                ml.ml_field_set_counts(h, counts_buf, stream)
         else:
             ml.ml_shoot_rays(h, r0, r0 + n_shoot, stream)
         if e: e[2].record(stream)
-        ml.ml_magnification_map(h, ml.MAP_MU_F32, mu_out, stream)
+        if consumer:
+            ml.ml_magnification_map(h, ml.MAP_MU_F32, mu_out, stream)
+            ml.ml_light_curves(h, tracks, TRACK_SAMPLES, SIGMA_PX, lc_out, stream)
+            if args.workload == "fold":
+                # the paper's light-curve statistics start from the 5 sigma peaks (§4.2)
+                info_holder["peaks"] = ml.ml_find_peaks(h, ml.ALONG_X, 5.0, peak_mask, 0, stream)[0]
+                # and bin them by distance beta_x from the caustic (Figs. 4-5)
+                info_holder["peak_stats"] = ml.ml_peak_statistics(h, FOLD_DISTANCE_EDGES, ml.ALONG_X, 0.0,
+                                                                  mask=peak_mask, stream=stream)
         if e: e[3].record(stream)
-        ml.ml_light_curves(h, tracks, TRACK_SAMPLES, SIGMA_PX, lc_out, stream)
-        if args.workload == "fold":
-            # the paper's light-curve statistics start from the 5 sigma peaks (§4.2)
-            info_holder["peaks"] = ml.ml_find_peaks(h, ml.ALONG_X, 5.0, peak_mask, 0, stream)[0]
-            # and bin them by distance beta_x from the caustic (Figs. 4-5)
-            info_holder["peak_stats"] = ml.ml_peak_statistics(h, FOLD_DISTANCE_EDGES, ml.ALONG_X, 0.0,
-                                                              mask=peak_mask, stream=stream)
-        if e: e[4].record(stream)
+        # counters and the map's uint32 wrap-around check (a 64-bit map sum)
         stats, _ = ml.ml_field_stats(h, stream)
+        if e: e[4].record(stream)
         ml.ml_field_destroy(h)
         info_holder["info"] = info
         info_holder["stats"] = stats
@@ -324,6 +348,15 @@ def run_ours(args, rank, world, local):
             timers.append(e)
         return info, stats
 
+    # the first step runs the autotuner (timed candidate builds and shots,
+    # cached for the process): its create is reported apart, untimed in the step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h0 = ml.ml_field_create(make_desc(True), stream)
+    torch.cuda.synchronize()
+    first_create_ms = (time.perf_counter() - t0) * 1e3
+    ml.ml_field_destroy(h0)
+    fp32_peak = measure_fp32_peak(ml, torch, stream, local, args.clocks_dir)
     for _ in range(args.warmup):
         step()
         flush.zero_()
@@ -352,9 +385,7 @@ def run_ours(args, rank, world, local):
         t_local = float(t.item())
     value = n_rays * (1 if sharded else world) / (t_local / 1e3)
 
-    # roofline of the dominant kernel (the shooting kernel): algorithmic FP32
-    # work per ray of this algorithm = 11 per near pair + 4p (two real Horner
-    # polynomials of degree p) + 6 (near fold, binning)
+    # roofline of the dominant kernel (the counting kernel)
     p = info["taylor_p"]
     shoot_ms = float(per[:, 1].mean())
     n_local = stats["rays_in"] + stats["rays_out"] + stats["rays_dropped"]   # this rank's rays
@@ -362,22 +393,34 @@ def run_ours(args, rank, world, local):
     if sharded:
         a, b = shard.ray_ranges(info["n_rays_x"], info["n_rays_y"], info["n1y"], world)[rank]
         expected_local = b - a
-    flops = 11.0 * stats["near_pairs"] + (4.0 * p + 6.0) * n_local
-    achieved = flops / (shoot_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    fixed_convention_flops = 11.0 * stats["near_pairs"] + (8.0 * p + 10.0) * n_local
-
+    launches = max(1, stats["launches"])
+    launch_s = shoot_ms / 1e3 / launches
+    # SURVEY §8(d)'s fixed count: 11 flop per near pair + (8p + 10) per ray
+    alg_flops = (11.0 * stats["near_pairs"] + (8.0 * p + 10.0) * n_local) / launches
+    # the FP32 arithmetic actually executed: rays evaluated one by one (the
+    # certified walk skips the rest), each its row polynomial as two real
+    # Horner chains (4p), 6 for the pixel, 11 per near pair at the mean near
+    # density (approximate for the evaluated rays)
+    evals = stats.get("rays_evaluated", n_local)
+    exec_flops = ((4.0 * p + 6.0) * evals + 11.0 * stats["near_pairs"] * evals / max(1, n_local)) / launches
+    peak = fp32_peak["two_lane_tflops"]
+    achieved = alg_flops / launch_s / 1e12
+    traffic = traffic_per_launch(n_local / launches)
+    hbm_peak, hbm_src = hbm_peak_gbs()
     out = {
         "metric": METRIC if args.workload == "paper" else
                   "rays/s of the Table-1 fold field (13,745 lenses) on 1 GB300; map L1 err vs FP64 oracle",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_local, "higher_is_better": True,
         "scaling": "strong" if sharded else "weak", "vs_baseline": None,
-        "dtype": "f32 near sum + f64 nodes",
+        "dtype": "f32 (f64 node bases, c_0, sheet)",
         "data": "synthetic (seeded lognormal lens disc; no dataset)",
         "config": {"workload": w.name + f", {N_TRACKS} light curves x {TRACK_SAMPLES}",
                    "n_lenses": int(w.lenses.n), "n_rays": int(n_rays),
-                   "map": f"{w.map_n[0]}x{w.map_n[1]} uint32", "precision": "mixed",
+                   "map": f"{w.map_n[0]}x{w.map_n[1]} uint32",
+                   "precision": "mixed: near sums, row series and c_1..c_p sums in FP32; node bases, "
+                                "c_0 and the sheet in FP64",
+                   "walk": args.walk, "build_flags": build_flags(),
                    "macro": "fold (Eq. 5)" if getattr(w, "macro", None) else "constant kappa, gamma (Eq. 1)",
                    "taylor_p": p, "far_bound_theta_e": info["far_bound"],
                    "l2_sub": [info["l2_sub_x"], info["l2_sub_y"]], "tuned_grid": bool(info["tuned"]),
@@ -385,26 +428,43 @@ def run_ours(args, rank, world, local):
                    "coefficient_build": {1: "direct", 2: "hierarchical"}.get(info["build"]),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": (f"one map sharded over {world} GPUs (level-1 bands, integer "
-                                   f"map sum)" if sharded else f"independent maps per GPU x{world}")},
+                                   f"map sum onto rank 0)" if sharded else f"independent maps per GPU x{world}")},
         "breakdown_ms": {"create": float(per[:, 0].mean()), "shoot": shoot_ms,
-                         "mu": float(per[:, 2].mean()),
-                         ("light_curves_and_peaks" if args.workload == "fold" else "light_curves"):
-                             float(per[:, 3].mean())},
+                         ("mu_light_curves_and_peaks" if args.workload == "fold" else "mu_and_light_curves"):
+                             float(per[:, 2].mean()),
+                         "stats_and_wrap_check": float(per[:, 3].mean())},
+        "first_create_with_autotuner_ms": first_create_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": traffic_per_launch(n_local / max(1, stats["launches"])),
-                     "kernel": "k_shoot_mixed", "flops_per_launch_fixed_convention":
-                         fixed_convention_flops / max(1, stats["launches"]),
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_shoot_mixed",
+                     "launch_ms": launch_s * 1e3,
+                     "flops_per_launch": alg_flops,
+                     "flop_count": "SURVEY 8(d): 11 per near pair + (8p+10) per lattice ray",
+                     "peak_note": "measured: ml_fp32_fma_peak two-lane FMA probe, best of 5 launches "
+                                  f"at {fp32_peak.get('sm_mhz')} MHz (scalar FFMA "
+                                  f"{fp32_peak['scalar_tflops']:.1f}, derived "
+                                  f"{fp32_peak['derived_tflops_at_max_clock']:.1f} TFLOP/s)",
+                     "executed": {"rays_evaluated_per_ray": evals / max(1, n_local),
+                                  "flops_per_launch": exec_flops,
+                                  "achieved": exec_flops / launch_s / 1e12,
+                                  "frac": exec_flops / launch_s / 1e12 / peak},
+                     "note": ("frac counts every lattice ray's fixed-convention work; the certified "
+                              "walk evaluates only the rays_evaluated_per_ray fraction and proves the "
+                              "others share an evaluated neighbour's pixel, so frac can exceed 1; "
+                              "executed.frac is the pipe's share of the arithmetic it ran")
+                             if args.walk == "certified" else None,
+                     "hbm": ({"achieved_gbs": traffic / launch_s / 1e9, "peak_gbs": hbm_peak,
+                              "frac": traffic / launch_s / 1e9 / hbm_peak, "peak_source": hbm_src}
+                             if traffic else None)},
         "shoot_rays_override": bool(args.shoot_rays),
         **({"true_peaks_5sigma": info_holder.get("peaks"),
             "peak_statistics": fold_peak_summary(info_holder["peak_stats"], info)}
-           if args.workload == "fold" else {}),
+           if args.workload == "fold" and consumer else {}),
         "rays_check": {"in": stats["rays_in"], "out": stats["rays_out"],
                        "dropped": stats["rays_dropped"], "total": n_local,
                        "conserved": n_local == expected_local},
-        "gpu_launches": int(args.steps * (BUILD_KERNELS + stats["launches"] + 2
-                                          + (4 if args.workload == "fold" else 0))),
+        "gpu_launches": int(args.steps * (BUILD_KERNELS + stats["launches"] + 1
+                                          + (2 if consumer else 0)
+                                          + (4 if args.workload == "fold" and consumer else 0))),
     }
     clk_sum = clk.summary()
     if clk_sum:
@@ -421,10 +481,59 @@ def run_ours(args, rank, world, local):
         # workload: its timing is the CPU baseline when it ran
         out["cpu_baseline"] = (cpu_baseline_of(oracle_run, w) if oracle_run
                                else cpu_baseline(w))
+    if sharded and not args.no_independent:
+        # the same ranks, one map of their own each (no exchange): weak scaling
+        out["independent_maps"] = independent_maps(ml, torch, w, grid_kw, stream, dev, rank, world, dist,
+                                                   args, make_desc, inputs)
+    if world == 1 and args.workload == "paper" and not args.no_sub:
+        out["batched"] = run_batched(_sub_args(args), rank, world, local, compact=True)
+        out["differentiable"] = run_differentiable(_sub_args(args), rank, world, local, compact=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def _sub_args(args):
+    """Arguments of the compact sub-records of the default line."""
+    import copy
+    a = copy.copy(args)
+    a.steps, a.warmup = 2, 1
+    a.no_e2e, a.no_cpu_baseline = True, True
+    return a
+
+
+def build_flags():
+    """Extra nvcc flags the loaded library was built with ([] = the default)."""
+    from paper_2308_14278_gb300 import build
+    return build.built_flags()
+
+
+def independent_maps(ml, torch, w0, grid_kw, stream, dev, rank, world, dist, args, make_desc, inputs):
+    """Weak-scaling companion of a sharded run: each rank shoots a whole map
+    of its own (seed = rank) with no data exchange; rays/s of the job."""
+    w = inputs.paper_map(seed=rank, n_rays=args.rays, map_px=args.map_px, n_tracks=N_TRACKS)
+    kw = dict(grid_kw)
+    if args.grid:
+        w.l1 = w0.l1
+    times = []
+    for k in range(1 + max(1, min(args.steps, 3))):
+        f = ml.Field(w, precision=ml.PREC_MIXED, **kw)
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f.shoot(stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            times.append(e0.elapsed_time(e1))
+        n = f.n_rays
+        f.close()
+    t = torch.tensor([float(np.mean(times))], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return {"value": n * world / (float(t.item()) / 1e3), "unit": UNIT, "scaling": "weak",
+            "ms_per_shot": float(t.item()), "note": "shooting only (field build outside the events)"}
 
 
 def e2e(ml, w, torch, dev, stream, tracks, args, flush):
@@ -528,22 +637,24 @@ def _events(torch, n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def run_batched(args, rank, world, local):
+def run_batched(args, rank, world, local, compact=False):
     """80 heterogeneous maps (2,000-20,000 lenses, 1e9-1e10 rays, 4096^2) and
     their 800 light curves as one CUDA-graph replay of the batched launch,
-    next to the same maps shot one at a time with their own default grids."""
+    next to the same maps shot one at a time, both with the batch's own
+    (autotuned) grids and orders and with Eq. 10's grids.  compact: the
+    sub-record of the default line (no e2e, no CPU baseline, no NCCL)."""
     import torch
     torch.cuda.set_device(local)
     import paper_2308_14278_gb300 as ml
     from paper_2308_14278_gb300 import inputs, shard
     ml.load()
     dist = None
-    if world > 1:
+    if world > 1 and not compact:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    # --shard: the ranks split one set of 80 maps (whole maps, balanced by
-    # rays, nothing exchanged); otherwise each rank runs its own 80 maps
-    sharded = bool(args.shard and world > 1)
+    # N > 1: the ranks split one set of 80 maps (whole maps, balanced by
+    # rays, nothing exchanged); --independent: each rank runs its own 80 maps
+    sharded = bool(dist is not None and not args.independent)
     seed = 0 if sharded else rank
     n_all, tpm, map_px = 80, 10, 4096
     ws = inputs.batched_maps(n_maps=n_all, seed=seed, map_px=map_px, ray_range=(1e9, 1e10),
@@ -556,8 +667,9 @@ def run_batched(args, rank, world, local):
     n_maps = len(ws)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    walk = ml.WALK_PER_RAY if args.walk == "per_ray" else ml.WALK_CERTIFIED
     t0 = time.perf_counter()
-    descs = [ml.make_desc(w, precision=ml.PREC_MIXED, tune=True) for w in ws]
+    descs = [ml.make_desc(w, precision=ml.PREC_MIXED, tune=True, walk=walk) for w in ws]
     b = ml.Batch(descs, tracks=tracks, n_samples=TRACK_SAMPLES, sigma_px=SIGMA_PX)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
@@ -570,7 +682,7 @@ def run_batched(args, rank, world, local):
     if dist:
         dist.barrier()
     times = []
-    with ClockSampler(local, args.clocks_dir) as clk:
+    with ClockSampler(local, args.clocks_dir, tag="_batched") as clk:
         for _ in range(args.steps):
             flush.zero_()
             e = _events(torch, 2)
@@ -593,58 +705,91 @@ def run_batched(args, rank, world, local):
             rays_job = int(r.item())
     value = rays_job / (t_local / 1e3)
 
-    # the same maps one at a time: own field, own default grid and order
-    fields = [ml.Field(w, precision=ml.PREC_MIXED) for w in ws]
+    # the same maps one at a time: (a) each with the batch's grid and order,
+    # (b) each with Eq. 10's level-1 cells and the paper's level-2 grid
     mu1 = torch.empty((map_px, map_px), dtype=torch.float32, device="cuda")
     lc1 = torch.empty((tpm, TRACK_SAMPLES), dtype=torch.float32, device="cuda")
 
-    def one_at_a_time():
+    def one_at_a_time(fields):
         for f, tr in zip(fields, tracks):
             f.clear(stream)
             f.shoot(stream=stream)
             ml.ml_magnification_map(f.h, ml.MAP_MU_F32, mu1, stream)
             ml.ml_light_curves(f.h, tr, TRACK_SAMPLES, SIGMA_PX, lc1, stream)
 
-    one_at_a_time()
-    single = []
-    for _ in range(max(1, min(args.steps, 2))):
-        flush.zero_()
-        e = _events(torch, 2)
-        e[0].record(stream)
-        one_at_a_time()
-        e[1].record(stream)
-        torch.cuda.synchronize()
-        single.append(e[0].elapsed_time(e[1]))
-    single_ms = float(np.mean(single))
-    single_p = sorted({f.info["taylor_p"] for f in fields})
-    for f in fields:
+    def time_fields(fields):
+        one_at_a_time(fields)
+        single = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.zero_()
+            e = _events(torch, 2)
+            e[0].record(stream)
+            one_at_a_time(fields)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            single.append(e[0].elapsed_time(e[1]))
+        return float(np.mean(single))
+
+    same = [ml.Field(w, precision=ml.PREC_MIXED, walk=walk, taylor_p=i["taylor_p"],
+                     l1=(i["n1x"] * i["l3x"], i["n1y"] * i["l3y"]), l2_sub=(i["l2_sub_x"], i["l2_sub_y"]),
+                     span_far=i["span_far"])
+            for w, i in zip(ws, infos)]
+    same_ms = time_fields(same)
+    # the batch's map 0 against the same map shot alone with the same grid
+    b.run(use_graph=True)
+    same[0].clear(stream)
+    same[0].shoot(stream=stream)
+    batch_equals_single = bool(torch.equal(b.counts(0), same[0].counts()))
+    for f in same:
+        f.close()
+    paper = [ml.Field(w, precision=ml.PREC_MIXED, walk=walk) for w in ws]
+    paper_ms = time_fields(paper)
+    paper_p = sorted({f.info["taylor_p"] for f in paper})
+    for f in paper:
         f.close()
 
-    flops = sum(11.0 * st["near_pairs"] + (4.0 * i["taylor_p"] + 6.0) * i["n_rays_x"] * i["n_rays_y"]
+    # map error against the oracle: a stripe of map 0 shot alone on its batch grid
+    map_err = None
+    if rank == 0 and not args.no_parity:
+        w0, i0 = ws[0], infos[0]
+        w0.l1 = (i0["n1x"] * i0["l3x"], i0["n1y"] * i0["l3y"])
+        map_err, _ = parity_stripe(ml, w0, stream, dict(l2_sub=(i0["l2_sub_x"], i0["l2_sub_y"]),
+                                                        taylor_p=i0["taylor_p"], walk=walk),
+                                   n_rays=200_000)
+
+    fixed = sum(11.0 * st["near_pairs"] + (8.0 * i["taylor_p"] + 10.0) * i["n_rays_x"] * i["n_rays_y"]
                 for st, i in zip(stats, infos))
-    achieved = flops / (step_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    evals = sum(st["rays_evaluated"] for st in stats)
+    fp32_peak = measure_fp32_peak(ml, torch, stream, local, args.clocks_dir, launches=3)
+    peak = fp32_peak["two_lane_tflops"]
+    achieved = fixed / (step_ms / 1e3) / 1e12
     out = {
-        "metric": "rays/s of 80 batched maps on 1 GB300 (one CUDA graph, a persistent launch per Taylor order)",
+        "metric": "rays/s of 80 batched maps on 1 GB300 (one CUDA graph: a persistent launch per Taylor order)",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_local, "higher_is_better": True, "scaling": "strong" if sharded else "weak",
         "vs_baseline": None,
-        "dtype": "f32 near sum + f64 nodes", "data": "synthetic (seeded lognormal lens discs; no dataset)",
+        "dtype": "f32 (f64 node bases, c_0, sheet)", "data": "synthetic (seeded lognormal lens discs; no dataset)",
         "config": {"workload": f"batched: {n_all} maps, 2,000-20,000 lenses, kappa_* in "
                                f"{{0.002, 0.005, 0.01}}, kappa+gamma 0.95-0.99, 1e9-1e10 rays each, "
                                f"{map_px}^2 uint32, {n_all * tpm} light curves x {TRACK_SAMPLES}",
                    "total_rays": int(rays_job if sharded else rays), "taylor_p": orders, "tuned_grids": True,
-                   "launches_per_step": len(orders),
+                   "walk": args.walk, "launches_per_step": len(orders),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": (f"one set of {n_all} maps split over {world} GPUs (whole maps, "
                                    f"balanced by rays)" if sharded else f"independent batches per GPU x{world}")},
         "create_s": create_s,
-        "one_map_at_a_time": {"ms_per_step": single_ms, "value": rays / (single_ms / 1e3),
-                              "taylor_p": single_p, "speedup_of_batched": single_ms / step_ms},
+        "one_map_at_a_time_same_grids": {"ms_per_step": same_ms, "value": rays / (same_ms / 1e3),
+                                         "speedup_of_batched": same_ms / step_ms},
+        "one_map_at_a_time_eq10_grids": {"ms_per_step": paper_ms, "value": rays / (paper_ms / 1e3),
+                                         "taylor_p": paper_p, "speedup_of_batched": paper_ms / step_ms},
+        "batch_map_equals_single_map": batch_equals_single,
+        "map_l1_vs_oracle": map_err,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_shoot_batch",
-                     "note": "whole graph step time (clear, shoot, mu, curves) as the kernel time",
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+                     "rays_evaluated_per_ray": evals / max(1, rays),
+                     "note": "whole graph step time (clear, shoot, mu, curves) as the kernel time; "
+                             "SURVEY 8(d)'s fixed flop count per lattice ray",
+                     "peak_note": "measured: ml_fp32_fma_peak two-lane FMA probe"},
         "rays_check": {"conserved": all(st["rays_in"] + st["rays_out"] + st["rays_dropped"] ==
                                         i["n_rays_x"] * i["n_rays_y"] for st, i in zip(stats, infos))},
         "gpu_launches": int(args.steps * (len(orders) + 2 * n_maps)),
@@ -661,7 +806,7 @@ def run_batched(args, rank, world, local):
         for _ in range(max(1, min(args.steps, 2))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            bb = ml.Batch([ml.make_desc(w, precision=ml.PREC_MIXED, tune=True) for w in ws],
+            bb = ml.Batch([ml.make_desc(w, precision=ml.PREC_MIXED, tune=True, walk=walk) for w in ws],
                           tracks=tracks, n_samples=TRACK_SAMPLES, sigma_px=SIGMA_PX)
             bb.run(use_graph=True)
             ml._check(ml.load().ml_batch_curves(bb.h, curves_h.numpy().ctypes.data, 0, None))
@@ -684,6 +829,12 @@ def run_batched(args, rank, world, local):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    if compact:
+        keep = ("value", "unit", "ms_per_step", "create_s", "one_map_at_a_time_same_grids",
+                "one_map_at_a_time_eq10_grids", "batch_map_equals_single_map", "map_l1_vs_oracle",
+                "roofline", "rays_check")
+        out = {k: out[k] for k in keep} | {"config": {"workload": out["config"]["workload"],
+                                                       "taylor_p": orders, "launches_per_step": len(orders)}}
     return out
 
 
@@ -691,7 +842,7 @@ def run_batched(args, rank, world, local):
 # differentiable map: CIC forward + hand-written adjoint
 # ---------------------------------------------------------------------------
 
-def run_differentiable(args, rank, world, local):
+def run_differentiable(args, rank, world, local, compact=False):
     """One optimisation step of a lens field against a target map: create the
     field from device lens arrays, the CIC map (ml_cic_forward), dL/dM of
     L = |M - T|^2, and the adjoint (ml_cic_backward) to d/d(x_k, y_k, m_k,
@@ -702,7 +853,7 @@ def run_differentiable(args, rank, world, local):
     from paper_2308_14278_gb300 import inputs
     ml.load()
     dist = None
-    if world > 1:
+    if world > 1 and not compact:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = inputs.differentiable_field(seed=rank)
@@ -722,9 +873,9 @@ def run_differentiable(args, rank, world, local):
     loss = torch.empty((), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
-    def desc():
+    def desc(lens=None):
         d = ml.make_desc(w, precision=ml.PREC_MIXED, deposit=ml.DEPOSIT_CIC)
-        d.lens_x, d.lens_y, d.lens_m = (t.data_ptr() for t in lens_dev)
+        d.lens_x, d.lens_y, d.lens_m = (t.data_ptr() for t in (lens or lens_dev))
         d.lens_mem_is_device = 1
         return d
 
@@ -753,7 +904,7 @@ def run_differentiable(args, rank, world, local):
     if dist:
         dist.barrier()
     timers = []
-    with ClockSampler(local, args.clocks_dir) as clk:
+    with ClockSampler(local, args.clocks_dir, tag="_differentiable") as clk:
         for _ in range(args.steps):
             flush.zero_()
             e = _events(torch, 5)
@@ -761,6 +912,32 @@ def run_differentiable(args, rank, world, local):
             timers.append(e)
         torch.cuda.synchronize()
     per = np.array([[a.elapsed_time(c) for a, c in zip(e[:-1], e[1:])] for e in timers])
+    # finite-difference spot check of one gradient component: the lens at least
+    # 0.3 theta_E outside the ray rectangle with the largest |dL/dx|, central
+    # differences of the loss through the library's forward at h = 3e-4
+    gl_h = gl.cpu().numpy()
+
+    def loss_of(lens):
+        h = ml.ml_field_create(desc(lens), stream)
+        ml.ml_cic_forward(h, mu, stream)
+        v = float(((mu.double() - T.double()) ** 2).sum().item())
+        ml.ml_field_destroy(h)
+        return v
+
+    rb = hold["info"]
+    x0, y0, x1, y1 = rb["ray_x0"], rb["ray_y0"], rb["ray_x1"], rb["ray_y1"]
+    dist_out = np.hypot(np.maximum(np.maximum(x0 - w.lenses.x, w.lenses.x - x1), 0),
+                        np.maximum(np.maximum(y0 - w.lenses.y, w.lenses.y - y1), 0))
+    k = int(np.argmax(np.where(dist_out > 0.3, np.abs(gl_h[:, 0]), -1.0)))
+    hfd = 3e-4
+    base = [loss_of(None) for _ in range(3)]
+    xp, xm = lens_dev[0].clone(), lens_dev[0].clone()
+    xp[k] += hfd
+    xm[k] -= hfd
+    fd = (loss_of([xp, lens_dev[1], lens_dev[2]]) - loss_of([xm, lens_dev[1], lens_dev[2]])) / (2 * hfd)
+    fd_check = {"lens": k, "component": "x", "h": hfd, "finite_difference": fd, "adjoint": float(gl_h[k, 0]),
+                "rel_diff": abs(fd - gl_h[k, 0]) / max(abs(gl_h[k, 0]), 1e-300),
+                "loss_spread_over_2h": (max(base) - min(base)) / (2 * hfd)}
     step_ms = float(per.sum(axis=1).mean())
     info, stats = hold["info"], hold["stats"]
     n_rays = info["n_rays_x"] * info["n_rays_y"]
@@ -779,12 +956,14 @@ def run_differentiable(args, rank, world, local):
     # near pair in the near pass
     flops = 11.0 * pairs + (4.0 * p + 6.0) * n_rays + live * (15.0 * pairs + (5.0 * p + 25.0) * n_rays)
     achieved = flops / (bw_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak = measure_fp32_peak(ml, torch, stream, local, args.clocks_dir, launches=3)
+    peak = fp32_peak["two_lane_tflops"]
+    peak_note = "measured: ml_fp32_fma_peak two-lane FMA probe"
     out = {
         "metric": "rays/s of a CIC forward + adjoint step (1,000 lenses, 4e8 rays) on 1 GB300",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_local, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 near sum + f64 nodes, f64 gradient sums",
+        "dtype": "f32 (f64 node bases, c_0, sheet; f64 gradient sums)",
         "data": "synthetic (seeded lognormal lens disc; target map from seed + 1000)",
         "config": {"workload": w.name + ", loss |M - T|^2, gradient w.r.t. all lenses, kappa, gamma, "
                                "kappa_*", "n_lenses": int(w.lenses.n), "n_rays": int(n_rays),
@@ -794,9 +973,10 @@ def run_differentiable(args, rank, world, local):
         "breakdown_ms": {"create": float(per[:, 0].mean()), "forward": float(per[:, 1].mean()),
                          "loss": float(per[:, 2].mean()), "backward": bw_ms},
         "loss": float(loss.item()),
+        "gradient_fd_check": fd_check,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "k_adj_rays + k_adj_far",
-                     "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+                     "peak_note": peak_note},
         "gpu_launches": int(args.steps * (BUILD_KERNELS + 2 + 3)),
     }
     clk_sum = clk.summary()
@@ -833,6 +1013,9 @@ def run_differentiable(args, rank, world, local):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    if compact:
+        keep = ("value", "unit", "ms_per_step", "breakdown_ms", "loss", "gradient_fd_check", "roofline")
+        out = {k: out[k] for k in keep} | {"config": {"workload": out["config"]["workload"]}}
     return out
 
 

@@ -173,6 +173,13 @@ typedef struct {
      * inside.  The near/far modes need every ray inside the sheet. */
     int32_t sheet_shape;
     double kappa0, d_x, d_y;
+    /* Certified walk (ML_WALK_CERTIFIED): a warp's level-2 column that has
+     * near lenses is walked in certified spans only if every near lens lies
+     * farther than span_far lattice spacings (l3x) from its rays, else ray by
+     * ray.  0: the library's choice (3000; with tune, whichever of 3000 and
+     * +inf measured faster; in a batch, +inf).  Any value gives the same
+     * counts. */
+    double span_far;
 } ml_field_desc;
 
 /* Macro models of ml_field_desc.macro_mode. */
@@ -199,6 +206,7 @@ typedef struct {
     int32_t tuned;                          /* 1 if the autotuner chose the level-2 grid */
     double far_bound;                       /* truncation bound at taylor_p (theta_E) */
     double mu_per_count;                    /* S_I / S_S of Eq. 12 */
+    double span_far;                        /* certified walk's lens-column threshold in use */
 } ml_field_params;
 
 /*

@@ -73,6 +73,7 @@ class FieldDesc(C.Structure):
         ("tune", C.c_int32), ("walk", C.c_int32),
         ("macro_mode", C.c_int32), ("sheet_shape", C.c_int32),
         ("kappa0", C.c_double), ("d_x", C.c_double), ("d_y", C.c_double),
+        ("span_far", C.c_double),
     ]
 
 
@@ -90,7 +91,7 @@ class FieldParams(C.Structure):
         ("taylor_p", C.c_int32), ("l2_sub_x", C.c_int32), ("l2_sub_y", C.c_int32),
         ("precision", C.c_int32), ("deposit", C.c_int32), ("max_near", C.c_int32),
         ("build", C.c_int32), ("tuned", C.c_int32),
-        ("far_bound", C.c_double), ("mu_per_count", C.c_double),
+        ("far_bound", C.c_double), ("mu_per_count", C.c_double), ("span_far", C.c_double),
     ]
 
     def as_dict(self):
@@ -338,7 +339,7 @@ def ml_field_destroy(field):
 
 def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_AUTO,
               taylor_p=0, far_tol=0.0, l1=None, l2_sub=(0, 0), max_launch_rays=0, lens_arrays=None,
-              tune=False, walk=WALK_CERTIFIED):
+              tune=False, walk=WALK_CERTIFIED, span_far=0.0):
     """ml_field_desc for an inputs.Workload (lens arrays from host numpy)."""
     w = workload
     lx, ly, lm = lens_arrays if lens_arrays is not None else (w.lenses.x, w.lenses.y, w.lenses.m)
@@ -372,6 +373,7 @@ def make_desc(workload, precision=PREC_MIXED, deposit=DEPOSIT_NGP, build=BUILD_A
     d.l2_sub_x, d.l2_sub_y = l2_sub
     d.tune = 1 if tune else 0
     d.walk = walk
+    d.span_far = span_far
     macro = getattr(w, "macro", None)
     if macro is not None:
         d.macro_mode = MACRO_FOLD

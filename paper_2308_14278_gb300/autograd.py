@@ -20,13 +20,26 @@ from .inputs import LensField, Workload
 
 
 def _desc(x, y, m, kappa, gamma, kappa_star, spec):
+    """Descriptor of the field.  Lens tensors on the current CUDA device are
+    passed to the library as device pointers (no copy to the host); others
+    as host arrays."""
     w = Workload("differentiable", LensField(None, None, None), float(kappa), float(gamma),
                  float(kappa_star), spec["sheet"], spec["map_box"], spec["map_n"],
                  ray_box=spec.get("ray_box"), ray_n=spec.get("ray_n"), n_av=spec.get("n_av", 0.0))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    on_dev = all(t.device == dev for t in (x, y, m))
+    if on_dev:
+        lens = [t.detach().to(torch.float64).contiguous() for t in (x, y, m)]
+        host = [np.zeros(0)] * 3
+    else:
+        host = [t.detach().cpu().numpy() for t in (x, y, m)]
     d = make_desc(w, precision=PREC_MIXED, deposit=DEPOSIT_CIC, taylor_p=spec.get("taylor_p", 0),
-                  l1=spec.get("l1"), l2_sub=spec.get("l2_sub", (0, 0)),
-                  lens_arrays=(x.detach().cpu().numpy(), y.detach().cpu().numpy(),
-                               m.detach().cpu().numpy()))
+                  l1=spec.get("l1"), l2_sub=spec.get("l2_sub", (0, 0)), lens_arrays=host)
+    if on_dev:
+        d.lens_x, d.lens_y, d.lens_m = (t.data_ptr() for t in lens)
+        d.n_lens = lens[0].numel()
+        d.lens_mem_is_device = 1
+        d._keep = lens           # alive until the field is created
     return d
 
 

@@ -88,6 +88,10 @@ struct ml_field {
     uint64_t rays_asked = 0, launches = 0;
     int64_t n_lens = 0;
     int32_t tuned = 0;
+    // certified walk: a warp's level-2 column with near lenses is spanned only
+    // if they all lie farther than this from its rays (lattice units; +inf:
+    // such columns always take the per-ray walk); the autotuner measures both
+    float span_far = ML_SPAN_FAR;
     ml_field_desc desc{};            // parameters (lens pointers cleared)
     std::vector<double> worst;       // truncation bound per Taylor order (worst level-1 cell)
     // device buffers
@@ -299,6 +303,7 @@ ml_status validate(const ml_field_desc *d)
         return fail(ML_ERR_INVALID_ARG, "unknown sheet_shape");
     if (d->walk != ML_WALK_CERTIFIED && d->walk != ML_WALK_PER_RAY)
         return fail(ML_ERR_INVALID_ARG, "unknown walk");
+    if (!(d->span_far >= 0.0)) return fail(ML_ERR_INVALID_ARG, "span_far must be >= 0");
     if (d->macro_mode == ML_MACRO_FOLD &&
         (!is_fin(d->kappa0) || !is_fin(d->d_x) || !is_fin(d->d_y) || d->kappa0 == 1.0 || d->d_x == 0.0))
         return fail(ML_ERR_INVALID_ARG, "fold macro needs finite kappa0 != 1 and d_x != 0");
@@ -382,6 +387,7 @@ struct GridChoice {
     int sx = 20, sy = 20, p = 0;
     double l1x = 0.0, l1y = 0.0;    // level-1 size; 0 = Eq. 10's
     double cost = 0.0;
+    float span_far = ML_SPAN_FAR;   // certified walk's lens-column threshold (see ml_field)
 };
 
 // One candidate level-2 grid of a field: its subdivisions, the compiled
@@ -393,6 +399,7 @@ struct TuneCand {
     double l1x, l1y;                // level-1 size; 0 = Eq. 10's
     double n2x;                     // rays per level-2 cell along a lattice row
     int walk;                       // ML_WALK_* of the field
+    double span_frac;               // expected share of rays the certified walk may span
 };
 
 // Shooting time per ray of the certified walk, picoseconds: a least-squares
@@ -405,10 +412,21 @@ double span_cost_ps(int P, double near_per_ray, double n2x)
     return 0.145 + 0.238 * near_per_ray + 30.6 / std::max(1.0, n2x) + 0.0159 * P;
 }
 
+// The certified walk spans a warp's level-2 column only when every near lens
+// lies farther than ML_SPAN_FAR lattice units from its rays; elsewhere it
+// runs the per-ray walk.  For lenses spread evenly over the 3 x 3 block of
+// level-1 cells, the share of columns without such a lens is
+// exp(-near * pi (ML_SPAN_FAR l3)^2 / (9 l1x l1y)).
+double span_share(double near_per_ray, double l3, double l1x, double l1y)
+{
+    const double r = (double)ML_SPAN_FAR * l3;
+    return exp(-near_per_ray * 3.14159265358979 * r * r / (9.0 * l1x * l1y));
+}
+
 double cand_cost(const TuneCand &c, int P)
 {
-    const double ps = c.walk == ML_WALK_CERTIFIED ? span_cost_ps(P, c.near_per_ray, c.n2x)
-                                                  : ray_cost_ps(P, c.near_per_ray);
+    const double f = c.walk == ML_WALK_CERTIFIED ? c.span_frac : 0.0;
+    const double ps = f * span_cost_ps(P, c.near_per_ray, c.n2x) + (1.0 - f) * ray_cost_ps(P, c.near_per_ray);
     return c.rays * ps * 1e-3 + c.nodes * (P + 1) * kNodeCostNs + c.cells * kCellCostNs;   // ns
 }
 
@@ -534,7 +552,8 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
         if (d.macro_mode == ML_MACRO_FOLD) p = std::max(p, 2);
         res.push_back(TuneCand{c.sx, c.sy, mixed_p_supported(p), (double)c.g.N2x * (double)c.g.N2y,
                                (double)c.g.n3x * (double)c.g.n3y, (double)c.g.N1x * (double)c.g.N1y,
-                               near_per_ray, c.l1x, c.l1y, (double)c.g.n2x, d.walk});
+                               near_per_ray, c.l1x, c.l1y, (double)c.g.n2x, d.walk,
+                               span_share(near_per_ray, c.g.l3x, c.g.l1x, c.g.l1y)});
     }
     for (Cand &c : cands) {
         if (c.cells) cudaFreeAsync(c.cells, s);
@@ -566,7 +585,8 @@ GridChoice best_single(const std::vector<TuneCand> &cands)
 }
 
 ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
-                       const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms);
+                       const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms,
+                       float &span_far);
 
 std::unordered_map<uint64_t, GridChoice> g_measured;   // guarded by g_tune_mu
 
@@ -612,9 +632,10 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
     for (size_t i = 0; i < std::min<size_t>(3, order.size()); ++i) {
         const TuneCand &c = cands[order[i]];
         double est = 0.0;
+        float far = ML_SPAN_FAR;
         // a candidate that cannot be built (near lists too long for the
         // mixed kernel's shared memory, memory) is passed over
-        if (measure_grid(d, hx, hy, hm, c, s, est) != ML_OK) {
+        if (measure_grid(d, hx, hy, hm, c, s, est, far) != ML_OK) {
             cudaGetLastError();
             continue;
         }
@@ -626,6 +647,7 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
             best_est = est;
             best.sx = c.sx; best.sy = c.sy; best.p = c.P; best.cost = cand_cost(c, c.P);
             best.l1x = c.l1x; best.l1y = c.l1y;
+            best.span_far = far;
         }
     }
     g_err.clear();
@@ -703,8 +725,10 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
         d->l2_sub_y = gc.sy;
         d->l1_x = gc.l1x;
         d->l1_y = gc.l1y;
+        if (d->span_far == 0.0) f->span_far = gc.span_far;
         f->tuned = 1;
     }
+    if (d->span_far > 0.0) f->span_far = (float)std::min(d->span_far, 3.0e38);
     ml_status st = derive_geometry(*d, hx, hy, f->g);
     if (st != ML_OK) return st;
     Geo &g = f->g;
@@ -862,7 +886,8 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
 // whole lattice.  The lenses come from the tuner's host copies (the
 // descriptor being built has handed its own pointers over already).
 ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
-                       const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms)
+                       const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms,
+                       float &span_far)
 {
     ml_field_desc dc = d;
     dc.lens_x = hx.data();
@@ -894,21 +919,34 @@ ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, co
         const uint64_t n = std::min<uint64_t>(total / 2, std::max<uint64_t>(500000000ull, total / 100));
         const uint64_t r0 = (total - 2 * n) / 2;
         const uint64_t warm = std::min<uint64_t>(n, 64ull * (uint64_t)g.n3x);
-        float ms[2] = {0.f, 0.f};
-        st = ml_shoot_rays(f, r0, r0 + warm, s);
-        for (int q = 0; q < 2 && st == ML_OK && n > 0; ++q) {
-            ce = cudaEventRecord(e1, s);
-            if (ce == cudaSuccess) st = ml_shoot_rays(f, r0, r0 + (q + 1) * n, s);
-            if (st == ML_OK && ce == cudaSuccess) ce = cudaEventRecord(e2, s);
-            if (st == ML_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e2);
-            if (st == ML_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms[q], e1, e2);
-            if (st == ML_OK && ce != cudaSuccess) st = cuda_fail(ce, "grid autotuner");
+        // the certified walk is timed with lens columns spanned beyond
+        // ML_SPAN_FAR and with them always walked ray by ray; the faster counts
+        const bool certified = f->desc.walk == ML_WALK_CERTIFIED && f->g.deposit == ML_DEPOSIT_NGP;
+        const float fars[2] = {ML_SPAN_FAR, 3.0e38f};
+        double best_ray = -1.0;
+        for (int v = 0; v < (certified ? 2 : 1) && st == ML_OK; ++v) {
+            f->span_far = fars[v];
+            float ms[2] = {0.f, 0.f};
+            st = ml_shoot_rays(f, r0, r0 + warm, s);
+            for (int q = 0; q < 2 && st == ML_OK && n > 0; ++q) {
+                ce = cudaEventRecord(e1, s);
+                if (ce == cudaSuccess) st = ml_shoot_rays(f, r0, r0 + (q + 1) * n, s);
+                if (st == ML_OK && ce == cudaSuccess) ce = cudaEventRecord(e2, s);
+                if (st == ML_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e2);
+                if (st == ML_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms[q], e1, e2);
+                if (st == ML_OK && ce != cudaSuccess) st = cuda_fail(ce, "grid autotuner");
+            }
+            const double per_ray = n > 0 ? std::max(0.0, (double)(ms[1] - ms[0])) / (double)n : 0.0;
+            if (st == ML_OK && (best_ray < 0.0 || per_ray < best_ray)) {
+                best_ray = per_ray;
+                span_far = fars[v];
+            }
+            if (st == ML_OK && getenv("ML_TUNE_LOG"))
+                fprintf(stderr, "ml tune:   create %.2f ms, %.3g and %.3g of %.3g rays in %.3f and %.3f ms%s\n",
+                        create_ms, (double)n, (double)(2 * n), (double)total, ms[0], ms[1],
+                        certified ? (v ? " (lens columns per ray)" : " (lens columns spanned)") : "");
         }
-        const double per_ray = n > 0 ? std::max(0.0, (double)(ms[1] - ms[0])) / (double)n : 0.0;
-        if (st == ML_OK) est_ms = create_ms + per_ray * (double)total;
-        if (st == ML_OK && getenv("ML_TUNE_LOG"))
-            fprintf(stderr, "ml tune:   create %.2f ms, %.3g and %.3g of %.3g rays in %.3f and %.3f ms\n",
-                    create_ms, (double)n, (double)(2 * n), (double)total, ms[0], ms[1]);
+        if (st == ML_OK) est_ms = create_ms + best_ray * (double)total;
     }
     if (e1) cudaEventDestroy(e1);
     if (e2) cudaEventDestroy(e2);
@@ -934,6 +972,7 @@ ShootArgs make_args(const ml_field *f)
     const Geo &g = f->g;
     a.near_cap = std::max(1, f->max_near);
     a.walk = f->desc.walk;
+    a.span_far = f->span_far;
     a.l3x_f = (float)g.l3x;
     a.l3x_lo = (float)(g.l3x - (double)a.l3x_f);
     a.c0_f = (float)(0.5 - 0.5 * (double)g.n2x);
@@ -1006,6 +1045,12 @@ struct ml_batch {
     float *d_taps = nullptr, *d_curves = nullptr;
     cudaStream_t s_int = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // one branch per Taylor order: the groups' persistent launches run on
+    // streams of their own (parallel branches of the graph), so that one
+    // group's blocks fill the SMs another group's tail leaves idle
+    std::vector<cudaStream_t> s_grp;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void *> owned;
@@ -1027,7 +1072,12 @@ struct ml_batch {
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (s_int) cudaStreamDestroy(s_int);
-        exec = nullptr; graph = nullptr; ev_in = ev_out = nullptr; s_int = nullptr;
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        for (cudaEvent_t ev : ev_join) cudaEventDestroy(ev);
+        for (cudaStream_t st : s_grp) cudaStreamDestroy(st);
+        ev_join.clear();
+        s_grp.clear();
+        exec = nullptr; graph = nullptr; ev_in = ev_out = ev_fork = nullptr; s_int = nullptr;
         for (void *q : owned) cudaFree(q);
         owned.clear();
         flag_put(h_abort);
@@ -1054,8 +1104,13 @@ cudaError_t batch_enqueue(ml_batch *b, cudaStream_t s)
         if ((e = cudaMemsetAsync(f->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     }
     if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-    for (const ml_batch::Group &gr : b->groups) {
+    for (const ml_batch::Group &gr : b->groups)
         if ((e = cudaMemsetAsync(gr.d_work, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess) return e;
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const ml_batch::Group &gr = b->groups[gi];
+        cudaStream_t sg = b->s_grp[gi];
+        if ((e = cudaStreamWaitEvent(sg, b->ev_fork, 0)) != cudaSuccess) return e;
         BatchArgs ba;
         ba.args = gr.d_args;
         ba.task_base = gr.d_base;
@@ -1066,8 +1121,11 @@ cudaError_t batch_enqueue(ml_batch *b, cudaStream_t s)
         ba.work = gr.d_work;
         ba.abort_flag = b->d_abort;
         ba.status = b->d_status;
-        if ((e = launch_batch(ba, gr.p, b->num_sms, s)) != cudaSuccess) return e;
+        if ((e = launch_batch(ba, gr.p, b->num_sms, sg)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(b->ev_join[gi], sg)) != cudaSuccess) return e;
     }
+    for (cudaEvent_t ev : b->ev_join)
+        if ((e = cudaStreamWaitEvent(s, ev, 0)) != cudaSuccess) return e;
     for (size_t i = 0; i < b->fields.size(); ++i) {
         const ml_field *f = b->fields[i];
         const Geo &g = f->g;
@@ -1118,7 +1176,13 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
             if (e == cudaSuccess) e = cudaMemcpyAsync(dm, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, s);
         }
         GridChoice best;
-        if (e == cudaSuccess) st = tune_grid(plan[i], hx, hy, hm, dx, dy, dm, s, false, best);
+        // the batch's grids come from the cost model alone (timing every map
+        // would cost more than it saves); the per-ray model ranks them: on
+        // the lens-dense maps of a batch the certified walk runs mostly per
+        // ray, and the certified model (fitted on a sparse field) misranks
+        ml_field_desc model = plan[i];
+        model.walk = ML_WALK_PER_RAY;
+        if (e == cudaSuccess) st = tune_grid(model, hx, hy, hm, dx, dy, dm, s, false, best);
         cudaFreeAsync(dx, s);
         cudaFreeAsync(dy, s);
         cudaFreeAsync(dm, s);
@@ -1139,6 +1203,9 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
         ml_status st = create_plan(&plan[i], s, b->fields[i]);
         if (st != ML_OK) return fail(st, "map " + std::to_string(i) + ": " + g_err);
         b->fields[i]->tuned = tuned[i];
+        // not timed per map: the batches measured (lens-dense fields) run
+        // faster with lens columns walked ray by ray
+        if (plan[i].span_far == 0.0) b->fields[i]->span_far = 3.0e38f;
     }
     // coefficient builds of different maps overlap on a few streams
     {
@@ -1222,6 +1289,15 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
     ML_CK(cudaStreamCreateWithFlags(&b->s_int, cudaStreamNonBlocking));
     ML_CK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     ML_CK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+    ML_CK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        cudaStream_t sg = nullptr;
+        cudaEvent_t ev = nullptr;
+        ML_CK(cudaStreamCreateWithFlags(&sg, cudaStreamNonBlocking));
+        b->s_grp.push_back(sg);
+        ML_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->ev_join.push_back(ev);
+    }
     ML_CK(cudaStreamSynchronize(s));
     return ML_OK;
 }
@@ -1772,6 +1848,7 @@ ml_status ml_field_info(const ml_field *f, ml_field_params *out)
     out->build = f->build_used;
     out->far_bound = f->far_bound;
     out->mu_per_count = (g.l3x * g.l3y) / (g.dpx * g.dpy);
+    out->span_far = f->span_far;
     return ML_OK;
 }
 

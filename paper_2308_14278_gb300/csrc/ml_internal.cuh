@@ -15,6 +15,21 @@ constexpr uint32_t PIX_OUT = 0xFFFFFFFFu;   // run-length code: outside the map
 constexpr uint32_t PIX_DROP = 0xFFFFFFFEu;  // run-length code: ray hit a lens
 constexpr int WARPS_PER_CTA = 8;
 
+// The certified walk (ML_WALK_CERTIFIED): rays it evaluates per step (its
+// window), rays short of the predicted pixel edge at which a window starts,
+// and the distance in lattice units within which a near lens makes it hand a
+// warp's level-2 column to the per-ray walk (runs shorten and certified spans
+// stay short near a lens).
+#ifndef ML_SPAN_W
+#define ML_SPAN_W 2
+#endif
+#ifndef ML_SPAN_OFF
+#define ML_SPAN_OFF 1
+#endif
+#ifndef ML_SPAN_FAR
+#define ML_SPAN_FAR 3000.0f
+#endif
+
 // Parameters derived from an ml_field_desc (§3.1 and §3.2).
 struct Geo {
     double kappa, gamma, kappa_star;
@@ -78,6 +93,8 @@ struct ShootArgs {
     int64_t n_tasks;
     int near_cap;                   // float4 slots of shared memory per warp
     int walk;                       // ML_WALK_CERTIFIED or ML_WALK_PER_RAY (mixed NGP)
+    float span_far;                 // certified walk: lens columns spanned only if every near
+                                    // lens lies farther than this (lattice units)
     // float constants of the mixed kernel
     float l3x_f, l3x_lo, c0_f, ipx_f, ipy_f;
     float cxy_f;                    // change of the u slope of beta_x per ray row (fold: d_y l3y l3x / dpx)

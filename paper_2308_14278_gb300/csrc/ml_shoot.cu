@@ -23,15 +23,6 @@
 #ifndef ML_MIN_BLOCKS
 #define ML_MIN_BLOCKS 3
 #endif
-// Rays the certified walk evaluates per step (its window).
-#ifndef ML_SPAN_W
-#define ML_SPAN_W 2
-#endif
-// Lattice units within which a near lens makes the certified walk hand a warp's
-// column to the per-ray walk (runs shorten and spans stay short near a lens).
-#ifndef ML_SPAN_FAR
-#define ML_SPAN_FAR 3000.0f
-#endif
 
 namespace ml {
 
@@ -732,7 +723,7 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
                 const float gX = sX > 0.f ? __fsub_rn(1.f, fX) : fX;
                 const float gY = sY > 0.f ? __fsub_rn(1.f, fY) : fY;
                 const float n = fminf(fminf(gX * rcp_approx(fabsf(sX)), gY * rcp_approx(fabsf(sY))), 1048576.f);
-                gap = max(1, floor_to_int(n) - 1);
+                gap = max(1, floor_to_int(n) - ML_SPAN_OFF);
             }
         }
     }
@@ -790,7 +781,7 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
         pairs += (unsigned long long)nn * (unsigned long long)(k1 - k0);
         if constexpr (SPAN) {
             // the certified walk where runs are long: no near lens, or every
-            // near lens farther than ML_SPAN_FAR lattice units from every ray
+            // near lens farther than a.span_far lattice units from every ray
             // of the warp's walk; elsewhere the per-ray walk
             bool far = true;
             if (nn > 0) {
@@ -801,7 +792,7 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
                         const float4 L = near[q];
                         const float dy = __fsub_rn(L.y, dyl);
                         const float dx = fmaxf(0.f, fmaxf(ulo - L.x, L.x - uhi));
-                        close |= __fmaf_rn(dx, dx, dy * dy) < ML_SPAN_FAR * ML_SPAN_FAR;
+                        close |= __fmaf_rn(dx, dx, dy * dy) < a.span_far * a.span_far;
                     }
                 }
                 far = !__any_sync(0xffffffffu, close);

@@ -51,9 +51,20 @@ def maps_for_rank(ray_counts, rank: int, world: int):
     return sorted(mine)
 
 
-def reduce_counts(counts, group=None):
-    """Sum the ranks' integer count maps in place (torch.distributed
-    all_reduce): exact for integers, so the result is the one-GPU map."""
+def reduce_counts(counts, dst=None, group=None):
+    """Sum the ranks' integer count maps in place: onto rank `dst` only
+    (torch.distributed.reduce; the other ranks' buffers are then undefined),
+    or onto every rank when dst is None (all_reduce).  Integer addition is
+    exact, so the result is the one-GPU map.
+
+    The library's counts are uint32; they travel as int32 because that is the
+    32-bit integer type the collectives reduce.  Two's-complement int32
+    addition wraps modulo 2^32 exactly as uint32 addition does, so the sum's
+    bits are the uint32 sum's; a pixel that wraps is then caught by the map
+    sum check of ml_field_stats, as on one GPU."""
     import torch.distributed as dist
-    dist.all_reduce(counts, op=dist.ReduceOp.SUM, group=group)
+    if dst is None:
+        dist.all_reduce(counts, op=dist.ReduceOp.SUM, group=group)
+    else:
+        dist.reduce(counts, dst=dst, op=dist.ReduceOp.SUM, group=group)
     return counts

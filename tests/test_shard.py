@@ -58,7 +58,7 @@ def _rank_main(rank, world, port, out_path):
     a, b = shard.ray_ranges(g.n3x, g.n3y, g.n1y, world)[rank]
     counts, stats = oracle.shoot_direct(g, w.lenses.x, w.lenses.y, w.lenses.m, a, b, threads=2)
     t = torch.from_numpy(counts.astype(np.int64))
-    shard.reduce_counts(t)
+    shard.reduce_counts(t, dst=0)            # the summed map is needed on rank 0 only
     st = torch.tensor([int(v) for v in stats], dtype=torch.int64)
     dist.all_reduce(st)
     if rank == 0:
@@ -79,6 +79,35 @@ def test_two_gloo_ranks_reproduce_the_one_rank_map(tmp_path):
     n = g.mnx * g.mny
     assert np.array_equal(got[:n].reshape(g.mny, g.mnx), ref.astype(np.int64))
     assert list(got[n:]) == [int(v) for v in stats]
+
+
+def _wrap_main(rank, world, port, out_path):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # uint32 counts near 2^32 travel as their int32 bit patterns
+    u = np.array([4294967000, 7, 2147483647, 2147483648], np.uint32) + np.uint32(rank)
+    t = torch.from_numpy(u.view(np.int32).copy())
+    shard.reduce_counts(t, dst=0)
+    if rank == 0:
+        np.save(out_path, t.numpy().view(np.uint32))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_int32_transport_of_uint32_counts_sums_modulo_2_32(tmp_path):
+    """The counts' int32 bit patterns sum to the uint32 sum's bits, wrapped
+    modulo 2^32 like the one-GPU map would be."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    out = str(tmp_path / "wrap.npy")
+    mp.spawn(_wrap_main, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    a = np.array([4294967000, 7, 2147483647, 2147483648], np.uint64)
+    want = ((a + a + 1) % (1 << 32)).astype(np.uint32)
+    assert np.array_equal(got, want)
 
 
 @pytest.mark.gpu
