@@ -44,8 +44,8 @@ HBM_GBS_FALLBACK = 6790.0
 # slice of the paper-scale lattice at the autotuned grid), valid for the
 # kernel sources whose code (comments and blank space left out, code_hash)
 # has these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = 484.152832e6 / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "e6acd6aa", "ml_internal.cuh": "8235950f", "ml_task.cuh": "3d1d5136"}
+TRAFFIC_BYTES_PER_RAY = (216.120320e6 + 270.870784e6) / 2.0e10
+TRAFFIC_SOURCES = {"ml_shoot.cu": "79c6c9c6", "ml_internal.cuh": "88dbd24c", "ml_task.cuh": "3d1d5136"}
 
 
 # The library's kernels in one field build: k_lens_cells, k_scan, k_scatter,
@@ -119,6 +119,8 @@ def parse():
                          "instead of splitting one set (whole maps balanced by rays)")
     ap.add_argument("--no-independent", action="store_true",
                     help="N > 1: skip the weak-scaling companion record of a sharded run")
+    ap.add_argument("--fp32-peak-only", action="store_true",
+                    help="print the measured FP32 FMA peak (ml_fp32_fma_peak) as JSON and exit")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the batched and differentiable sub-records of the default line")
     ap.add_argument("--no-tune", action="store_true",
@@ -1088,6 +1090,29 @@ def run_reference(args, rank, world):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.fp32_peak_only:
+        import torch
+        torch.cuda.set_device(local)
+        import paper_2308_14278_gb300 as ml
+        ml.load()
+        res = {}
+        for bps in (1, 2, 4, 8):
+            sink = torch.zeros(8 * 1024, dtype=torch.float32, device=f"cuda:{local}")
+            for two in (False, True):
+                best = 0.0
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    st = torch.cuda.current_stream()
+                    e0.record(st)
+                    flop = ml.ml_fp32_fma_peak(two, bps, PEAK_ITERS // 2, sink, st)
+                    e1.record(st)
+                    e1.synchronize()
+                    best = max(best, flop / (e0.elapsed_time(e1) / 1e3) / 1e12)
+                res[f"{bps}_blocks_per_sm_{'two_lane' if two else 'scalar'}_tflops"] = best
+        res["bench_measurement"] = measure_fp32_peak(ml, torch, torch.cuda.current_stream(), local,
+                                                     args.clocks_dir)
+        print(json.dumps(res), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     elif args.workload == "batched":
