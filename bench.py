@@ -422,7 +422,9 @@ def run_ours(args, rank, world, local):
                    "map": f"{w.map_n[0]}x{w.map_n[1]} uint32",
                    "precision": "mixed: near sums, row series and c_1..c_p sums in FP32; node bases, "
                                 "c_0 and the sheet in FP64",
-                   "walk": args.walk, "build_flags": build_flags(),
+                   "walk": args.walk, "certified_spans": bool(info["spans"]),
+                   "span_far_lattice_units": info["span_far"] if info["span_far"] < 1e30 else "inf",
+                   "build_flags": build_flags(),
                    "macro": "fold (Eq. 5)" if getattr(w, "macro", None) else "constant kappa, gamma (Eq. 1)",
                    "taylor_p": p, "far_bound_theta_e": info["far_bound"],
                    "l2_sub": [info["l2_sub_x"], info["l2_sub_y"]], "tuned_grid": bool(info["tuned"]),

@@ -176,9 +176,9 @@ typedef struct {
     /* Certified walk (ML_WALK_CERTIFIED): a warp's level-2 column that has
      * near lenses is walked in certified spans only if every near lens lies
      * farther than span_far lattice spacings (l3x) from its rays, else ray by
-     * ray.  0: the library's choice (3000; with tune, whichever of 3000 and
-     * +inf measured faster; in a batch, +inf).  Any value gives the same
-     * counts. */
+     * ray.  0: the library's choice (3000; with tune, whichever of 3000, +inf
+     * and no certified spans at all measured fastest; in a batch, +inf).  Any
+     * choice gives the same counts. */
     double span_far;
 } ml_field_desc;
 
@@ -207,6 +207,9 @@ typedef struct {
     double far_bound;                       /* truncation bound at taylor_p (theta_E) */
     double mu_per_count;                    /* S_I / S_S of Eq. 12 */
     double span_far;                        /* certified walk's lens-column threshold in use */
+    int32_t spans;                          /* 1 if the counting kernel walks certified spans (the
+                                               autotuner may find the per-ray kernel faster) */
+    int32_t reserved;
 } ml_field_params;
 
 /*

@@ -92,6 +92,7 @@ class FieldParams(C.Structure):
         ("precision", C.c_int32), ("deposit", C.c_int32), ("max_near", C.c_int32),
         ("build", C.c_int32), ("tuned", C.c_int32),
         ("far_bound", C.c_double), ("mu_per_count", C.c_double), ("span_far", C.c_double),
+        ("spans", C.c_int32), ("reserved", C.c_int32),
     ]
 
     def as_dict(self):

@@ -92,6 +92,10 @@ struct ml_field {
     // if they all lie farther than this from its rays (lattice units; +inf:
     // such columns always take the per-ray walk); the autotuner measures both
     float span_far = ML_SPAN_FAR;
+    // certified walk at all: false runs the per-ray kernel (the autotuner
+    // measures it beside the two thresholds; fields with near lenses nearly
+    // everywhere gain nothing from spans)
+    bool use_span = true;
     ml_field_desc desc{};            // parameters (lens pointers cleared)
     std::vector<double> worst;       // truncation bound per Taylor order (worst level-1 cell)
     // device buffers
@@ -388,6 +392,7 @@ struct GridChoice {
     double l1x = 0.0, l1y = 0.0;    // level-1 size; 0 = Eq. 10's
     double cost = 0.0;
     float span_far = ML_SPAN_FAR;   // certified walk's lens-column threshold (see ml_field)
+    bool use_span = true;           // certified walk at all (see ml_field)
 };
 
 // One candidate level-2 grid of a field: its subdivisions, the compiled
@@ -586,7 +591,7 @@ GridChoice best_single(const std::vector<TuneCand> &cands)
 
 ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
                        const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms,
-                       float &span_far);
+                       float &span_far, bool &use_span);
 
 std::unordered_map<uint64_t, GridChoice> g_measured;   // guarded by g_tune_mu
 
@@ -633,9 +638,10 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
         const TuneCand &c = cands[order[i]];
         double est = 0.0;
         float far = ML_SPAN_FAR;
+        bool span = true;
         // a candidate that cannot be built (near lists too long for the
         // mixed kernel's shared memory, memory) is passed over
-        if (measure_grid(d, hx, hy, hm, c, s, est, far) != ML_OK) {
+        if (measure_grid(d, hx, hy, hm, c, s, est, far, span) != ML_OK) {
             cudaGetLastError();
             continue;
         }
@@ -648,6 +654,7 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
             best.sx = c.sx; best.sy = c.sy; best.p = c.P; best.cost = cand_cost(c, c.P);
             best.l1x = c.l1x; best.l1y = c.l1y;
             best.span_far = far;
+            best.use_span = span;
         }
     }
     g_err.clear();
@@ -725,7 +732,10 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
         d->l2_sub_y = gc.sy;
         d->l1_x = gc.l1x;
         d->l1_y = gc.l1y;
-        if (d->span_far == 0.0) f->span_far = gc.span_far;
+        if (d->span_far == 0.0) {
+            f->span_far = gc.span_far;
+            f->use_span = gc.use_span;
+        }
         f->tuned = 1;
     }
     if (d->span_far > 0.0) f->span_far = (float)std::min(d->span_far, 3.0e38);
@@ -887,7 +897,7 @@ ml_status create_impl(const ml_field_desc *d, cudaStream_t s, ml_field *f)
 // descriptor being built has handed its own pointers over already).
 ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, const std::vector<double> &hy,
                        const std::vector<double> &hm, const TuneCand &c, cudaStream_t s, double &est_ms,
-                       float &span_far)
+                       float &span_far, bool &use_span)
 {
     ml_field_desc dc = d;
     dc.lens_x = hx.data();
@@ -920,12 +930,16 @@ ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, co
         const uint64_t r0 = (total - 2 * n) / 2;
         const uint64_t warm = std::min<uint64_t>(n, 64ull * (uint64_t)g.n3x);
         // the certified walk is timed with lens columns spanned beyond
-        // ML_SPAN_FAR and with them always walked ray by ray; the faster counts
+        // ML_SPAN_FAR, with them always walked ray by ray, and without spans
+        // (the per-ray kernel); the fastest counts
         const bool certified = f->desc.walk == ML_WALK_CERTIFIED && f->g.deposit == ML_DEPOSIT_NGP;
-        const float fars[2] = {ML_SPAN_FAR, 3.0e38f};
+        const float fars[3] = {ML_SPAN_FAR, 3.0e38f, 3.0e38f};
+        static const char *const names[3] = {" (lens columns spanned)", " (lens columns per ray)",
+                                             " (no spans)"};
         double best_ray = -1.0;
-        for (int v = 0; v < (certified ? 2 : 1) && st == ML_OK; ++v) {
+        for (int v = 0; v < (certified ? 3 : 1) && st == ML_OK; ++v) {
             f->span_far = fars[v];
+            f->use_span = v < 2;
             float ms[2] = {0.f, 0.f};
             st = ml_shoot_rays(f, r0, r0 + warm, s);
             for (int q = 0; q < 2 && st == ML_OK && n > 0; ++q) {
@@ -940,11 +954,12 @@ ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, co
             if (st == ML_OK && (best_ray < 0.0 || per_ray < best_ray)) {
                 best_ray = per_ray;
                 span_far = fars[v];
+                use_span = v < 2;
             }
             if (st == ML_OK && getenv("ML_TUNE_LOG"))
                 fprintf(stderr, "ml tune:   create %.2f ms, %.3g and %.3g of %.3g rays in %.3f and %.3f ms%s\n",
                         create_ms, (double)n, (double)(2 * n), (double)total, ms[0], ms[1],
-                        certified ? (v ? " (lens columns per ray)" : " (lens columns spanned)") : "");
+                        certified ? names[v] : "");
         }
         if (st == ML_OK) est_ms = create_ms + best_ray * (double)total;
     }
@@ -971,7 +986,7 @@ ShootArgs make_args(const ml_field *f)
     a.abort_flag = f->d_abort;
     const Geo &g = f->g;
     a.near_cap = std::max(1, f->max_near);
-    a.walk = f->desc.walk;
+    a.walk = f->desc.walk == ML_WALK_CERTIFIED && f->use_span ? ML_WALK_CERTIFIED : ML_WALK_PER_RAY;
     a.span_far = f->span_far;
     a.l3x_f = (float)g.l3x;
     a.l3x_lo = (float)(g.l3x - (double)a.l3x_f);
@@ -1849,6 +1864,7 @@ ml_status ml_field_info(const ml_field *f, ml_field_params *out)
     out->far_bound = f->far_bound;
     out->mu_per_count = (g.l3x * g.l3y) / (g.dpx * g.dpy);
     out->span_far = f->span_far;
+    out->spans = f->desc.walk == ML_WALK_CERTIFIED && f->use_span ? 1 : 0;
     return ML_OK;
 }
 

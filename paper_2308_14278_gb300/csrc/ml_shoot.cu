@@ -504,7 +504,12 @@ __device__ void flush_spans(const ShootArgs &a, const SpanCount &sc)
 //    (Y: 6 m_q |dyy_q| / rho_q^4);
 //  - so X lies in [min(X_a, X_b) - 2E - K, max(X_a, X_b) + 2E + K] (margin
 //    widened by 1 %, ends rounded outwards); if that interval has one floor,
-//    and the same holds for Y, every ray between shares the anchor's pixel.
+//    and the same holds for Y, every ray between shares the anchor's pixel;
+//  - when |X_b - X_a| - 2E > (b - a)^2 max|F''| (= 8K), F' has one sign on
+//    the span (it is within (b - a) max|F''| of the chord's slope, by the
+//    mean value theorem), so F is monotone, lies between F(a) and F(b), and
+//    the interval needs no K: near a pixel edge, spans several times longer
+//    pass.
 // A span whose rays could come within the close-pass radius of a lens is never
 // certified (those rays would take the hi/lo arithmetic), and anchors outside
 // |X|, |Y| < 2^21 (rays dropped on a lens) are never certified from.
@@ -648,8 +653,16 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
         }
         const float w = __fsub_rn(ub, ua);
         const float kk = 0.125f * w * w;
-        const float MX = 1.01f * fmaf(kk, cX, c2e * (SX + tX));
-        const float MY = 1.01f * fmaf(kk, cY, c2e * (SY + tY));
+        // 2E and K of each component; where the chord's rise exceeds what the
+        // curvature can undo over the span, |F(b) - F(a)| - 2E > (b - a)^2
+        // max|F''| = 8K, F' keeps one sign (mean value theorem), F lies
+        // between F(a) and F(b), and K is not needed
+        const float eX = c2e * (SX + tX), eY = c2e * (SY + tY);
+        const float kX = kk * cX, kY = kk * cY;
+        const bool monoX = __fsub_rd(__fmul_rd(fabsf(__fsub_rn(Xb, Xa)), 0.9999998f), eX) > 8.1f * kX;
+        const bool monoY = __fsub_rd(__fmul_rd(fabsf(__fsub_rn(Yb, Ya)), 0.9999998f), eY) > 8.1f * kY;
+        const float MX = 1.01f * (monoX ? eX : eX + kX);
+        const float MY = 1.01f * (monoY ? eY : eY + kY);
         const bool okx = floor_to_int(__fsub_rd(fminf(Xa, Xb), MX)) == floor_to_int(__fadd_ru(fmaxf(Xa, Xb), MX));
         const bool oky = floor_to_int(__fsub_rd(fminf(Ya, Yb), MY)) == floor_to_int(__fadd_ru(fmaxf(Ya, Yb), MY));
         return clear && okx && oky;
@@ -744,7 +757,9 @@ __device__ __forceinline__ float pin(float v)
 // One warp task of the mixed kernel (NGP deposit): stage the near list, then
 // walk each level-2 column of the task.  Shared by the single-map and the
 // batched persistent kernels.
-template <int P, bool SPAN>
+// SPAN: 0 the per-ray walk only; 1 the certified walk in one copy for every
+// near-list length; 2 the same with a second copy for empty near lists.
+template <int P, int SPAN>
 __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4 *near, float2 *nlo,
                                            int lane, float dyl, float dyl_lo, RunState &rs,
                                            unsigned &drop, unsigned long long &pairs,
@@ -798,7 +813,12 @@ __device__ __forceinline__ void shoot_task(const ShootArgs &a, int64_t t, float4
                 far = !__any_sync(0xffffffffu, close);
             }
             if (far) {
-                if (nn == 0)
+                // one copy of the walk for every near-list length (its lens loops
+                // run from shared memory) in the single-map kernel, where a second
+                // copy for empty lists measured slower, its code competing for the
+                // instruction cache; the batch kernel, whose lens-dense maps walk
+                // most lens columns ray by ray, measured faster with it
+                if (SPAN == 2 && nn == 0)
                     walk_span<P, 0>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc);
                 else
                     walk_span<P, NN_DYN>(rp, a, nl, nn, k0, k1, dyl, dyl_lo, rs, drop, sc);
@@ -874,7 +894,7 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_mix
         bool stop;
         const int64_t t = fetch_task(a, lane, stop);
         if (stop || t >= a.n_tasks) break;
-        shoot_task<P, SPAN>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks, sc);
+        shoot_task<P, SPAN ? 1 : 0>(a, t, near, nlo, lane, dyl, dyl_lo, rs, drop, pairs, tasks, sc);
     }
     run_flush(rs, a.map_u32, a.g.mnx, a.g.mny);
     // dropped rays were sent far outside the map and counted as out above
@@ -934,8 +954,8 @@ __global__ void __launch_bounds__(WARPS_PER_CTA * 32, ML_MIN_BLOCKS) k_shoot_bat
             cur = lo;
             lane_dy(b.args[cur].l3yx, lane, dyl, dyl_lo);
         }
-        shoot_task<P, SPAN>(b.args[cur], t - b.task_base[cur], near, nlo, lane, dyl, dyl_lo, rs, drop,
-                            pairs, tasks, sc);
+        shoot_task<P, SPAN ? 2 : 0>(b.args[cur], t - b.task_base[cur], near, nlo, lane, dyl, dyl_lo, rs,
+                                    drop, pairs, tasks, sc);
     }
     if (cur >= 0) {
         const ShootArgs &ac = b.args[cur];
