@@ -694,11 +694,30 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
             const bool dr = eval(kb + w, w == 0 ? act : ok, X, Y, rx, ry);
             if (w == 0) {
                 if (span) {
-                    ok = rx == rcx && ry == rcy && certify(ka, kb, Xa, Ya, X, Y);
+                    const bool same = rx == rcx && ry == rcy;
+                    ok = same && certify(ka, kb, Xa, Ya, X, Y);
                     sc.spans += ok ? 1ull : 0ull;
                     if (!ok) {
                         ++sc.evals;
-                        gap = max(1, (kb - ka) >> 1);
+                        // ray kb is past a pixel edge: the next window starts
+                        // where the chord from ka crosses it; otherwise the
+                        // bound failed, and the gap halves
+                        int g2 = (kb - ka) >> 1;
+                        if (!same && fabsf(Xa) < LIM && fabsf(X) < LIM && fabsf(Ya) < LIM && fabsf(Y) < LIM) {
+                            float t = 1.f;
+                            const float fa = __fsub_rn(__int_as_float((int)rcx), 12582912.0f);
+                            const float ga = __fsub_rn(__int_as_float((int)rcy), 12582912.0f);
+                            if (rx != rcx) {
+                                const float e = X > Xa ? __fadd_rn(fa, 1.f) : fa;
+                                t = fminf(t, __fsub_rn(e, Xa) * rcp_approx(__fsub_rn(X, Xa)));
+                            }
+                            if (ry != rcy) {
+                                const float e = Y > Ya ? __fadd_rn(ga, 1.f) : ga;
+                                t = fminf(t, __fsub_rn(e, Ya) * rcp_approx(__fsub_rn(Y, Ya)));
+                            }
+                            g2 = floor_to_int(fmaxf(t, 0.f) * (float)(kb - ka)) - ML_SPAN_OFF;
+                        }
+                        gap = max(1, min(g2, kb - ka - 1));
                     }
                 }
                 if (ka < k0) {
