@@ -563,7 +563,8 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
         for (int m = P - 1; m >= 0; --m) v = fma2(v, U, C[m]);
         unpack2(v, X, Y);
         bool dropped = false;
-        if constexpr (!(REG && NN == 0)) {
+        // (nlen is warp-uniform: an empty near list skips the lens loop and its vote)
+        if (!(REG && NN == 0) && nlen > 0) {
             float mn = 3.0e38f;
             auto lens = [&](int q) {
                 float x, m, d2, dd;
@@ -630,7 +631,7 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
         const float ua = __fadd_rn((float)ka, a.c0_f), ub = __fadd_rn((float)kb, a.c0_f);
         float tX = 0.f, tY = 0.f, cX = QX, cY = QY;
         bool clear = true;
-        if constexpr (!(REG && NN == 0)) {
+        if (!(REG && NN == 0) && nlen > 0) {
             auto lens = [&](int q) {
                 float x, m, d2, dd;
                 rec(q, x, m, d2, dd);
@@ -675,6 +676,7 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
     int ka = k0 - 1;              // last evaluated ray (none yet)
     float Xa = 0.f, Ya = 0.f;
     int gap = 1;                  // next window at ka + gap
+    unsigned ev = 0, spn = 0;     // this column's evaluations and certified spans
     for (;;) {
         const bool act = on && ka + 1 < k1;
         if (!__any_sync(0xffffffffu, act)) break;
@@ -696,9 +698,9 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
                 if (span) {
                     const bool same = rx == rcx && ry == rcy;
                     ok = same && certify(ka, kb, Xa, Ya, X, Y);
-                    sc.spans += ok ? 1ull : 0ull;
+                    spn += ok ? 1u : 0u;
                     if (!ok) {
-                        ++sc.evals;
+                        ++ev;
                         // ray kb is past a pixel edge: the next window starts
                         // where the chord from ka crosses it; otherwise the
                         // bound failed, and the gap halves
@@ -728,7 +730,7 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
                 if (!__any_sync(0xffffffffu, ok)) break;
             }
             if (ok && kb + w < k1) {
-                ++sc.evals;
+                ++ev;
                 if (dr) ++drop;
                 if (rx != rcx || ry != rcy) {
                     flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(kb + w - kst),
@@ -762,6 +764,8 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
     if (on) rs.cnt += (unsigned)(k1 - kst);
     rs.cx = (int)(rcx + offx);
     rs.cy = (int)(rcy + offy);
+    sc.evals += ev;
+    sc.spans += spn;
 }
 
 // Keeps a value in a register: the compiler may not recompute it (it would
