@@ -929,17 +929,23 @@ ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, co
         const uint64_t n = std::min<uint64_t>(total / 2, std::max<uint64_t>(500000000ull, total / 100));
         const uint64_t r0 = (total - 2 * n) / 2;
         const uint64_t warm = std::min<uint64_t>(n, 64ull * (uint64_t)g.n3x);
-        // the certified walk is timed with lens columns spanned beyond
-        // ML_SPAN_FAR, with them always walked ray by ray, and without spans
-        // (the per-ray kernel); the fastest counts
+        // the certified walk is timed with lens columns spanned beyond three
+        // distances (lattice spacings: where spanning pays depends on the
+        // lenses' pull in pixels per spacing, which differs between fields),
+        // with them always walked ray by ray, and without spans (the per-ray
+        // kernel); the fastest counts
         const bool certified = f->desc.walk == ML_WALK_CERTIFIED && f->g.deposit == ML_DEPOSIT_NGP;
-        const float fars[3] = {ML_SPAN_FAR, 3.0e38f, 3.0e38f};
-        static const char *const names[3] = {" (lens columns spanned)", " (lens columns per ray)",
-                                             " (no spans)"};
+        constexpr int NV = 6;
+        const float fars[NV] = {ML_SPAN_FAR, 1000.f, 300.f, 100.f, 3.0e38f, 3.0e38f};
+        static const char *const names[NV] = {" (lens columns spanned beyond 3000)",
+                                              " (lens columns spanned beyond 1000)",
+                                              " (lens columns spanned beyond 300)",
+                                              " (lens columns spanned beyond 100)",
+                                              " (lens columns per ray)", " (no spans)"};
         double best_ray = -1.0;
-        for (int v = 0; v < (certified ? 3 : 1) && st == ML_OK; ++v) {
+        for (int v = 0; v < (certified ? NV : 1) && st == ML_OK; ++v) {
             f->span_far = fars[v];
-            f->use_span = v < 2;
+            f->use_span = v < NV - 1;
             float ms[2] = {0.f, 0.f};
             st = ml_shoot_rays(f, r0, r0 + warm, s);
             for (int q = 0; q < 2 && st == ML_OK && n > 0; ++q) {
@@ -954,7 +960,7 @@ ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, co
             if (st == ML_OK && (best_ray < 0.0 || per_ray < best_ray)) {
                 best_ray = per_ray;
                 span_far = fars[v];
-                use_span = v < 2;
+                use_span = v < NV - 1;
             }
             if (st == ML_OK && getenv("ML_TUNE_LOG"))
                 fprintf(stderr, "ml tune:   create %.2f ms, %.3g and %.3g of %.3g rays in %.3f and %.3f ms%s\n",

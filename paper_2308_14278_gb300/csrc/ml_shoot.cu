@@ -500,8 +500,11 @@ __device__ void flush_spans(const ShootArgs &a, const SpanCount &sc)
 //    least twice the count of roundings on the path (Horner FMAs, per lens
 //    the offset, r^2, reciprocal, mass product and accumulation);
 //  - shape: F lies within K = (b - a)^2 / 8 max|F''| of the chord between
-//    F(a) and F(b), with |F''| <= sum m(m-1) |C_m| U^(m-2) + sum_q 6 m_q / rho_q^3
-//    (Y: 6 m_q |dyy_q| / rho_q^4);
+//    F(a) and F(b), with |F''| <= sum m(m-1) |C_m| U^(m-2) + sum_q 2 m_q / rho_q^3
+//    (Y: 6 m_q |dyy_q| / rho_q^4): with r^2 = x^2 + dy2 and c = x / r, a
+//    lens's term m x / r^2 has second derivative (2 m / r^3) c (4 c^2 - 3),
+//    and |4 c^3 - 3 c| <= 1 on [-1, 1] (the Chebyshev polynomial T_3); its y
+//    term m dyy / r^2 has (m dyy / r^4) (8 c^2 - 2), at most 6 in size;
 //  - so X lies in [min(X_a, X_b) - 2E - K, max(X_a, X_b) + 2E + K] (margin
 //    widened by 1 %, ends rounded outwards); if that interval has one floor,
 //    and the same holds for Y, every ray between shares the anchor's pixel;
@@ -642,7 +645,7 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
                 const float mr = m * ir, md = m * fabsf(dd);
                 tX += mr;
                 tY = fmaf(md, ir2, tY);
-                cX = fmaf(6.f * mr, ir2, cX);
+                cX = fmaf(2.f * mr, ir2, cX);
                 cY = fmaf(6.f * md, ir2 * ir2, cY);
             };
             if constexpr (REG) {
