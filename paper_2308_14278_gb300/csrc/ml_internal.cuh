@@ -23,8 +23,8 @@ constexpr int WARPS_PER_CTA = 8;
 #ifndef ML_SPAN_W
 #define ML_SPAN_W 2
 #endif
-#ifndef ML_SPAN_OFF
-#define ML_SPAN_OFF 1
+#ifndef ML_SPAN_MARGIN
+#define ML_SPAN_MARGIN 1.0f
 #endif
 #ifndef ML_SPAN_FAR
 #define ML_SPAN_FAR 3000.0f

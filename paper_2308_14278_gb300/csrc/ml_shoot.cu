@@ -484,11 +484,14 @@ __device__ void flush_spans(const ShootArgs &a, const SpanCount &sc)
 // ka.  When kb > ka + 1 the rays strictly between them are not evaluated:
 // they join the current run only if ray kb lands in the run's pixel and a
 // bound proves that every ray between lands there too; otherwise the lane
-// evaluates nothing more in this step and retries with half the gap.  Every
-// ray therefore gets the pixel the per-ray walk gives it, and the counts are
-// bit-identical.  The gap is chosen so that the window starts two rays short
-// of where the lane's (X, Y) slope says the next pixel edge lies, so that one
-// step usually crosses it.
+// takes nothing from this step and retries with a shorter gap.  Every ray
+// therefore gets the pixel the per-ray walk gives it, and the counts are
+// bit-identical.  The gap is chosen so that the window starts ML_SPAN_MARGIN
+// rays short of where the lane's (X, Y) slope says the next pixel edge lies,
+// so that one step usually crosses it.  The window's rays are evaluated
+// together, in straight-line code: their Horner chains are independent and
+// interleave, the near list is read once for all of them, and one warp vote
+// serves the window's close-pass test.
 //
 // The bound.  Along the row the walk's value X(u) (and Y(u)) is the FP32
 // evaluation of F(u) = P(u) + sum_q (lx_q - u) m_q / ((lx_q - u)^2 + dy2_q)
@@ -554,30 +557,48 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
     const f32x2 MAGIC = pack2(12582912.0f, 12582912.0f);
     constexpr float LIM = 2097152.0f;           // 2^21
 
-    // source position of ray k by the per-ray arithmetic, in raw floor form;
-    // returns true for a ray on a lens (sent far outside the map, as
+    // source positions of rays kb .. kb+W-1 by the per-ray arithmetic, in raw
+    // floor form; dr[r] marks a ray on a lens (sent far outside the map, as
     // walk_fixed does).  Called by all lanes together (the close-pass branch
-    // is taken by warp vote).
-    auto eval = [&](int k, bool act, float &X, float &Y, unsigned &rx, unsigned &ry) {
-        const float u = __fadd_rn((float)k, a.c0_f);
-        const f32x2 U = pack2(u, u);
-        f32x2 v = C[P];
+    // is taken by warp vote); av[r] says which rays the lane will use.
+    float X[W], Y[W];
+    unsigned rx[W], ry[W];
+    bool dr[W];
+    auto eval_window = [&](int kb, const bool (&av)[W]) {
+        float u[W];
+        f32x2 v[W];
 #pragma unroll
-        for (int m = P - 1; m >= 0; --m) v = fma2(v, U, C[m]);
-        unpack2(v, X, Y);
-        bool dropped = false;
+        for (int r = 0; r < W; ++r) {
+            u[r] = __fadd_rn((float)(kb + r), a.c0_f);
+            v[r] = C[P];
+        }
+#pragma unroll
+        for (int m = P - 1; m >= 0; --m) {
+#pragma unroll
+            for (int r = 0; r < W; ++r) v[r] = fma2(v[r], pack2(u[r], u[r]), C[m]);
+        }
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+            unpack2(v[r], X[r], Y[r]);
+            dr[r] = false;
+        }
         // (nlen is warp-uniform: an empty near list skips the lens loop and its vote)
         if (!(REG && NN == 0) && nlen > 0) {
-            float mn = 3.0e38f;
+            float mn[W];
+#pragma unroll
+            for (int r = 0; r < W; ++r) mn[r] = 3.0e38f;
             auto lens = [&](int q) {
                 float x, m, d2, dd;
                 rec(q, x, m, d2, dd);
-                const float dx = __fsub_rn(x, u);
-                const float r2 = __fmaf_rn(dx, dx, d2);
-                mn = fminf(mn, r2);
-                const float sv = __fmul_rn(m, rcp_approx(r2));
-                X = __fmaf_rn(dx, sv, X);
-                Y = __fmaf_rn(dd, sv, Y);
+#pragma unroll
+                for (int r = 0; r < W; ++r) {
+                    const float dx = __fsub_rn(x, u[r]);
+                    const float r2 = __fmaf_rn(dx, dx, d2);
+                    mn[r] = fminf(mn[r], r2);
+                    const float sv = __fmul_rn(m, rcp_approx(r2));
+                    X[r] = __fmaf_rn(dx, sv, X[r]);
+                    Y[r] = __fmaf_rn(dd, sv, Y[r]);
+                }
             };
             if constexpr (REG) {
 #pragma unroll
@@ -585,22 +606,43 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
             } else {
                 for (int q = 0; q < nlen; ++q) lens(q);
             }
-            const bool close = act && mn < a.rc2u;
-            if (__any_sync(0xffffffffu, close)) {
-                if (close) {
-                    unpack2(v, X, Y);
-                    if (!near_sum_hilo_lat(nl, nlen, u, dyl, dyl_lo, a.yx_f, X, Y)) {
-                        X = -1.0e30f;
-                        dropped = true;
+            bool cl[W], any = false;
+#pragma unroll
+            for (int r = 0; r < W; ++r) {
+                cl[r] = av[r] && mn[r] < a.rc2u;
+                any |= cl[r];
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                // rare: one copy of the hi/lo path, the window rotated through slot 0
+#pragma unroll 1
+                for (int i = 0; i < W; ++i) {
+                    if (cl[0]) {
+                        unpack2(v[0], X[0], Y[0]);
+                        if (!near_sum_hilo_lat(nl, nlen, u[0], dyl, dyl_lo, a.yx_f, X[0], Y[0])) {
+                            X[0] = -1.0e30f;
+                            dr[0] = true;
+                        }
                     }
+                    const float u0 = u[0], X0 = X[0], Y0 = Y[0];
+                    const f32x2 v0 = v[0];
+                    const bool c0 = cl[0], d0 = dr[0];
+#pragma unroll
+                    for (int r = 0; r + 1 < W; ++r) {
+                        u[r] = u[r + 1]; X[r] = X[r + 1]; Y[r] = Y[r + 1];
+                        v[r] = v[r + 1]; cl[r] = cl[r + 1]; dr[r] = dr[r + 1];
+                    }
+                    u[W - 1] = u0; X[W - 1] = X0; Y[W - 1] = Y0;
+                    v[W - 1] = v0; cl[W - 1] = c0; dr[W - 1] = d0;
                 }
             }
         }
-        float fx, fy;
-        unpack2(add2_rd(pack2(X, Y), MAGIC), fx, fy);
-        rx = (unsigned)__float_as_int(fx);
-        ry = (unsigned)__float_as_int(fy);
-        return dropped;
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+            float fx, fy;
+            unpack2(add2_rd(pack2(X[r], Y[r]), MAGIC), fx, fy);
+            rx[r] = (unsigned)__float_as_int(fx);
+            ry[r] = (unsigned)__float_as_int(fy);
+        }
     };
 
     // bounds of the row polynomial over the lane's range: S = sum |C_m| U^m,
@@ -685,72 +727,63 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
         if (!__any_sync(0xffffffffu, act)) break;
         const int kb = act ? min(ka + gap, k1 - 1) : ka + 1;
         const bool span = act && kb > ka + 1;
-        // slope baseline: the last evaluated ray, or at the column's start
-        // the window's first ray
-        int kp = ka;
-        float Xp = Xa, Yp = Ya;
+        bool av[W];
+#pragma unroll
+        for (int r = 0; r < W; ++r) av[r] = act && kb + r < k1;
+        eval_window(kb, av);
         bool ok = act;
-        // the window: ray kb (which must first certify the span before it),
-        // then the next W - 1 rays; one copy of the evaluation
-#pragma unroll 1
-        for (int w = 0; w < W; ++w) {
-            float X, Y;
-            unsigned rx, ry;
-            const bool dr = eval(kb + w, w == 0 ? act : ok, X, Y, rx, ry);
-            if (w == 0) {
-                if (span) {
-                    const bool same = rx == rcx && ry == rcy;
-                    ok = same && certify(ka, kb, Xa, Ya, X, Y);
-                    spn += ok ? 1u : 0u;
-                    if (!ok) {
-                        ++ev;
-                        // ray kb is past a pixel edge: the next window starts
-                        // where the chord from ka crosses it; otherwise the
-                        // bound failed, and the gap halves
-                        int g2 = (kb - ka) >> 1;
-                        if (!same && fabsf(Xa) < LIM && fabsf(X) < LIM && fabsf(Ya) < LIM && fabsf(Y) < LIM) {
-                            float t = 1.f;
-                            const float fa = __fsub_rn(__int_as_float((int)rcx), 12582912.0f);
-                            const float ga = __fsub_rn(__int_as_float((int)rcy), 12582912.0f);
-                            if (rx != rcx) {
-                                const float e = X > Xa ? __fadd_rn(fa, 1.f) : fa;
-                                t = fminf(t, __fsub_rn(e, Xa) * rcp_approx(__fsub_rn(X, Xa)));
-                            }
-                            if (ry != rcy) {
-                                const float e = Y > Ya ? __fadd_rn(ga, 1.f) : ga;
-                                t = fminf(t, __fsub_rn(e, Ya) * rcp_approx(__fsub_rn(Y, Ya)));
-                            }
-                            g2 = floor_to_int(fmaxf(t, 0.f) * (float)(kb - ka)) - ML_SPAN_OFF;
-                        }
-                        gap = max(1, min(g2, kb - ka - 1));
-                    }
-                }
-                if (ka < k0) {
-                    kp = kb;
-                    Xp = X;
-                    Yp = Y;
-                }
-                if (!__any_sync(0xffffffffu, ok)) break;
-            }
-            if (ok && kb + w < k1) {
+        if (span) {
+            const bool same = rx[0] == rcx && ry[0] == rcy;
+            ok = same && certify(ka, kb, Xa, Ya, X[0], Y[0]);
+            spn += ok ? 1u : 0u;
+            if (!ok) {
                 ++ev;
-                if (dr) ++drop;
-                if (rx != rcx || ry != rcy) {
-                    flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(kb + w - kst),
-                              a.map_u32, g.mnx, g.mny);
-                    rs.cnt = 0;
-                    kst = kb + w;
-                    rcx = rx;
-                    rcy = ry;
+                // ray kb is past a pixel edge: the next window starts where the
+                // chord from ka crosses it; otherwise the bound failed, and the
+                // gap halves
+                int g2 = (kb - ka) >> 1;
+                if (!same && fabsf(Xa) < LIM && fabsf(X[0]) < LIM && fabsf(Ya) < LIM && fabsf(Y[0]) < LIM) {
+                    float t = 1.f;
+                    const float fa = __fsub_rn(__int_as_float((int)rcx), 12582912.0f);
+                    const float ga = __fsub_rn(__int_as_float((int)rcy), 12582912.0f);
+                    if (rx[0] != rcx) {
+                        const float e = X[0] > Xa ? __fadd_rn(fa, 1.f) : fa;
+                        t = fminf(t, __fsub_rn(e, Xa) * rcp_approx(__fsub_rn(X[0], Xa)));
+                    }
+                    if (ry[0] != rcy) {
+                        const float e = Y[0] > Ya ? __fadd_rn(ga, 1.f) : ga;
+                        t = fminf(t, __fsub_rn(e, Ya) * rcp_approx(__fsub_rn(Y[0], Ya)));
+                    }
+                    g2 = floor_to_int(fmaxf(t, 0.f) * (float)(kb - ka) - ML_SPAN_MARGIN);
                 }
-                ka = kb + w;
-                Xa = X;
-                Ya = Y;
+                gap = max(1, min(g2, kb - ka - 1));
             }
         }
         if (ok) {
+            // slope baseline: the last evaluated ray, or at the column's start
+            // the window's first ray
+            const int kp = ka < k0 ? kb : ka;
+            const float Xp = ka < k0 ? X[0] : Xa, Yp = ka < k0 ? Y[0] : Ya;
+#pragma unroll
+            for (int r = 0; r < W; ++r) {
+                if (av[r]) {
+                    ++ev;
+                    if (dr[r]) ++drop;
+                    if (rx[r] != rcx || ry[r] != rcy) {
+                        flush_run(rs, (int)(rcx + offx), (int)(rcy + offy), rs.cnt + (unsigned)(kb + r - kst),
+                                  a.map_u32, g.mnx, g.mny);
+                        rs.cnt = 0;
+                        kst = kb + r;
+                        rcx = rx[r];
+                        rcy = ry[r];
+                    }
+                    ka = kb + r;
+                    Xa = X[r];
+                    Ya = Y[r];
+                }
+            }
             // rays to the next pixel edge along the slope since the baseline;
-            // the next window starts two rays before it
+            // the next window starts ML_SPAN_MARGIN rays before it
             gap = 1;
             if (ka > kp && fabsf(Xa) < LIM && fabsf(Ya) < LIM && fabsf(Xp) < LIM && fabsf(Yp) < LIM) {
                 const float inv = rcp_approx((float)(ka - kp));
@@ -760,7 +793,7 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
                 const float gX = sX > 0.f ? __fsub_rn(1.f, fX) : fX;
                 const float gY = sY > 0.f ? __fsub_rn(1.f, fY) : fY;
                 const float n = fminf(fminf(gX * rcp_approx(fabsf(sX)), gY * rcp_approx(fabsf(sY))), 1048576.f);
-                gap = max(1, floor_to_int(n) - ML_SPAN_OFF);
+                gap = max(1, floor_to_int(n - ML_SPAN_MARGIN));
             }
         }
     }
