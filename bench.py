@@ -44,8 +44,8 @@ HBM_GBS_FALLBACK = 6790.0
 # slice of the paper-scale lattice at the autotuned grid), valid for the
 # kernel sources whose code (comments and blank space left out, code_hash)
 # has these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = (216.565504e6 + 273.323776e6) / 2.0e10
-TRAFFIC_SOURCES = {"ml_shoot.cu": "e3a4f223", "ml_internal.cuh": "4806c1e0", "ml_task.cuh": "3d1d5136"}
+TRAFFIC_BYTES_PER_RAY = (216.086016e6 + 272.358144e6) / 2.0e10
+TRAFFIC_SOURCES = {"ml_shoot.cu": "48c686ae", "ml_internal.cuh": "4806c1e0", "ml_task.cuh": "3d1d5136"}
 
 
 # The library's kernels in one field build: k_lens_cells, k_scan, k_scatter,

@@ -260,65 +260,95 @@ __device__ __forceinline__ float gap_hilo(float ph, float pl, float ah, float al
 // rounded down by 1e-6 relative (its FP32 error is below 4e-7), rho up by
 // 1e-6, and the sum up by 1e-5 (rounding of the powers and the sums).  The
 // near lenses are the cell's 3 x 3 block: three runs of extended cell ids.
-__global__ void k_p_bound(Geo g, LensTable L, double *__restrict__ bound)
+// PB_CELLS consecutive level-1 cells per block: each lens record is read once
+// for all of them (one lens table pass per block).
+#ifndef ML_PB_CELLS
+#define ML_PB_CELLS 2
+#endif
+#ifndef ML_PB_THREADS
+#define ML_PB_THREADS 128
+#endif
+constexpr int PB_CELLS = ML_PB_CELLS;
+
+__global__ void __launch_bounds__(ML_PB_THREADS) k_p_bound(Geo g, LensTable L, double *__restrict__ bound)
 {
-    int64_t c = blockIdx.x;
-    int64_t c1x = c % g.N1x, c1y = c / g.N1x;
-    int64_t a2x = c1x * g.l2sx, b2x = min((c1x + 1) * (int64_t)g.l2sx, g.N2x) - 1;
-    int64_t a2y = c1y * g.l2sy, b2y = min((c1y + 1) * (int64_t)g.l2sy, g.N2y) - 1;
-    double x0 = g.rx0 + (a2x + 0.5) * g.l2x, x1 = g.rx0 + (b2x + 0.5) * g.l2x;
-    double y0 = g.ry0 + (a2y + 0.5) * g.l2y, y1 = g.ry0 + (b2y + 0.5) * g.l2y;
-    double hx = 0.5 * (double)(g.n2x - 1) * g.l3x, hy = 0.5 * (double)(g.n2y - 1) * g.l3y;
+    const int64_t ncell = g.N1x * g.N1y;
+    const int64_t cbase = (int64_t)blockIdx.x * PB_CELLS;
+    const double hx = 0.5 * (double)(g.n2x - 1) * g.l3x, hy = 0.5 * (double)(g.n2y - 1) * g.l3y;
     const float rho = (float)(sqrt(hx * hx + hy * hy) * (1.0 + 1e-6));
-    float x0h, x0l, x1h, x1l, y0h, y0l, y1h, y1l;
-    x0h = (float)x0; x0l = (float)(x0 - (double)x0h);
-    x1h = (float)x1; x1l = (float)(x1 - (double)x1h);
-    y0h = (float)y0; y0l = (float)(y0 - (double)y0h);
-    y1h = (float)y1; y1l = (float)(y1 - (double)y1h);
-    // extended ids of the near block: rows c1y..c1y+2, columns c1x..c1x+2
-    const int32_t n0 = (int32_t)(c1y * g.NEx + c1x), nstep = (int32_t)g.NEx;
-    float acc[PMAX];
+    float x0h[PB_CELLS], x0l[PB_CELLS], x1h[PB_CELLS], x1l[PB_CELLS];
+    float y0h[PB_CELLS], y0l[PB_CELLS], y1h[PB_CELLS], y1l[PB_CELLS];
+    int32_t n0[PB_CELLS];
+    const int32_t nstep = (int32_t)g.NEx;
 #pragma unroll
-    for (int q = 0; q < PMAX; ++q) acc[q] = 0.f;
+    for (int i = 0; i < PB_CELLS; ++i) {
+        const int64_t c = min(cbase + i, ncell - 1);
+        const int64_t c1x = c % g.N1x, c1y = c / g.N1x;
+        const int64_t a2x = c1x * g.l2sx, b2x = min((c1x + 1) * (int64_t)g.l2sx, g.N2x) - 1;
+        const int64_t a2y = c1y * g.l2sy, b2y = min((c1y + 1) * (int64_t)g.l2sy, g.N2y) - 1;
+        const double x0 = g.rx0 + (a2x + 0.5) * g.l2x, x1 = g.rx0 + (b2x + 0.5) * g.l2x;
+        const double y0 = g.ry0 + (a2y + 0.5) * g.l2y, y1 = g.ry0 + (b2y + 0.5) * g.l2y;
+        x0h[i] = (float)x0; x0l[i] = (float)(x0 - (double)x0h[i]);
+        x1h[i] = (float)x1; x1l[i] = (float)(x1 - (double)x1h[i]);
+        y0h[i] = (float)y0; y0l[i] = (float)(y0 - (double)y0h[i]);
+        y1h[i] = (float)y1; y1l[i] = (float)(y1 - (double)y1h[i]);
+        // extended ids of the near block: rows c1y..c1y+2, columns c1x..c1x+2
+        n0[i] = (int32_t)(c1y * g.NEx + c1x);
+    }
+    float acc[PB_CELLS][PMAX];
+#pragma unroll
+    for (int i = 0; i < PB_CELLS; ++i)
+#pragma unroll
+        for (int q = 0; q < PMAX; ++q) acc[i][q] = 0.f;
     for (int64_t k = threadIdx.x; k < L.n; k += blockDim.x) {
-        const int32_t lc = L.cell[k] - n0;
-        if ((unsigned)lc < 3u || (unsigned)(lc - nstep) < 3u || (unsigned)(lc - 2 * nstep) < 3u) continue;
-        const float dx = gap_hilo(L.xh[k], L.xl[k], x0h, x0l, x1h, x1l);
-        const float dy = gap_hilo(L.yh[k], L.yl[k], y0h, y0l, y1h, y1l);
-        const float D = __fmul_rn(sqrt_approx(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))), 1.f - 1e-6f);
-        if (D <= rho) {
+        const int32_t cell = L.cell[k];
+        const float xh = L.xh[k], xl = L.xl[k], yh = L.yh[k], yl = L.yl[k], mf = L.mf[k];
 #pragma unroll
-            for (int q = 0; q < PMAX; ++q) acc[q] = INFINITY;
-            continue;
+        for (int i = 0; i < PB_CELLS; ++i) {
+            const int32_t lc = cell - n0[i];
+            if ((unsigned)lc < 3u || (unsigned)(lc - nstep) < 3u || (unsigned)(lc - 2 * nstep) < 3u) continue;
+            const float dx = gap_hilo(xh, xl, x0h[i], x0l[i], x1h[i], x1l[i]);
+            const float dy = gap_hilo(yh, yl, y0h[i], y0l[i], y1h[i], y1l[i]);
+            const float D = __fmul_rn(sqrt_approx(__fmaf_rn(dx, dx, __fmul_rn(dy, dy))), 1.f - 1e-6f);
+            if (D <= rho) {
+#pragma unroll
+                for (int q = 0; q < PMAX; ++q) acc[i][q] = INFINITY;
+                continue;
+            }
+            const float u = __fmul_rn(rho, rcp_approx(D));
+            float t = __fmul_rn(__fmul_rn(mf, u), rcp_approx(__fsub_rn(D, rho)));  // times u^{p} below
+#pragma unroll
+            for (int q = 0; q < PMAX; ++q) {
+                t = __fmul_rn(t, u);
+                acc[i][q] = __fadd_rn(acc[i][q], t);
+            }
         }
-        const float u = __fmul_rn(rho, rcp_approx(D));
-        float t = __fmul_rn(__fmul_rn(L.mf[k], u), rcp_approx(__fsub_rn(D, rho)));  // times u^{p} below
+    }
+    __shared__ float red[PB_CELLS][PMAX][ML_PB_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < PB_CELLS; ++i)
 #pragma unroll
         for (int q = 0; q < PMAX; ++q) {
-            t = __fmul_rn(t, u);
-            acc[q] = __fadd_rn(acc[q], t);
+            float v = acc[i][q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[i][q][wid] = v;
         }
-    }
-    __shared__ float red[PMAX][32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < PMAX; ++q) {
-        float v = acc[q];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[q][wid] = v;
-    }
     __syncthreads();
-    if (threadIdx.x < PMAX) {
-        double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += (double)red[threadIdx.x][w];
-        bound[c * PMAX + threadIdx.x] = v * (1.0 + 1e-5);
+    if (threadIdx.x < PB_CELLS * PMAX) {
+        const int i = threadIdx.x / PMAX, q = threadIdx.x % PMAX;
+        if (cbase + i < ncell) {
+            double v = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += (double)red[i][q][w];
+            bound[(cbase + i) * PMAX + q] = v * (1.0 + 1e-5);
+        }
     }
 }
 
 cudaError_t launch_p_bound(const Geo &g, const LensTable &L, double *bound, cudaStream_t s)
 {
     int64_t ncell = g.N1x * g.N1y;
-    k_p_bound<<<(unsigned)ncell, 256, 0, s>>>(g, L, bound);
+    k_p_bound<<<(unsigned)((ncell + PB_CELLS - 1) / PB_CELLS), ML_PB_THREADS, 0, s>>>(g, L, bound);
     return cudaGetLastError();
 }
 
@@ -463,6 +493,9 @@ struct BinomTable {
     }
 };
 __constant__ BinomTable c_binom = BinomTable();
+// The same in global memory, for loops whose lanes read different entries
+// (consecutive lanes, consecutive addresses: coalesced, cached).
+__device__ BinomTable g_binom = BinomTable();
 
 // The same rounded to FP32, for the FP32 tail orders of the node shift.
 struct BinomTableF {
@@ -547,18 +580,18 @@ __device__ __forceinline__ void p2l_add(double m, double dx, double dy, double h
     }
 }
 
-// Sum the (HP+1) complex accumulators of a 128-thread block into out
-// (global) in a fixed order.  Within a warp, orders 0..31 (64 values) go
-// through a reduce-scatter: at each of five steps a lane keeps the half of
-// its values that its lane bit selects, sends the other half to its partner
-// and adds what it receives, so that lane l ends with the warp's sums of
-// order l (about 64 additions per lane instead of 320 for a shuffle tree per
-// value); order HP takes a shuffle tree.  The warps' sums are then added in
-// warp order.
-static_assert(HP == 32, "block_sum_store's reduce-scatter assumes 33 orders");
-__device__ void block_sum_store(double *ar, double *ai, double *__restrict__ out, double *red)
+// Sum the (HP+1) complex accumulators over a warp's lanes.  Orders 0..31
+// (64 values) go through a reduce-scatter: at each of five steps a lane keeps
+// the half of its values that its lane bit selects, sends the other half to
+// its partner and adds what it receives, so that lane l ends with the warp's
+// sums of order l (about 64 additions per lane instead of 320 for a shuffle
+// tree per value), returned in (sr, si); order HP takes a shuffle tree and
+// every lane gets it in (xr, xi).
+static_assert(HP == 32, "warp_sum_orders' reduce-scatter assumes 33 orders");
+__device__ __forceinline__ void warp_sum_orders(const double *ar, const double *ai, double &sr, double &si,
+                                                double &xr, double &xi)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     double v[64];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -577,13 +610,26 @@ __device__ void block_sum_store(double *ar, double *ai, double *__restrict__ out
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
-    double xr = ar[HP], xi = ai[HP];
+    sr = v[0];
+    si = v[1];
+    xr = ar[HP];
+    xi = ai[HP];
     for (int o = 16; o > 0; o >>= 1) {
         xr += __shfl_xor_sync(0xffffffffu, xr, o);
         xi += __shfl_xor_sync(0xffffffffu, xi, o);
     }
-    red[(wid * (HP + 1) + lane) * 2] = v[0];
-    red[(wid * (HP + 1) + lane) * 2 + 1] = v[1];
+}
+
+// Sum the (HP+1) complex accumulators of a 128-thread block into out
+// (global) in a fixed order: each warp's sums (warp_sum_orders), then the
+// warps' sums added in warp order.
+__device__ void block_sum_store(double *ar, double *ai, double *__restrict__ out, double *red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double sr, si, xr, xi;
+    warp_sum_orders(ar, ai, sr, si, xr, xi);
+    red[(wid * (HP + 1) + lane) * 2] = sr;
+    red[(wid * (HP + 1) + lane) * 2 + 1] = si;
     if (lane == 0) {
         red[(wid * (HP + 1) + HP) * 2] = xr;
         red[(wid * (HP + 1) + HP) * 2 + 1] = xi;
@@ -651,18 +697,24 @@ __global__ void __launch_bounds__(128) k_box_p2l(Geo g, LensTable L, const int2 
 }
 
 // 2. sub-block series: box series shifted to z_s plus the direct sum of the
-// lenses in the box block but outside the cell's 3 x 3 block.
-__global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 *__restrict__ lc,
-                                                 Hier h, const double *__restrict__ part,
-                                                 const int32_t *__restrict__ ostart,
-                                                 const int32_t *__restrict__ oidx,
-                                                 double *__restrict__ sub, float *__restrict__ sub32,
-                                                 int32_t *__restrict__ j64)
+// lenses in the box block but outside the cell's 3 x 3 block.  One warp per
+// sub-block (a sub-block sums a few hundred lenses at most, and its fixed
+// work, the shift, is one order per lane), SUB_WARPS sub-blocks per block.
+constexpr int SUB_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * SUB_WARPS, 3) k_sub_p2l(Geo g, LensTable L, const int2 *__restrict__ lc,
+                                                             Hier h, const double *__restrict__ part,
+                                                             const int32_t *__restrict__ ostart,
+                                                             const int32_t *__restrict__ oidx,
+                                                             double *__restrict__ sub, float *__restrict__ sub32,
+                                                             int32_t *__restrict__ j64, int64_t ns)
 {
-    __shared__ double red[4 * (HP + 1) * 2];
-    __shared__ double A[(HP + 1) * 2];
-    __shared__ double binom[(HP + 1) * (HP + 1)];
-    const int64_t s = blockIdx.x;
+    __shared__ double shA[SUB_WARPS][(HP + 1) * 2];
+    __shared__ double shR[SUB_WARPS][HP + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t s = (int64_t)blockIdx.x * SUB_WARPS + wid;
+    if (s >= ns) return;                     // warp-uniform; the kernel has no block barrier
+    double *A = shA[wid], *red = shR[wid];
     const int64_t nsub = h.nsx * h.nsy;
     const int64_t cell = s / nsub, sb = s % nsub;
     const int64_t cx = cell % g.N1x, cy = cell / g.N1x;
@@ -691,7 +743,7 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
         const int64_t b0 = (ry + 1) * g.NEx + (rx0 + 1), b1 = (ry + 1) * g.NEx + (rx1 + 1);
         const int64_t k0 = L.start[b0], k1 = L.start[b1 + 1];
         const bool near_row = ry - cy <= 1 && cy - ry <= 1;
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        for (int64_t k = k0 + lane; k < k1; k += 32) {
             if (near_row) {
                 const int64_t lx = lc[k].x;
                 if (lx - cx <= 1 && cx - lx <= 1) continue;
@@ -703,7 +755,7 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
         const int64_t obx = h.NBx + 2;
         for (int64_t by = By - 1; by <= By + 1; ++by) {
             const int64_t b0 = (by + 1) * obx + Bx;          // bins of boxes Bx-1..Bx+1
-            for (int64_t q = ostart[b0] + threadIdx.x; q < ostart[b0 + 3]; q += blockDim.x) {
+            for (int64_t q = ostart[b0] + lane; q < ostart[b0 + 3]; q += 32) {
                 const int32_t k = oidx[q];
                 p2l_add(L.m[k], L.x[k] - zx, L.y[k] - zy, hs, ihs, ar, ai);
             }
@@ -711,7 +763,7 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
     }
     // box series of this cell's box: sum of the partitions (fixed order)
     const int64_t b = By * h.NBx + Bx;
-    for (int j = threadIdx.x; j <= HP; j += blockDim.x) {
+    for (int j = lane; j <= HP; j += 32) {
         double vr = 0.0, vi = 0.0;
         for (int q = 0; q < HPARTS; ++q) {
             vr += part[((b * HPARTS + q) * (HP + 1) + j) * 2];
@@ -720,40 +772,40 @@ __global__ void __launch_bounds__(128) k_sub_p2l(Geo g, LensTable L, const int2 
         A[2 * j] = vr;
         A[2 * j + 1] = vi;
     }
-    for (int t = threadIdx.x; t < (HP + 1) * (HP + 1); t += blockDim.x) binom[t] = c_binom.v[t];
-    __syncthreads();
-    block_sum_store(ar, ai, sub + s * (HP + 1) * 2, red);
-    __syncthreads();
+    // the direct sums: lane j holds order j, every lane order HP
+    double sr, si, xr, xi;
+    warp_sum_orders(ar, ai, sr, si, xr, xi);
+    __syncwarp();
     // shift the box series to z_s: coefficient of V^j, V = (z - z_s)/hs, is
     // rho^j sum_{i>=j} C(i, j) A_i d^{i-j},  d = (z_s - z_B)/h_B, rho = hs/h_B
     const double zBx = g.rx0 + ((double)Bx + 0.5) * (double)h.bxn * g.l1x;
     const double zBy = g.ry0 + ((double)By + 0.5) * (double)h.byn * g.l1y;
     const double dr = (zx - zBx) / h.hB, di = (zy - zBy) / h.hB, rho = hs / h.hB;
-    for (int j = threadIdx.x; j <= HP; j += blockDim.x) {
+    for (int j = lane; j <= HP; j += 32) {
         double vr = 0.0, vi = 0.0;
         for (int i = HP; i >= j; --i) {      // Horner in d
-            double c = binom[i * (HP + 1) + j];
-            double nr = vr * dr - vi * di + c * A[2 * i];
-            double ni = vr * di + vi * dr + c * A[2 * i + 1];
+            const double c = g_binom.v[i * (HP + 1) + j];
+            const double nr = vr * dr - vi * di + c * A[2 * i];
+            const double ni = vr * di + vi * dr + c * A[2 * i + 1];
             vr = nr;
             vi = ni;
         }
         double sc = 1.0, rp = rho;           // rho^j by squaring
         for (int e = j; e > 0; e >>= 1, rp *= rp)
             if (e & 1) sc *= rp;
-        const double fr = sub[(s * (HP + 1) + j) * 2] + vr * sc;
-        const double fi = sub[(s * (HP + 1) + j) * 2 + 1] + vi * sc;
+        const double fr = (j == HP ? xr : sr) + vr * sc;
+        const double fi = (j == HP ? xi : si) + vi * sc;
         sub[(s * (HP + 1) + j) * 2] = fr;
         sub[(s * (HP + 1) + j) * 2 + 1] = fi;
         sub32[(s * (HP + 1) + j) * 2] = (float)fr;
         sub32[(s * (HP + 1) + j) * 2 + 1] = (float)fi;
-        red[j] = fabs(fr) + fabs(fi);   // red is free after block_sum_store
+        red[j] = fabs(fr) + fabs(fi);
     }
-    __syncthreads();
+    __syncwarp();
     // FP64 length of the node's c_0 sum: the orders above j64 add up (in
     // |re| + |im|) to at most 2^-35 max(|re a_0|, |im a_0|), so their FP32 sum
     // (error below 2^-19 of that, |e| <= 1) stays under the FP64 rounding of c_0
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         const double lim = 2.9103830456733704e-11 * fmax(fabs(sub[s * (HP + 1) * 2]),
                                                          fabs(sub[s * (HP + 1) * 2 + 1]));
         double tail = 0.0;
@@ -881,7 +933,9 @@ cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64,
     k_outer_csr<<<1, SCAT_THREADS, 0, s>>>(lc, L.start, g.NEx * g.NEy, h, ocnt, ostart, oidx);
     dim3 gb((unsigned)nb, HPARTS);
     k_box_p2l<<<gb, 128, 0, s>>>(g, L, lc, h, part);
-    k_sub_p2l<<<(unsigned)ns, 128, 0, s>>>(g, L, lc, h, part, ostart, oidx, sub, sub32, j64);
+    k_sub_p2l<<<(unsigned)((ns + SUB_WARPS - 1) / SUB_WARPS), 32 * SUB_WARPS, 0, s>>>(g, L, lc, h, part, ostart,
+                                                                                  oidx, sub, sub32, j64,
+                                                                                  (int64_t)ns);
     int64_t nn = g.N2x * g.N2y;
     k_node_shift<<<(unsigned)((nn + 127) / 128), 128, 0, s>>>(g, h, sub, sub32, j64, coef64);
     e = cudaGetLastError();

@@ -786,13 +786,14 @@ __device__ __forceinline__ void walk_span(const RowPoly<P> &rp, const ShootArgs 
             // the next window starts ML_SPAN_MARGIN rays before it
             gap = 1;
             if (ka > kp && fabsf(Xa) < LIM && fabsf(Ya) < LIM && fabsf(Xp) < LIM && fabsf(Yp) < LIM) {
-                const float inv = rcp_approx((float)(ka - kp));
-                const float sX = __fsub_rn(Xa, Xp) * inv, sY = __fsub_rn(Ya, Yp) * inv;
+                // (one reciprocal per component on the step's critical path)
+                const float fk = (float)(ka - kp);
+                const float dX = __fsub_rn(Xa, Xp), dY = __fsub_rn(Ya, Yp);
                 const float fX = __fsub_rn(Xa, __fsub_rn(__int_as_float((int)rcx), 12582912.0f));
                 const float fY = __fsub_rn(Ya, __fsub_rn(__int_as_float((int)rcy), 12582912.0f));
-                const float gX = sX > 0.f ? __fsub_rn(1.f, fX) : fX;
-                const float gY = sY > 0.f ? __fsub_rn(1.f, fY) : fY;
-                const float n = fminf(fminf(gX * rcp_approx(fabsf(sX)), gY * rcp_approx(fabsf(sY))), 1048576.f);
+                const float gX = (dX > 0.f ? __fsub_rn(1.f, fX) : fX) * fk;
+                const float gY = (dY > 0.f ? __fsub_rn(1.f, fY) : fY) * fk;
+                const float n = fminf(fminf(gX * rcp_approx(fabsf(dX)), gY * rcp_approx(fabsf(dY))), 1048576.f);
                 gap = max(1, floor_to_int(n - ML_SPAN_MARGIN));
             }
         }
