@@ -39,13 +39,25 @@ N_TRACKS, TRACK_SAMPLES, SIGMA_PX = 10, 4096, 0.5
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # copy bandwidth of the GB300s (GB/s), the HBM roofline's denominator
 HBM_GBS_FALLBACK = 6790.0
-# DRAM bytes per ray of the counting kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch over a 2e10-ray
-# slice of the paper-scale lattice at the autotuned grid), valid for the
-# kernel sources whose code (comments and blank space left out, code_hash)
-# has these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = (216.086016e6 + 272.358144e6) / 2.0e10
+# DRAM bytes per ray of the certified counting kernel, from one ncu capture
+# per workload (dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# over a centred slice of the lattice at the autotuned grid: 2e10 rays of the
+# paper-scale map, 2e9 of the Table-1 fold field, whose 84 MB map stays in
+# L2), valid for the kernel sources whose code (comments and blank space left
+# out, code_hash) has these sha1 prefixes only.
+TRAFFIC_BYTES_PER_RAY = {"paper": (216.086016e6 + 272.358144e6) / 2.0e10,
+                         "fold": (23.782144e6 + 512.0) / 2.0e9}
 TRAFFIC_SOURCES = {"ml_shoot.cu": "48c686ae", "ml_internal.cuh": "4806c1e0", "ml_task.cuh": "3d1d5136"}
+
+
+def code_hash(text: str) -> str:
+    """sha1 of a C++/CUDA source's code: comments, blank lines and spacing
+    left out, so that editing a comment does not count as a kernel change."""
+    import hashlib
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    lines = (" ".join(re.sub(r"//.*$", "", ln).split()) for ln in text.splitlines())
+    return hashlib.sha1("\n".join(ln for ln in lines if ln).encode()).hexdigest()
 
 
 # The library's kernels in one field build: k_lens_cells, k_scan, k_scatter,
@@ -72,24 +84,17 @@ def fold_peak_summary(stats, info):
             "mean_mu_peak": [round(float(v), 3) for v in mu]}
 
 
-def code_hash(text: str) -> str:
-    """sha1 of a C++/CUDA source's code: comments, blank lines and spacing
-    left out, so that editing a comment does not count as a kernel change."""
-    import hashlib
-    import re
-    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-    lines = (" ".join(re.sub(r"//.*$", "", ln).split()) for ln in text.splitlines())
-    return hashlib.sha1("\n".join(ln for ln in lines if ln).encode()).hexdigest()
-
-
-def traffic_per_launch(rays_per_launch: float):
-    """Measured DRAM bytes per launch, or None once the kernel has changed."""
+def traffic_per_launch(rays_per_launch: float, workload: str = "paper", walk: str = "certified"):
+    """Measured DRAM bytes per launch of a workload's certified walk, or None
+    for another kernel or once the kernel has changed."""
+    if walk != "certified" or workload not in TRAFFIC_BYTES_PER_RAY:
+        return None
     csrc = os.path.join(ROOT, "paper_2308_14278_gb300", "csrc")
     for name, prefix in TRAFFIC_SOURCES.items():
         with open(os.path.join(csrc, name)) as fh:
             if not code_hash(fh.read()).startswith(prefix):
                 return None
-    return TRAFFIC_BYTES_PER_RAY * rays_per_launch
+    return TRAFFIC_BYTES_PER_RAY[workload] * rays_per_launch
 
 
 def parse():
@@ -126,8 +131,10 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="the paper's level-2 grid (L2 = L1/20) instead of the autotuned one")
     ap.add_argument("--grid", default="",
-                    help="profiling: fix the grid the autotuner chose, 'L1X,L1Y,SX,SY' (level-1 "
-                         "cell size in theta_E, level-2 subdivisions), instead of tuning again")
+                    help="profiling: fix the grid the autotuner chose, 'L1X,L1Y,SX,SY[,FAR]' "
+                         "(level-1 cell size in theta_E, level-2 subdivisions and, optionally, "
+                         "the certified walk's lens distance in lattice spacings, 'inf' for "
+                         "lens columns walked per ray), instead of tuning again")
     ap.add_argument("--walk", default="certified", choices=["certified", "per_ray"],
                     help="ray walk of the counting kernel: certified spans (default) or every "
                          "ray evaluated; both give bit-identical maps")
@@ -144,9 +151,13 @@ def grid_kwargs(args, w):
     walk = ml.WALK_PER_RAY if getattr(args, "walk", "certified") == "per_ray" else ml.WALK_CERTIFIED
     if not args.grid:
         return dict(tune=not args.no_tune, walk=walk)
-    l1x, l1y, sx, sy = (float(v) for v in args.grid.split(","))
+    vals = args.grid.split(",")
+    l1x, l1y, sx, sy = (float(v) for v in vals[:4])
     w.l1 = (l1x, l1y)
-    return dict(tune=False, l2_sub=(int(sx), int(sy)), walk=walk)
+    kw = dict(tune=False, l2_sub=(int(sx), int(sy)), walk=walk)
+    if len(vals) > 4:
+        kw["span_far"] = 3.0e38 if vals[4].strip() == "inf" else float(vals[4])
+    return kw
 
 
 def dist_env():
@@ -407,7 +418,7 @@ def run_ours(args, rank, world, local):
     exec_flops = ((4.0 * p + 6.0) * evals + 11.0 * stats["near_pairs"] * evals / max(1, n_local)) / launches
     peak = fp32_peak["two_lane_tflops"]
     achieved = alg_flops / launch_s / 1e12
-    traffic = traffic_per_launch(n_local / launches)
+    traffic = traffic_per_launch(n_local / launches, args.workload, args.walk)
     hbm_peak, hbm_src = hbm_peak_gbs()
     out = {
         "metric": METRIC if args.workload == "paper" else
