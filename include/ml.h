@@ -279,11 +279,10 @@ ml_status ml_light_curves(ml_field *f, const double *tracks, int32_t n_tracks, i
  * until the process exits.
  *  tracks:  host, n_tracks x (x0, y0, x1, y1) in map pixel coordinates.
  *  out:     DEVICE buffer of n_tracks x n_samples float32 (caller-owned).
- * The first call on each device looks up the array's device address; make
- * that first call before any stream capture.  All calls share the one
- * array: calls that overlap on the GPU (different streams without ordering)
- * race, so order them on one stream.  Nothing in the array needs clearing:
- * each call overwrites the part it uses.
+ * The first call on each device looks up the array's device address.  All
+ * calls share the one array: calls that overlap on the GPU (different
+ * streams without ordering) race, so order them on one stream.  Nothing in
+ * the array needs clearing: each call overwrites the part it uses.
  * Errors: ML_ERR_INVALID_ARG for n_tracks > ML_NOALLOC_MAX_TRACKS, counts < 1,
  * sigma_px outside (0, 16] or NULL pointers; ML_ERR_CUDA.
  */
