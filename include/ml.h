@@ -491,6 +491,10 @@ ml_status ml_field_info(const ml_field *f, ml_field_params *out);
 ml_status ml_field_abort(ml_field *f, int32_t on);
 
 /* ml_field_destroy - free the field and its device memory.  NULL is a no-op.
+ * The library takes device memory from a stream-ordered pool of its own per
+ * device, which keeps freed memory for the next fields (creating a field
+ * then reuses its predecessor's buffers instead of mapping new ones); the
+ * pool's memory is returned when the process exits.
  * Bookkeeping; no counterpart in the paper. */
 ml_status ml_field_destroy(ml_field *f);
 

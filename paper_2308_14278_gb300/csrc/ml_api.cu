@@ -1,6 +1,7 @@
 // C ABI of the microlensing library: descriptor validation, the parameter
 // derivation of §3.1-§3.2, device buffers, and stream-ordered launches.
 #include "ml_internal.cuh"
+#include "ml_alloc.h"
 
 #include <math.h>
 #include <stdio.h>
@@ -122,7 +123,7 @@ struct ml_field {
     {
         *p = nullptr;
         if (count == 0) count = 1;
-        cudaError_t e = cudaMallocAsync((void **)p, count * sizeof(T), s);
+        cudaError_t e = ml_malloc_async((void **)p, count * sizeof(T), s);
         if (e == cudaSuccess) owned.push_back(*p);
         return e;
     }
@@ -455,7 +456,27 @@ uint64_t tune_key(const ml_field_desc &d, const std::vector<double> &hx, const s
     h = mix64(h, (uint64_t)d.taylor_p); h = mix64(h, (uint64_t)hx.size());
     h = mix64(h, (uint64_t)d.walk); h = mix64(h, (uint64_t)d.macro_mode);
     h = mix64(h, (uint64_t)d.sheet_shape); mixd(d.kappa0); mixd(d.d_x); mixd(d.d_y);
-    for (size_t k = 0; k < hx.size(); ++k) { mixd(hx[k]); mixd(hy[k]); mixd(hm[k]); }
+    // the lens arrays in four independent lanes (no serial dependency per word),
+    // then the lanes into the parameter hash
+    uint64_t l[4] = {0x243F6A8885A308D3ull, 0x13198A2E03707344ull, 0xA4093822299F31D0ull,
+                     0x082EFA98EC4E6C89ull};
+    const std::vector<double> *arr[3] = {&hx, &hy, &hm};
+    for (const std::vector<double> *a : arr) {
+        const size_t n = a->size();
+        size_t k = 0;
+        for (; k + 4 <= n; k += 4)
+            for (int q = 0; q < 4; ++q) {
+                uint64_t u;
+                memcpy(&u, &(*a)[k + q], 8);
+                l[q] = mix64(l[q], u);
+            }
+        for (; k < n; ++k) {
+            uint64_t u;
+            memcpy(&u, &(*a)[k], 8);
+            l[0] = mix64(l[0], u);
+        }
+    }
+    for (int q = 0; q < 4; ++q) h = mix64(h, l[q]);
     return h;
 }
 
@@ -464,12 +485,11 @@ std::unordered_map<uint64_t, std::vector<TuneCand>> g_tune_cache;
 
 // Feasible candidate grids of a field (cached per process by a hash of the
 // descriptor's parameters and the lens arrays).
-ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
+ml_status tune_candidates(uint64_t key, const ml_field_desc &d, const std::vector<double> &hx,
                           const std::vector<double> &hy, const std::vector<double> &hm,
                           const double *dx, const double *dy, const double *dm, cudaStream_t s,
                           std::vector<TuneCand> &out)
 {
-    const uint64_t key = tune_key(d, hx, hy, hm);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -489,7 +509,7 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
     struct Cand { int sx, sy; double l1x, l1y; Geo g; int32_t *cells; int32_t *counts; double *bound; };
     std::vector<Cand> cands;
     float *f32 = nullptr;            // FP32 copies of the (unsorted) lenses for the bounds
-    cudaError_t e = cudaMallocAsync((void **)&f32, sizeof(float) * 5 * (size_t)std::max<int64_t>(n, 1), s);
+    cudaError_t e = ml_malloc_async((void **)&f32, sizeof(float) * 5 * (size_t)std::max<int64_t>(n, 1), s);
     if (e == cudaSuccess) e = launch_split_f32(dx, dy, dm, n, f32, s);
     for (double sc : scales)
     for (int a : fine)
@@ -509,10 +529,10 @@ ml_status tune_candidates(const ml_field_desc &d, const std::vector<double> &hx,
             if (c.g.n2x < 2 || c.g.n2y < 1 || c.g.N2x * c.g.N2y > ((int64_t)1 << 26)) continue;
             if (c.g.NEx * c.g.NEy >= ((int64_t)1 << 30)) continue;
             const int64_t NE = c.g.NEx * c.g.NEy;
-            e = cudaMallocAsync((void **)&c.cells, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1), s);
-            if (e == cudaSuccess) e = cudaMallocAsync((void **)&c.counts, sizeof(int32_t) * (size_t)(NE + 1), s);
+            e = ml_malloc_async((void **)&c.cells, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1), s);
+            if (e == cudaSuccess) e = ml_malloc_async((void **)&c.counts, sizeof(int32_t) * (size_t)(NE + 1), s);
             if (e == cudaSuccess)
-                e = cudaMallocAsync((void **)&c.bound, sizeof(double) * (size_t)(c.g.N1x * c.g.N1y * PMAX), s);
+                e = ml_malloc_async((void **)&c.bound, sizeof(double) * (size_t)(c.g.N1x * c.g.N1y * PMAX), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(c.counts, 0, sizeof(int32_t) * (size_t)(NE + 1), s);
             if (e == cudaSuccess) e = launch_lens_cells(c.g, dx, dy, n, c.cells, c.counts, s);
             if (e == cudaSuccess) {
@@ -606,11 +626,11 @@ ml_status tune_grid(const ml_field_desc &d, const std::vector<double> &hx, const
                     cudaStream_t s, bool measure, GridChoice &best)
 {
     std::vector<TuneCand> cands;
-    ml_status st = tune_candidates(d, hx, hy, hm, dx, dy, dm, s, cands);
+    const uint64_t key = tune_key(d, hx, hy, hm);
+    ml_status st = tune_candidates(key, d, hx, hy, hm, dx, dy, dm, s, cands);
     if (st != ML_OK) return st;
     best = cands.empty() ? GridChoice() : best_single(cands);
     if (!measure || cands.size() < 2) return ML_OK;
-    const uint64_t key = tune_key(d, hx, hy, hm);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_measured.find(key);
@@ -801,7 +821,7 @@ ml_status create_plan(const ml_field_desc *d_in, cudaStream_t s, ml_field *f)
     // truncation bound of every Taylor order, worst level-1 cell
     std::vector<double> bound((size_t)(g.N1x * g.N1y) * PMAX);
     double *d_bound = nullptr;
-    ML_CK(cudaMallocAsync((void **)&d_bound, bound.size() * sizeof(double), s));
+    ML_CK(ml_malloc_async((void **)&d_bound, bound.size() * sizeof(double), s));
     g.p = 1;
     cudaError_t e = launch_p_bound(g, f->table(), d_bound, s);
     if (e == cudaSuccess)
@@ -852,7 +872,7 @@ ml_status create_finish(ml_field *f, int p, cudaStream_t s, bool sync = true)
             size_t ns = hier_scratch_doubles(g);
             if (ns > 0) {
                 double *scratch = nullptr;
-                ML_CK(cudaMallocAsync((void **)&scratch, ns * sizeof(double), s));
+                ML_CK(ml_malloc_async((void **)&scratch, ns * sizeof(double), s));
                 cudaError_t e = launch_coeffs_hier(g, L, f->d_coef64, scratch, ns, s);
                 cudaFreeAsync(scratch, s);
                 if (e != cudaSuccess) return cuda_fail(e, "hierarchical coefficient build");
@@ -1081,7 +1101,7 @@ struct ml_batch {
     {
         *ptr = nullptr;
         if (count == 0) count = 1;
-        cudaError_t e = cudaMallocAsync((void **)ptr, count * sizeof(T), s);
+        cudaError_t e = ml_malloc_async((void **)ptr, count * sizeof(T), s);
         if (e == cudaSuccess) owned.push_back(*ptr);
         return e;
     }
@@ -1187,9 +1207,9 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
         if (st != ML_OK) return st;
         const size_t nl = std::max<size_t>(hx.size(), 1);
         double *dx = nullptr, *dy = nullptr, *dm = nullptr;
-        ML_CK(cudaMallocAsync((void **)&dx, nl * sizeof(double), s));
-        ML_CK(cudaMallocAsync((void **)&dy, nl * sizeof(double), s));
-        ML_CK(cudaMallocAsync((void **)&dm, nl * sizeof(double), s));
+        ML_CK(ml_malloc_async((void **)&dx, nl * sizeof(double), s));
+        ML_CK(ml_malloc_async((void **)&dy, nl * sizeof(double), s));
+        ML_CK(ml_malloc_async((void **)&dm, nl * sizeof(double), s));
         cudaError_t e = cudaSuccess;
         if (!hx.empty()) {
             e = cudaMemcpyAsync(dx, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -1326,6 +1346,39 @@ ml_status batch_create_impl(const ml_field_desc *descs, int32_t n, int32_t tpm, 
 }  // namespace
 
 namespace ml {
+cudaError_t ml_malloc_async(void **p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[MAXDEV] = {};
+    if (dev < 0 || dev >= MAXDEV) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            e = cudaMemPoolCreate(&np, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = UINT64_MAX;   // never trim at synchronisation
+            e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(np);
+                return e;
+            }
+            pools[dev] = np;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 // peak statistics kernels (ml_maps.cu): out holds n_peaks, sum_counts and
 // n_positions, nbins 64-bit counters each
 cudaError_t launch_peak_stats(const uint32_t *N, int nx, int ny, int along, const uint8_t *mask,
@@ -1528,7 +1581,7 @@ ml_status ml_magnification_map(ml_field *f, int32_t want, void *out, int32_t out
     }
     const size_t esz = want == ML_MAP_MU_F32 ? 4 : 8;
     void *dst = out;
-    if (!out_is_device) ML_CK(cudaMallocAsync(&dst, npix * esz, s));
+    if (!out_is_device) ML_CK(ml_malloc_async(&dst, npix * esz, s));
     else if ((uintptr_t)out % 16 != 0)
         return fail(ML_ERR_INVALID_ARG, "device output must be 16-byte aligned");
     cudaError_t e = launch_mu(g, f->d_map_u32, f->d_map_f32, want, dst, scale, s);
@@ -1556,10 +1609,10 @@ ml_status ml_light_curves(ml_field *f, const double *tracks, int32_t n_tracks, i
     const size_t nout = (size_t)n_tracks * n_samples;
     double *d_tr = nullptr;
     float *dst = out;
-    ML_CK(cudaMallocAsync((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
+    ML_CK(ml_malloc_async((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
     cudaError_t e = cudaMemcpyAsync(d_tr, tracks, sizeof(double) * 4 * n_tracks,
                                     cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && !out_is_device) e = cudaMallocAsync((void **)&dst, nout * sizeof(float), s);
+    if (e == cudaSuccess && !out_is_device) e = ml_malloc_async((void **)&dst, nout * sizeof(float), s);
     if (e == cudaSuccess)
         e = launch_light_curves(g, f->d_map_u32, f->d_map_f32, scale, d_tr, n_tracks, n_samples,
                                 sigma_px, dst, s);
@@ -1599,7 +1652,7 @@ ml_status ml_map_light_curves(const float *mu, int32_t nx, int32_t ny, const dou
     g.mnx = nx;
     g.mny = ny;
     double *d_tr = nullptr;
-    ML_CK(cudaMallocAsync((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
+    ML_CK(ml_malloc_async((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
     cudaError_t e = cudaMemcpyAsync(d_tr, tracks, sizeof(double) * 4 * n_tracks, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = launch_light_curves(g, nullptr, mu, 1.0, d_tr, n_tracks, n_samples, sigma_px, out, s);
@@ -1617,7 +1670,7 @@ ml_status ml_map_light_curves_backward(int32_t nx, int32_t ny, const double *tra
     cudaStream_t s = (cudaStream_t)stream;
     double *d_tr = nullptr;
     ML_CK(cudaMemsetAsync(dL_dmu, 0, sizeof(float) * (size_t)nx * (size_t)ny, s));
-    ML_CK(cudaMallocAsync((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
+    ML_CK(ml_malloc_async((void **)&d_tr, sizeof(double) * 4 * n_tracks, s));
     cudaError_t e = cudaMemcpyAsync(d_tr, tracks, sizeof(double) * 4 * n_tracks, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = launch_light_curves_adj(nx, ny, d_tr, n_tracks, n_samples, sigma_px, dL_dcurves, dL_dmu, s);
@@ -1686,8 +1739,8 @@ ml_status ml_cic_backward_ex(ml_field *f, const float *dL_dM, double *grad_lens,
     const size_t n_mom = (size_t)(g.N2x * g.N2y) * (size_t)(g.p + 1);
     double *gs = nullptr;
     double2 *mom = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&gs, sizeof(double) * 3 * (size_t)std::max<int64_t>(n, 1), s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&mom, sizeof(double2) * n_mom, s);
+    cudaError_t e = ml_malloc_async((void **)&gs, sizeof(double) * 3 * (size_t)std::max<int64_t>(n, 1), s);
+    if (e == cudaSuccess) e = ml_malloc_async((void **)&mom, sizeof(double2) * n_mom, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(gs, 0, sizeof(double) * 3 * (size_t)n, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(mom, 0, sizeof(double2) * n_mom, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(f->d_work, 0, sizeof(unsigned long long), s);
@@ -1738,8 +1791,8 @@ ml_status ml_find_peaks(ml_field *f, int32_t along, double nsigma, uint8_t *mask
     uint8_t *m = mask;
     unsigned long long *found = nullptr, h_found = 0;
     cudaError_t e = cudaSuccess;
-    if (!m) e = cudaMallocAsync((void **)&m, npix + 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&found, sizeof(unsigned long long), s);
+    if (!m) e = ml_malloc_async((void **)&m, npix + 4, s);
+    if (e == cudaSuccess) e = ml_malloc_async((void **)&found, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
         e = launch_peaks(f->d_map_u32, f->g.mnx, f->g.mny, along, nsigma, m, peaks, capacity, found, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h_found, found, sizeof(h_found), cudaMemcpyDeviceToHost, s);
@@ -1780,7 +1833,7 @@ ml_status ml_peak_statistics(ml_field *f, int32_t along, double nsigma, const ui
     const size_t bytes = mask ? o_mask : o_found + 16;
     char *scratch = nullptr;
     std::vector<unsigned long long> h(3 * (size_t)nbins);
-    cudaError_t e = cudaMallocAsync((void **)&scratch, bytes, s);
+    cudaError_t e = ml_malloc_async((void **)&scratch, bytes, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scratch + o_edges, edges, (size_t)(nbins + 1) * sizeof(double),
                             cudaMemcpyHostToDevice, s);

@@ -3,6 +3,7 @@
 // coefficients at the level-2 nodes (§3.2 Level 2) and the per-node records
 // of the mixed-precision path.
 #include "ml_internal.cuh"
+#include "ml_alloc.h"
 
 #include <math.h>
 
@@ -205,7 +206,7 @@ cudaError_t launch_scatter(const double *x, const double *y, const double *m,
 {
     if (n == 0) return cudaSuccess;
     int32_t *cnt = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&cnt, sizeof(int32_t) * (size_t)(SCAT_THREADS / 32) * (size_t)nb, s);
+    cudaError_t e = ml_malloc_async((void **)&cnt, sizeof(int32_t) * (size_t)(SCAT_THREADS / 32) * (size_t)nb, s);
     if (e != cudaSuccess) return e;
     k_scatter<<<1, SCAT_THREADS, 0, s>>>(x, y, m, cell, n, start, nb, cnt, sx, sy, sm, scell, perm, f32);
     e = cudaGetLastError();
@@ -925,7 +926,7 @@ cudaError_t launch_coeffs_hier(const Geo &g, const LensTable &L, double *coef64,
     const size_t nob = (size_t)((h.NBx + 2) * (h.NBy + 2));
     const size_t ints = 2 * nl + (nob + 1) + nl + (size_t)(SCAT_THREADS / 32) * nob;
     int32_t *iw = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&iw, sizeof(int32_t) * ints, s);
+    cudaError_t e = ml_malloc_async((void **)&iw, sizeof(int32_t) * ints, s);
     if (e != cudaSuccess) return e;
     int2 *lc = reinterpret_cast<int2 *>(iw);
     int32_t *ostart = iw + 2 * nl, *oidx = ostart + nob + 1, *ocnt = oidx + nl;

@@ -1,6 +1,7 @@
 // Map kernels: magnification from counts (Eq. 12) and light curves of a
 // Gaussian source along straight tracks (§4.1, Fig. 3).
 #include "ml_internal.cuh"
+#include "ml_alloc.h"
 
 #include <algorithm>
 
@@ -218,7 +219,7 @@ cudaError_t launch_light_curves(const Geo &g, const uint32_t *cu, const float *c
     int h = light_curve_taps(sigma_px, taps);
     if (h < 0) return cudaErrorInvalidValue;
     float *d_taps = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d_taps, sizeof(float) * (2 * h + 1), s);
+    cudaError_t e = ml_malloc_async((void **)&d_taps, sizeof(float) * (2 * h + 1), s);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d_taps, taps, sizeof(float) * (2 * h + 1), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) { cudaFreeAsync(d_taps, s); return e; }
@@ -480,7 +481,7 @@ cudaError_t launch_light_curves_adj(int mnx, int mny, const double *d_tracks, in
     const int h = light_curve_taps(sigma_px, taps);
     if (h < 0) return cudaErrorInvalidValue;
     float *d_taps = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d_taps, sizeof(float) * (2 * h + 1), s);
+    cudaError_t e = ml_malloc_async((void **)&d_taps, sizeof(float) * (2 * h + 1), s);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(d_taps, taps, sizeof(float) * (2 * h + 1), cudaMemcpyHostToDevice, s);
     const int64_t n = (int64_t)n_tracks * n_samples;
