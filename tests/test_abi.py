@@ -142,6 +142,33 @@ def test_bench_traffic_check_ignores_comments():
     c = "int f(int x)\n{\n    return x + 2;\n}\n"
     assert bench.code_hash(a) == bench.code_hash(b) != bench.code_hash(c)
     assert bench.traffic_per_launch(1e9) is not None
+    # one measured figure per workload of the certified walk; none for the
+    # per-ray walk or a workload that was not captured
+    assert bench.traffic_per_launch(2e10) == pytest.approx(216.086016e6 + 272.358144e6)
+    assert bench.traffic_per_launch(2e9, "fold") == pytest.approx(23.782144e6 + 512.0)
+    assert bench.traffic_per_launch(1e9, "paper", "per_ray") is None
+    assert bench.traffic_per_launch(1e9, "batched") is None
+
+
+def test_bench_grid_flag_takes_an_optional_span_distance():
+    """--grid fixes the level-1 size and level-2 subdivisions, and optionally
+    the certified walk's lens distance ('inf': lens columns walked per ray)."""
+    import sys
+    import types
+    bench = _bench_module()
+    for grid, far in (("7.5,1.25,20,10", None), ("28.5,28,20,10,100", 100.0),
+                      ("7.5,1.25,20,10,inf", 3.0e38)):
+        argv = sys.argv
+        try:
+            sys.argv = ["bench.py", "--grid", grid]
+            args = bench.parse()
+        finally:
+            sys.argv = argv
+        w = types.SimpleNamespace()
+        kw = bench.grid_kwargs(args, w)
+        vals = [float(v) for v in grid.split(",")[:4]]
+        assert w.l1 == (vals[0], vals[1]) and kw["l2_sub"] == (int(vals[2]), int(vals[3]))
+        assert kw["tune"] is False and kw.get("span_far") == far
 
 
 def _bench_module():
