@@ -246,6 +246,9 @@ ml_status ml_shoot_rays(ml_field *f, uint64_t ray_begin, uint64_t ray_end, void 
  * S_S, Eq. 12; for CIC maps the weights take the place of N_ij).
  *  out: caller-owned buffer of map_nx * map_ny elements, device memory if
  *       out_is_device else host memory (then the call synchronises stream).
+ *       Host memory that is page-locked and mapped (cudaHostAlloc, pinned
+ *       tensors) receives mu straight from the kernel over the host link;
+ *       other host memory receives it through a device buffer and a copy.
  * Errors: ML_ERR_STATE for counts of a CIC map; ML_ERR_INVALID_ARG; ML_ERR_CUDA.
  */
 ml_status ml_magnification_map(ml_field *f, int32_t want, void *out, int32_t out_is_device,

@@ -189,9 +189,24 @@ def ml_shoot_rays(field, ray_begin: int, ray_end: int, stream=None):
     _check(load().ml_shoot_rays(field, int(ray_begin), int(ray_end), _stream(stream)))
 
 
+_MAP_ITEMSIZE = {MAP_COUNTS_U32: 4, MAP_MU_F32: 4, MAP_MU_F64: 8}
+
+
 def ml_magnification_map(field, want: int, out, stream=None):
-    """out: torch CUDA tensor (device) or numpy array (host)."""
+    """out: torch CUDA tensor (device) or numpy array (host) of the map's
+    map_ny x map_nx elements of the kind's type (host arrays are checked:
+    C-contiguous, its element size and at least that many elements)."""
     if isinstance(out, np.ndarray):
+        info = ml_field_info(field)
+        npix = info["map_nx"] * info["map_ny"]
+        kind = {MAP_COUNTS_U32: "ui", MAP_MU_F32: "f", MAP_MU_F64: "f"}.get(want)
+        if kind is None:
+            raise ValueError(f"unknown map kind {want}")
+        if (out.dtype.kind not in kind or out.dtype.itemsize != _MAP_ITEMSIZE[want]
+                or not out.flags.c_contiguous or out.size < npix):
+            raise ValueError(f"host map needs {npix} contiguous elements of "
+                             f"{_MAP_ITEMSIZE[want]} bytes ({'integer' if kind == 'ui' else 'float'}), "
+                             f"got {out.dtype} {out.shape}")
         _check(load().ml_magnification_map(field, want, out.ctypes.data, 0, _stream(stream)))
     else:
         _check(load().ml_magnification_map(field, want, _dptr(out), 1, _stream(stream)))

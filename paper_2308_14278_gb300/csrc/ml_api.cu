@@ -1581,16 +1581,29 @@ ml_status ml_magnification_map(ml_field *f, int32_t want, void *out, int32_t out
     }
     const size_t esz = want == ML_MAP_MU_F32 ? 4 : 8;
     void *dst = out;
-    if (!out_is_device) ML_CK(ml_malloc_async(&dst, npix * esz, s));
-    else if ((uintptr_t)out % 16 != 0)
-        return fail(ML_ERR_INVALID_ARG, "device output must be 16-byte aligned");
-    cudaError_t e = launch_mu(g, f->d_map_u32, f->d_map_f32, want, dst, scale, s);
-    if (e == cudaSuccess && !out_is_device)
-        e = cudaMemcpyAsync(out, dst, npix * esz, cudaMemcpyDeviceToHost, s);
+    bool staged = false;             // through a device buffer and a copy
     if (!out_is_device) {
-        cudaFreeAsync(dst, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        // page-locked host memory the GPU addresses (pinned and mapped, as
+        // cudaHostAlloc gives under unified addressing): the kernel writes the
+        // map straight into it over the host link, with no device buffer and
+        // no separate transfer; other host memory goes through a copy
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer != nullptr && (uintptr_t)pa.devicePointer % 16 == 0) {
+            dst = pa.devicePointer;
+        } else {
+            cudaGetLastError();
+            ML_CK(ml_malloc_async(&dst, npix * esz, s));
+            staged = true;
+        }
+    } else if ((uintptr_t)out % 16 != 0) {
+        return fail(ML_ERR_INVALID_ARG, "device output must be 16-byte aligned");
     }
+    cudaError_t e = launch_mu(g, f->d_map_u32, f->d_map_f32, want, dst, scale, s);
+    if (e == cudaSuccess && staged)
+        e = cudaMemcpyAsync(out, dst, npix * esz, cudaMemcpyDeviceToHost, s);
+    if (staged) cudaFreeAsync(dst, s);
+    if (!out_is_device && e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "magnification map");
     return ML_OK;
 }

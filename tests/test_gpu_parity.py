@@ -401,6 +401,22 @@ def test_mixed_light_curves_and_mu(ml):
     import paper_2308_14278_gb300 as mlmod
     mlmod.ml_light_curves(f.h, tr, 257, 0.5, host)
     assert np.array_equal(host, lc)
+    # the map into host memory: page-locked (written by the kernel over the
+    # host link) and pageable (through a device buffer), both bit-equal to the
+    # device map; a host buffer of the wrong type or size is refused
+    import torch
+    for want, dt, dev in ((mlmod.MAP_MU_F32, np.float32, mu32), (mlmod.MAP_MU_F64, np.float64, mu64),
+                          (mlmod.MAP_COUNTS_U32, np.uint32, counts.astype(np.uint32))):
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.uint32: torch.int32}[dt]
+        pinned = torch.zeros((g.mny, g.mnx), dtype=tdt).pin_memory().numpy().view(dt)
+        pageable = np.zeros((g.mny, g.mnx), dt)
+        for out in (pinned, pageable):
+            mlmod.ml_magnification_map(f.h, want, out)
+            assert np.array_equal(out, dev)
+    with pytest.raises(ValueError):
+        mlmod.ml_magnification_map(f.h, mlmod.MAP_MU_F64, np.zeros((g.mny, g.mnx), np.float32))
+    with pytest.raises(ValueError):
+        mlmod.ml_magnification_map(f.h, mlmod.MAP_MU_F32, np.zeros((g.mny, g.mnx - 1), np.float32))
     f.close()
 
 
