@@ -172,13 +172,19 @@ def dist_env():
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the SM clock, power and throttle reasons every
+    50 ms while the block runs.  Entering waits for the first sample, so that
+    sampling is under way when the timed region starts; summary() keeps the
+    samples taken between entry and exit (by their timestamps)."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, index: int, directory: str | None = None, tag: str = ""):
         self.index = index
         self.proc = None
+        self.t_in = self.t_out = None
         d = directory or os.path.join(tempfile.gettempdir(), f"ml_bench_clocks_{os.getpid()}")
         self.path = os.path.join(d, f"clocks{tag}_rank{index}.csv")
 
@@ -188,12 +194,21 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
                                           f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", str(self.PERIOD_MS)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and self.proc.poll() is None:
+                with open(self.path) as fh:
+                    if fh.read().count("\n") >= 1:
+                        break
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+        self.t_in = time.time()
         return self
 
     def __exit__(self, *exc):
+        self.t_out = time.time()
         if self.proc is not None:
             self.proc.send_signal(signal.SIGTERM)
             try:
@@ -202,28 +217,40 @@ class ClockSampler:
                 self.proc.kill()
             self.fh.close()
 
+    @staticmethod
+    def _epoch(stamp: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return None
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                sm, mx = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+            rows.append((self._epoch(parts[0]), sm, mx,
+                         {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
+        if not rows:
             return None
-        load = [s for s in sm if s > 0.5 * max(sm)] or sm
-        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        pad = self.PERIOD_MS / 1e3
+        inside = [r for r in rows if r[0] is not None and self.t_in is not None and
+                  self.t_in - pad <= r[0] <= self.t_out + pad]
+        use = inside or rows
+        sm = [r[1] for r in use]
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": float(max(r[2] for r in use)),
+                "reasons": sorted(set().union(*(r[3] for r in use))), "samples": len(use),
+                "period_ms": self.PERIOD_MS, "in_timed_region": bool(inside)}
 
 
 # ---------------------------------------------------------------------------

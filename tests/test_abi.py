@@ -275,3 +275,30 @@ def test_light_curve_outputs_are_checked_before_any_call(libpath, entry):
                 getattr(ml, entry)(None, tracks, 16, 0.5, out)
     with pytest.raises(ValueError):
         ml.ml_light_curves(None, tracks, 16, 0.5, np.zeros((2, 15), np.float32))
+
+
+def test_bench_clock_summary_keeps_the_timed_region(tmp_path):
+    """The clock summary keeps the nvidia-smi samples stamped between the
+    sampler's entry and exit (reporting their median SM clock and every
+    throttle reason seen), and falls back to all samples when none is inside."""
+    import datetime
+    import time
+    bench = _bench_module()
+    c = bench.ClockSampler(0, str(tmp_path))
+    c.proc = object()
+    now = time.time()
+
+    def st(t):
+        return datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    rows = [(now - 1.0, 1500, "Not Active", "Not Active"), (now + 0.1, 2070, "Not Active", "Active"),
+            (now + 0.2, 2070, "Not Active", "Not Active"), (now + 3.0, 1000, "Active", "Not Active")]
+    with open(c.path, "w") as fh:
+        for t, sm, hw, cap in rows:
+            fh.write(f"{st(t)}, 0, {sm}, 2070, 900.0, 0x0, {hw}, Not Active, Not Active, {cap}\n")
+    c.t_in, c.t_out = now, now + 0.3
+    s = c.summary()
+    assert s["samples"] == 2 and s["in_timed_region"] and s["sm_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    c.t_in, c.t_out = now + 10.0, now + 11.0
+    s = c.summary()
+    assert s["samples"] == 4 and not s["in_timed_region"] and "hw_slowdown" in s["reasons"]
