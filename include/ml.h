@@ -176,8 +176,8 @@ typedef struct {
     /* Certified walk (ML_WALK_CERTIFIED): a warp's level-2 column that has
      * near lenses is walked in certified spans only if every near lens lies
      * farther than span_far lattice spacings (l3x) from its rays, else ray by
-     * ray.  0: the library's choice (3000; with tune, whichever of 3000, 1000,
-     * 300, 100, +inf and no certified spans at all measured fastest; in a
+     * ray.  0: the library's choice (3000; with tune, whichever of 3000, 1500,
+     * 700, 300, 100, +inf and no certified spans at all measured fastest; in a
      * batch, +inf).  Any choice gives the same counts. */
     double span_far;
 } ml_field_desc;

@@ -949,16 +949,17 @@ ml_status measure_grid(const ml_field_desc &d, const std::vector<double> &hx, co
         const uint64_t n = std::min<uint64_t>(total / 2, std::max<uint64_t>(500000000ull, total / 100));
         const uint64_t r0 = (total - 2 * n) / 2;
         const uint64_t warm = std::min<uint64_t>(n, 64ull * (uint64_t)g.n3x);
-        // the certified walk is timed with lens columns spanned beyond three
-        // distances (lattice spacings: where spanning pays depends on the
-        // lenses' pull in pixels per spacing, which differs between fields),
-        // with them always walked ray by ray, and without spans (the per-ray
-        // kernel); the fastest counts
+        // the certified walk is timed with lens columns spanned beyond five
+        // distances about a factor two apart (lattice spacings: where spanning
+        // pays depends on the lenses' pull in pixels per spacing, which differs
+        // between fields), with them always walked ray by ray, and without
+        // spans (the per-ray kernel); the fastest counts
         const bool certified = f->desc.walk == ML_WALK_CERTIFIED && f->g.deposit == ML_DEPOSIT_NGP;
-        constexpr int NV = 6;
-        const float fars[NV] = {ML_SPAN_FAR, 1000.f, 300.f, 100.f, 3.0e38f, 3.0e38f};
+        constexpr int NV = 7;
+        const float fars[NV] = {ML_SPAN_FAR, 1500.f, 700.f, 300.f, 100.f, 3.0e38f, 3.0e38f};
         static const char *const names[NV] = {" (lens columns spanned beyond 3000)",
-                                              " (lens columns spanned beyond 1000)",
+                                              " (lens columns spanned beyond 1500)",
+                                              " (lens columns spanned beyond 700)",
                                               " (lens columns spanned beyond 300)",
                                               " (lens columns spanned beyond 100)",
                                               " (lens columns per ray)", " (no spans)"};
