@@ -45,7 +45,7 @@ HBM_GBS_FALLBACK = 6790.0
 # paper-scale map, 2e9 of the Table-1 fold field, whose 84 MB map stays in
 # L2), valid for the kernel sources whose code (comments and blank space left
 # out, code_hash) has these sha1 prefixes only.
-TRAFFIC_BYTES_PER_RAY = {"paper": (216.086016e6 + 272.358144e6) / 2.0e10,
+TRAFFIC_BYTES_PER_RAY = {"paper": (216.402944e6 + 269.967104e6) / 2.0e10,
                          "fold": (23.782144e6 + 512.0) / 2.0e9}
 TRAFFIC_SOURCES = {"ml_shoot.cu": "48c686ae", "ml_internal.cuh": "4806c1e0", "ml_task.cuh": "3d1d5136"}
 

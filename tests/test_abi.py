@@ -144,7 +144,7 @@ def test_bench_traffic_check_ignores_comments():
     assert bench.traffic_per_launch(1e9) is not None
     # one measured figure per workload of the certified walk; none for the
     # per-ray walk or a workload that was not captured
-    assert bench.traffic_per_launch(2e10) == pytest.approx(216.086016e6 + 272.358144e6)
+    assert bench.traffic_per_launch(2e10) == pytest.approx(216.402944e6 + 269.967104e6)
     assert bench.traffic_per_launch(2e9, "fold") == pytest.approx(23.782144e6 + 512.0)
     assert bench.traffic_per_launch(1e9, "paper", "per_ray") is None
     assert bench.traffic_per_launch(1e9, "batched") is None
