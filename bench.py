@@ -435,7 +435,8 @@ def run_ours(args, rank, world, local):
         expected_local = b - a
     launches = max(1, stats["launches"])
     launch_s = shoot_ms / 1e3 / launches
-    # SURVEY §8(d)'s fixed count: 11 flop per near pair + (8p + 10) per ray
+    # the fixed algorithmic count per launch: 11 flop per near pair (Eq. 9's
+    # near sum) + (8p + 10) per lattice ray (the degree-p series and the pixel)
     alg_flops = (11.0 * stats["near_pairs"] + (8.0 * p + 10.0) * n_local) / launches
     # the FP32 arithmetic actually executed: rays evaluated one by one (the
     # certified walk skips the rest), each its row polynomial as two real
@@ -480,7 +481,7 @@ def run_ours(args, rank, world, local):
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_shoot_mixed",
                      "launch_ms": launch_s * 1e3,
                      "flops_per_launch": alg_flops,
-                     "flop_count": "SURVEY 8(d): 11 per near pair + (8p+10) per lattice ray",
+                     "flop_count": "fixed count: 11 per near pair + (8p+10) per lattice ray",
                      "peak_note": "measured: ml_fp32_fma_peak two-lane FMA probe, best of 5 launches "
                                   f"at {fp32_peak.get('sm_mhz')} MHz (scalar FFMA "
                                   f"{fp32_peak['scalar_tflops']:.1f}, derived "
@@ -830,7 +831,7 @@ def run_batched(args, rank, world, local, compact=False):
                      "frac": achieved / peak, "traffic": None, "kernel": "k_shoot_batch",
                      "rays_evaluated_per_ray": evals / max(1, rays),
                      "note": "whole graph step time (clear, shoot, mu, curves) as the kernel time; "
-                             "SURVEY 8(d)'s fixed flop count per lattice ray",
+                             "the fixed flop count per lattice ray (11 per near pair + (8p+10))",
                      "peak_note": "measured: ml_fp32_fma_peak two-lane FMA probe"},
         "rays_check": {"conserved": all(st["rays_in"] + st["rays_out"] + st["rays_dropped"] ==
                                         i["n_rays_x"] * i["n_rays_y"] for st, i in zip(stats, infos))},
